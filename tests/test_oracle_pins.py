@@ -1,0 +1,390 @@
+"""Pins of the FP64 oracle against what the mathematics fixes.
+
+Each test checks the oracle against something other than itself: closed
+forms (finite-difference weights, stencil symbols, the Kronecker-sum
+spectrum of a separable Hamiltonian, harmonic-oscillator levels), exact
+integer enumeration, invariants (Hermiticity, positivity and rank of the
+nonlocal term, orthonormality) and library routines applied to the same
+mathematical object (dense eigensolvers, Cholesky, linear solves).
+"""
+from fractions import Fraction
+from math import factorial
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import eigensolver, grid as og, hamiltonian as oh, linalg as ol, precond as op, stencil as os_
+
+
+# ---------------------------------------------------------------- stencil ---
+
+def closed_form_weights(m):
+    """Central 2nd-derivative weights, closed form (Fornberg 1988):
+    c_j = 2 (-1)^(j+1) (m!)^2 / (j^2 (m-j)! (m+j)!),  c_0 = -2 sum_j c_j."""
+    c = [Fraction(2 * (-1) ** (j + 1) * factorial(m) ** 2, j * j * factorial(m - j) * factorial(m + j))
+         for j in range(1, m + 1)]
+    return [-2 * sum(c)] + c
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6])
+def test_fd_weights_closed_form(m):
+    assert os_.fd_weights_exact(m) == closed_form_weights(m)
+
+
+def test_fd_weights_golden():
+    # tests/golden/fd_weights_m4.txt: the 25-point (half-width 4) weights
+    lines = [l for l in open(__file__.replace("test_oracle_pins.py", "golden/fd_weights_m4.txt"))
+             if l.strip() and not l.startswith("#")]
+    gold = [Fraction(l.split()[1]) for l in lines]
+    assert os_.fd_weights_exact(4) == gold
+
+
+# ------------------------------------------------------------------- grid ---
+
+def test_single_sphere_count_exact():
+    # atom on a lattice point, dyadic h and R: FP64 arithmetic is exact
+    for h, R in [(0.5, 1.0), (0.5, 1.5), (0.25, 1.0), (0.5, 2.0)]:
+        g = og.sphere_union_grid(np.zeros((1, 3)), R, h)
+        n = int(round(R / h))
+        brute = sum(1 for i in range(-n, n + 1) for j in range(-n, n + 1) for k in range(-n, n + 1)
+                    if (i * i + j * j + k * k) * h * h <= R * R)
+        assert g.npts == brute
+    # lattice points of norm^2 <= 1, 2, 4 in Z^3 (sphere of radius h, sqrt2 h, 2h)
+    assert og.sphere_union_grid(np.zeros((1, 3)), 0.5, 0.5).npts == 7
+    assert og.sphere_union_grid(np.zeros((1, 3)), 1.0, 0.5).npts == 33
+
+
+def test_union_grid_bruteforce_exact_rationals():
+    atoms = np.array([[0.25, 0.5, -0.75], [1.5, 0.0, 0.25], [0.5, 1.25, 1.0]])
+    h, R = 0.25, 1.0
+    g = og.sphere_union_grid(atoms, R, h)
+    A = [[Fraction(v) for v in a] for a in atoms]
+    hF, RF = Fraction(h), Fraction(R)
+    pts = set()
+    for i in range(-10, 12):
+        for j in range(-10, 12):
+            for k in range(-10, 12):
+                r = (i * hF, j * hF, k * hF)
+                if any(sum((r[d] - a[d]) ** 2 for d in range(3)) <= RF * RF for a in A):
+                    pts.add((i, j, k))
+    assert set(map(tuple, g.ijk.tolist())) == pts
+    # lexicographic order and a consistent map
+    assert np.all(np.diff(g.ijk[:, 0]) >= 0)
+    assert np.array_equal(g.lookup(g.ijk), np.arange(g.npts))
+
+
+def test_box_grid():
+    g = og.box_grid(5, 0.3)
+    assert g.npts == 125
+    assert np.allclose(g.coords.sum(axis=0), 0.0)
+    assert np.isclose(g.coords[:, 0].max(), 0.6)
+
+
+# ---------------------------------------------------------------- kinetic ---
+
+def kinetic_only(grid, m=4):
+    return oh.Hamiltonian(grid, np.zeros(grid.npts), None, m=m)
+
+
+def interior(grid, n, w=4):
+    i = grid.ijk
+    return np.all((i >= w) & (i < n - w), axis=1)
+
+
+def test_polynomial_exactness():
+    n, h = 20, 0.25
+    g = og.box_grid(n, h)
+    x, y, z = g.coords.T
+    psi = x ** 9 + 3 * x ** 4 * y ** 5 - z ** 8 + x * y * z + 2.0
+    lap = 72 * x ** 7 + 3 * (12 * x ** 2 * y ** 5 + 20 * x ** 4 * y ** 3) - 56 * z ** 6
+    T = kinetic_only(g).apply(psi)
+    m = interior(g, n)
+    err = np.abs(T[m] - (-0.5 * lap[m])).max() / np.abs(lap[m]).max()
+    assert err < 1e-11
+    # degree 10 is not reproduced: the check has teeth
+    T10 = kinetic_only(g).apply(x ** 10)
+    assert np.abs(T10[m] - (-0.5 * 90 * x[m] ** 8)).max() > 1e-6
+
+
+def test_plane_wave_symbol_interior():
+    n, h = 16, 0.3
+    g = og.box_grid(n, h)
+    k = np.array([0.7, -1.3, 2.1])
+    psi = np.cos(g.coords @ k + 0.4)
+    c = closed_form_weights(4)
+    lam = -0.5 / h ** 2 * sum(float(c[0]) + 2 * sum(float(c[j]) * np.cos(j * ka * h) for j in range(1, 5))
+                              for ka in k)
+    T = kinetic_only(g).apply(psi)
+    m = interior(g, n)
+    assert np.abs(T[m] - lam * psi[m]).max() < 1e-11 * abs(lam)
+
+
+def test_seven_point_sine_modes_whole_box():
+    # half-width 1: sine modes are exact eigenvectors with zero boundaries
+    n, h = 9, 0.4
+    g = og.box_grid(n, h)
+    H = oh.Hamiltonian(g, np.zeros(g.npts), None, m=1)
+    for modes in [(1, 1, 1), (2, 1, 3), (4, 5, 2)]:
+        psi = np.ones(g.npts)
+        lam = 0.0
+        for a, na in enumerate(modes):
+            psi *= np.sin(np.pi * na * (g.ijk[:, a] + 1) / (n + 1))
+            lam += (1 - np.cos(np.pi * na / (n + 1))) / h ** 2
+        assert np.abs(H.apply(psi) - lam * psi).max() < 1e-12 * lam
+
+
+# ------------------------------------------------- separable spectrum (P1) ---
+
+def one_d_levels(n, h, omega):
+    c = closed_form_weights(4)
+    x = (np.arange(n) - (n - 1) / 2) * h
+    T = np.zeros((n, n))
+    for i in range(n):
+        for j in range(-4, 5):
+            if 0 <= i + j < n:
+                T[i, i + j] += -0.5 * float(c[abs(j)]) / h ** 2
+    w, v = np.linalg.eigh(T + np.diag(0.5 * omega ** 2 * x ** 2))
+    return w, v
+
+
+def test_separable_spectrum_dense():
+    n, h, om = 7, 0.45, 1.0
+    g = og.box_grid(n, h)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, om))
+    M = H.dense()
+    assert np.abs(M - M.T).max() < 1e-12
+    e1, _ = one_d_levels(n, h, om)
+    expect = np.sort((e1[:, None, None] + e1[None, :, None] + e1[None, None, :]).ravel())
+    assert np.abs(np.linalg.eigvalsh(M) - expect).max() < 1e-10
+    wj, vj = ol.jacobi_eigh(M)
+    assert np.abs(wj - expect).max() < 1e-10
+    assert np.abs(M @ vj - vj * wj).max() < 1e-9
+
+
+def test_harmonic_oscillator_block_cg():
+    # the 32^3, h=0.3 oscillator; 16 states, lowest 10 judged
+    w = wl.HO32
+    g = og.box_grid(w.system.n, w.system.h)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, w.system.omega))
+    psi0 = wl.random_block(g.npts, w.n_states, w.seed)
+    solver = eigensolver.BlockCG(H, psi0, w.block, tol=1e-7)
+    eps = solver.solve(max_iter=400, judged=w.judged)
+    e1, _ = one_d_levels(w.system.n, w.system.h, w.system.omega)
+    expect = np.sort((e1[:, None, None] + e1[None, :, None] + e1[None, None, :]).ravel())[:w.judged]
+    assert np.abs(eps - expect).max() < 1e-9
+    # analytic (n + 3/2) omega with degeneracies 1, 3, 6 within discretisation error
+    analytic = np.array([1.5] + [2.5] * 3 + [3.5] * 6)
+    assert np.abs(eps - analytic).max() < 1e-4
+
+
+# ------------------------------------------------------------ projectors ---
+
+def small_molecule(h=0.4, R=3.0):
+    atoms = np.array([[0.0, 0.0, 0.0], [1.9, 0.3, -0.2], [0.4, 1.7, 0.8]])
+    g = og.sphere_union_grid(atoms, R, h)
+    E = np.array([[1.3, 0.7], [0.5, 1.9], [1.1, 1.4]])
+    pr = oh.make_projectors(g, atoms, E, 1.0, 3.0)
+    V = wl.local_potential(g.coords, atoms)
+    return g, oh.Hamiltonian(g, V, pr), atoms, E
+
+
+def test_hermiticity_with_overlapping_projectors():
+    g, H, _, _ = small_molecule()
+    rng = np.random.default_rng(5)
+    phi = rng.standard_normal((g.npts, 3))
+    psi = rng.standard_normal((g.npts, 3))
+    a = phi.T @ H.apply(psi)
+    b = H.apply(phi).T @ psi
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+def test_projector_normalisation_and_kb_eigen():
+    h = 0.3
+    g = og.sphere_union_grid(np.zeros((1, 3)), 4.0, h)
+    E = np.array([[1.7, 0.6]])
+    pr = oh.make_projectors(g, np.zeros((1, 3)), E, 1.0, 3.0)
+    gm = pr.gamma(0)
+    Gram = g.dV * gm @ gm.T
+    assert np.abs(Gram - np.eye(4)).max() < 1e-13     # atom on a lattice point: s, p orthonormal
+    H = oh.Hamiltonian(g, np.zeros(g.npts), pr)
+    for q in range(4):
+        v = np.zeros(g.npts)
+        v[pr.points(0)] = gm[q]
+        out = H.apply(v) - H.apply(v, local_only=True)
+        assert np.abs(out - E[0, 0 if q == 0 else 1] * v).max() < 1e-12
+
+
+def test_nonlocal_psd_rank_and_dense_agree():
+    g, H, atoms, _ = small_molecule(h=0.5, R=2.5)
+    n = g.npts
+    eye = np.eye(n)
+    Vnl_apply = H.apply(eye) - H.apply(eye, local_only=True)
+    Vnl = H.nonlocal_dense()
+    assert np.abs(Vnl_apply - Vnl).max() < 1e-12
+    w = np.linalg.eigvalsh(Vnl)
+    assert w.min() > -1e-12
+    assert np.sum(w > 1e-9) <= 4 * len(atoms)
+
+
+# ---------------------------------------------------------- linear algebra ---
+
+def test_cholesky_triinv_against_library():
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((40, 25))
+    S = A.T @ A
+    U = ol.cholesky_upper(S)
+    assert np.abs(U - np.linalg.cholesky(S).T).max() < 1e-12
+    Ui = ol.tri_inv_upper(U)
+    assert np.abs(Ui - np.linalg.inv(U)).max() < 1e-10
+    with pytest.raises(ol.NotPositiveDefinite):
+        ol.cholesky_upper(-S)
+
+
+def test_orthonormalize_invariants():
+    g, H, _, _ = small_molecule()
+    psi = wl.random_block(g.npts, 12, 3)
+    out, Ui = ol.orthonormalize(psi, g.dV)
+    assert np.abs(ol.overlap(out, out, g.dV) - np.eye(12)).max() < 1e-13
+    # span unchanged: psi is reproduced by its projection on the new set
+    proj = out @ ol.overlap(out, psi, g.dV)
+    assert np.abs(proj - psi).max() < 1e-12 * np.abs(psi).max()
+
+
+def test_rayleigh_ritz_on_exact_separable_eigenvectors():
+    n, h = 10, 0.35
+    g = og.box_grid(n, h)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, 1.0))
+    e1, v1 = one_d_levels(n, h, 1.0)
+    idx = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (2, 0, 0)]
+    cols = [np.einsum("i,j,k->ijk", v1[:, a], v1[:, b], v1[:, c]).ravel() for a, b, c in idx]
+    psi = np.stack(cols, axis=1) / np.sqrt(g.dV)
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    psi = psi @ Q                          # rotate inside the subspace
+    eps, _, _, _ = ol.subspace_diag(H.apply, psi, g.dV)
+    expect = np.sort([e1[a] + e1[b] + e1[c] for a, b, c in idx])
+    assert np.abs(eps - expect).max() < 1e-11
+
+
+def test_tiny_molecule_dense_vs_block_cg():
+    atoms = np.array([[0.0, 0.0, 0.0], [1.8, 0.0, 0.0]])
+    g = og.sphere_union_grid(atoms, 2.5, 0.6)
+    pr = oh.make_projectors(g, atoms, np.array([[1.0, 0.8], [1.5, 0.6]]), 1.0, 3.0)
+    H = oh.Hamiltonian(g, wl.local_potential(g.coords, atoms), pr)
+    M = H.dense()
+    ref = np.linalg.eigvalsh(M)
+    wj, _ = ol.jacobi_eigh(M)
+    assert np.abs(wj - ref).max() < 1e-10
+    solver = eigensolver.BlockCG(H, wl.random_block(g.npts, 8, 2), 4, tol=1e-9)
+    eps = solver.solve(max_iter=500)
+    assert np.abs(eps - ref[:8]).max() < 1e-9
+
+
+def test_filter_preconditioner_symmetric():
+    g, _, _, _ = small_molecule()
+    K = eigensolver.FilterPreconditioner(g)
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal((2, g.npts, 2))
+    assert abs(np.sum(a * K(b)) - np.sum(K(a) * b)) < 1e-12 * np.sum(np.abs(a * b))
+    # a constant is unchanged where all six face neighbours are grid points
+    one = np.ones((g.npts, 1))
+    full = np.all(g.neighbours(1).reshape(g.npts, 6) >= 0, axis=1)
+    assert np.abs(K(one)[full] - 1).max() < 1e-15
+
+
+# ------------------------------------------------------ CG and conv net ---
+
+def test_cg_converges_to_direct_solve():
+    atoms = np.array([[0.0, 0.0, 0.0]])
+    g = og.sphere_union_grid(atoms, 1.5, 0.5)
+    r = wl.random_block(g.npts, 2, 9)
+    x = op.shifted_poisson_cg(g, r, sigma=1.0, n_iter=200)
+    A = oh.Hamiltonian(g, np.full(g.npts, 1.0)).dense()
+    assert np.abs(x - np.linalg.solve(A, r)).max() < 1e-10
+
+
+def test_cg_iterate_is_krylov_minimiser():
+    # after k steps CG minimises the A-norm error over the Krylov space K_k(A, r)
+    atoms = np.array([[0.0, 0.0, 0.0]])
+    g = og.sphere_union_grid(atoms, 2.0, 0.5)
+    r = wl.random_block(g.npts, 1, 4)[:, 0]
+    A = oh.Hamiltonian(g, np.full(g.npts, 1.0)).dense()
+    k = 6
+    x = op.shifted_poisson_cg(g, r[:, None], n_iter=k)[:, 0]
+    K = np.stack([np.linalg.matrix_power(A, j) @ r for j in range(k)], axis=1)
+    Q, _ = np.linalg.qr(K)
+    y = np.linalg.solve(Q.T @ A @ Q, Q.T @ r)
+    assert np.abs(x - Q @ y).max() < 1e-8 * np.abs(x).max()
+
+
+def brute_conv(x, w):
+    B, ci, X, Y, Z = x.shape
+    co = w.shape[0]
+    y = np.zeros((B, co, X, Y, Z))
+    for b in range(B):
+        for o in range(co):
+            for i in range(X):
+                for j in range(Y):
+                    for k in range(Z):
+                        s = 0.0
+                        for c in range(ci):
+                            for a in range(3):
+                                for bb in range(3):
+                                    for cc in range(3):
+                                        ii, jj, kk = i + a - 1, j + bb - 1, k + cc - 1
+                                        if 0 <= ii < X and 0 <= jj < Y and 0 <= kk < Z:
+                                            s += w[o, c, a, bb, cc] * x[b, c, ii, jj, kk]
+                        y[b, o, i, j, k] = s
+    return y
+
+
+def test_conv3_bruteforce():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((1, 2, 4, 5, 3))
+    w = rng.standard_normal((3, 2, 3, 3, 3))
+    assert np.abs(op.conv3(x, w) - brute_conv(x, w)).max() < 1e-12
+
+
+def test_net_gradients_finite_difference():
+    rng = np.random.default_rng(1)
+    ws = [w.astype(np.float64) for w in wl.conv_init(7, channels=3)]
+    shape = (2, 6, 6, 6)
+    xhat = rng.standard_normal(shape)
+    mask = rng.uniform(size=shape) > 0.2
+    target = rng.standard_normal(shape)
+    valid = np.zeros(shape)
+    valid[:, 1:5, 1:5, 1:5] = mask[:, 1:5, 1:5, 1:5]
+
+    def loss(wl_):
+        y, _ = op.net_forward(xhat, mask, wl_)
+        return op.tile_loss(y, target, valid)[0]
+
+    y, cache = op.net_forward(xhat, mask, ws)
+    _, gy = op.tile_loss(y, target, valid)
+    grads = op.net_backward(gy, cache, ws)
+    for li in range(3):
+        for _ in range(6):
+            idx = tuple(rng.integers(0, s) for s in ws[li].shape)
+            e = 1e-6
+            wp = [w.copy() for w in ws]
+            wm = [w.copy() for w in ws]
+            wp[li][idx] += e
+            wm[li][idx] -= e
+            fd = (loss(wp) - loss(wm)) / (2 * e)
+            assert abs(fd - grads[li][idx]) <= 1e-7 * max(1.0, abs(fd)) + 1e-9
+
+
+def test_bf16_round_matches_library():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(2).standard_normal(10000).astype(np.float32) * 100
+    ref = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
+    assert np.array_equal(op.bf16_round(x), ref)
+
+
+def test_adam_first_step_is_signed_lr():
+    # with bias correction, the first Adam step is lr * g / (|g| + eps')
+    p = [np.array([1.0, -2.0, 0.5])]
+    g = [np.array([0.3, -4.0, 1e-3])]
+    out = op.Adam(p).step(p, g)[0]
+    assert np.allclose(out, p[0] - 1e-3 * g[0] / (np.abs(g[0]) + 1e-8), rtol=0, atol=1e-12)

@@ -1,0 +1,161 @@
+"""Seeded synthetic inputs for the real-space Kohn-Sham workloads.
+
+This module is the one piece shared by the CPU oracle, the tests and the
+benchmark.  It draws random numbers and evaluates the synthetic *input*
+fields (atom positions, Kleinman-Bylander couplings, the local
+pseudopotential's values at given coordinates, orbital blocks, network
+weights).  It holds none of the method's arithmetic: no grid construction,
+no stencil, no projector, no linear algebra.
+
+The paper's own molecules, pseudopotentials and geometries are not
+available (its 40-molecule set is supplementary material, Table I), so
+seeded synthetic molecules stand in for them with the sizes of the paper's
+workloads (uniform grids with spacing of a few tenths of a Bohr on a union
+of atom-centred spheres, Sec. II and Sec. XI).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy.special import erf
+
+# Synthetic local pseudopotential  v(d) = -Z erf(d / a) / d  (Z=4, a=0.8 Bohr)
+Z_ION = 4.0
+A_LOC = 0.8
+
+
+@dataclass(frozen=True)
+class MoleculeSpec:
+    """A synthetic molecule: atoms placed uniformly at random in a cube."""
+    n_atoms: int
+    cube: float          # side of the cube the atoms are drawn in [Bohr]
+    min_sep: float       # minimum distance between atoms [Bohr]
+    radius: float        # radius of the union-of-spheres grid [Bohr]
+    h: float             # grid spacing [Bohr]
+    seed: int
+    r_c: float = 1.0     # Gaussian width of the projector radial function
+    r_cut: float = 3.0   # projector sphere radius
+    e_lo: float = 0.5    # KB coupling range [Ha]
+    e_hi: float = 2.0
+
+
+@dataclass(frozen=True)
+class BoxSpec:
+    """A full cubic box of n^3 points, coordinates centred on the origin."""
+    n: int
+    h: float
+    omega: float = 1.0
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    system: object       # MoleculeSpec | BoxSpec
+    n_states: int
+    block: int
+    judged: int
+    precision: str       # "f64" | "mixed"
+    precond: str         # "filter" | "learned"
+    seed: int
+
+
+# The five workloads of the hot path (harmonic oscillator, 20/100/300 atoms).
+HO32 = Workload("ho32_h0.3", BoxSpec(32, 0.3, 1.0), 16, 16, 10, "f64", "filter", 1306)
+MOL20 = Workload("mol20_h0.35", MoleculeSpec(20, 12.0, 2.0, 5.0, 0.35, 1306), 48, 16, 48, "f64", "filter", 1306)
+MOL100 = Workload("mol100_h0.3", MoleculeSpec(100, 22.0, 2.0, 5.0, 0.3, 1307), 256, 32, 256, "mixed", "filter", 1307)
+MOL100_LEARNED = Workload("mol100_h0.3_learned", MOL100.system, 256, 32, 256, "mixed", "learned", 1307)
+MOL300 = Workload("mol300_h0.3", MoleculeSpec(300, 32.0, 2.0, 5.0, 0.3, 1308), 1024, 32, 1024, "mixed", "learned", 1308)
+WORKLOADS = {w.name: w for w in (HO32, MOL20, MOL100, MOL100_LEARNED, MOL300)}
+
+
+def atom_positions(spec: MoleculeSpec, max_tries: int = 1_000_000) -> np.ndarray:
+    """Rejection-sample ``n_atoms`` points uniform in [0, cube]^3 with pairwise
+    distance >= ``min_sep``.  Returns float64 [n_atoms, 3] (Bohr)."""
+    rng = np.random.default_rng(spec.seed)
+    pos = np.empty((spec.n_atoms, 3))
+    n = 0
+    tries = 0
+    while n < spec.n_atoms:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place atoms with the requested separation")
+        c = rng.uniform(0.0, spec.cube, size=3)
+        if n == 0 or np.min(np.sum((pos[:n] - c) ** 2, axis=1)) >= spec.min_sep ** 2:
+            pos[n] = c
+            n += 1
+    return pos
+
+
+def kb_couplings(spec: MoleculeSpec) -> np.ndarray:
+    """One coupling per atom and angular channel (s, p), uniform in
+    [e_lo, e_hi] Ha.  Returns float64 [n_atoms, 2]."""
+    rng = np.random.default_rng([spec.seed, 1])
+    return rng.uniform(spec.e_lo, spec.e_hi, size=(spec.n_atoms, 2))
+
+
+def local_potential(coords: np.ndarray, atoms: np.ndarray, z: float = Z_ION, a: float = A_LOC,
+                    chunk: int = 65536) -> np.ndarray:
+    """Synthetic local pseudopotential  V(r) = sum_A -z erf(|r-R_A|/a)/|r-R_A|
+    evaluated at ``coords`` [n,3]; the d -> 0 limit is -2z/(a sqrt(pi))."""
+    coords = np.asarray(coords, dtype=np.float64)
+    out = np.zeros(len(coords))
+    lim = -2.0 * z / (a * np.sqrt(np.pi))
+    for s in range(0, len(coords), chunk):
+        c = coords[s:s + chunk]
+        acc = np.zeros(len(c))
+        for A in atoms:
+            d = np.sqrt(((c - A) ** 2).sum(axis=1))
+            small = d < 1e-12
+            dd = np.where(small, 1.0, d)
+            acc += np.where(small, lim, -z * erf(dd / a) / dd)
+        out[s:s + chunk] = acc
+    return out
+
+
+def harmonic_potential(coords: np.ndarray, omega: float) -> np.ndarray:
+    """V(r) = omega^2 |r|^2 / 2 at ``coords`` [n,3]."""
+    coords = np.asarray(coords, dtype=np.float64)
+    return 0.5 * omega * omega * (coords ** 2).sum(axis=1)
+
+
+def random_block(n_rows: int, n_cols: int, seed: int) -> np.ndarray:
+    """Uniform [-1, 1] float64 block [n_rows, n_cols] (state index fastest)."""
+    rng = np.random.default_rng([seed, 2])
+    return rng.uniform(-1.0, 1.0, size=(n_rows, n_cols))
+
+
+def gaussian_sum_block(coords: np.ndarray, n_cols: int, seed: int, n_gauss: int = 6) -> np.ndarray:
+    """Smooth orbitals: each column is a sum of ``n_gauss`` Gaussians with
+    random centres inside the bounding box of ``coords``, widths in
+    [0.6, 2.0] Bohr and weights in [-1, 1]."""
+    rng = np.random.default_rng([seed, 3])
+    coords = np.asarray(coords, dtype=np.float64)
+    lo, hi = coords.min(axis=0), coords.max(axis=0)
+    out = np.zeros((len(coords), n_cols))
+    for k in range(n_cols):
+        for _ in range(n_gauss):
+            c = rng.uniform(lo, hi)
+            w = rng.uniform(0.6, 2.0)
+            a = rng.uniform(-1.0, 1.0)
+            out[:, k] += a * np.exp(-((coords - c) ** 2).sum(axis=1) / (2 * w * w))
+    return out
+
+
+def conv_init(seed: int, channels: int = 8, ksize: int = 3) -> list[np.ndarray]:
+    """He-normal initial weights of the 1 -> C -> C -> 1 conv net, float32,
+    shapes [c_out, c_in, k, k, k]."""
+    rng = np.random.default_rng([seed, 4])
+    shapes = [(channels, 1), (channels, channels), (1, channels)]
+    ws = []
+    for co, ci in shapes:
+        fan_in = ci * ksize ** 3
+        ws.append((rng.standard_normal((co, ci, ksize, ksize, ksize)) * np.sqrt(2.0 / fan_in)).astype(np.float32))
+    return ws
+
+
+def lexsort_ijk(ijk: np.ndarray) -> np.ndarray:
+    """Permutation that sorts integer lattice coordinates [n,3] with i
+    slowest and k fastest (lexicographic order)."""
+    ijk = np.asarray(ijk)
+    return np.lexsort((ijk[:, 2], ijk[:, 1], ijk[:, 0]))
