@@ -1,0 +1,287 @@
+"""Benchmark of the real-space Kohn-Sham hot path on GB300.
+
+Default workload: the 100-atom synthetic molecule (22 Bohr cube, union of
+5 Bohr spheres at h = 0.3 Bohr), 256 states stored [npts][256] FP32, H psi
+applied block by block (8 blocks of 32 states) -- one step is H applied to
+every state.  Metric: H psi GB/s of algorithmic traffic (psi read once,
+H psi written once, potential, point map and projector tables), reported
+against the measured HBM copy bandwidth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the path runs as independent replicas (one per rank, no
+collective on the data path); value = work of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "H·ψ GB/s & % HBM roofline; eigensolve s to 1e-6 Ha, mixed+learned vs FP64"
+NB = 32
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rsdft_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_system(workload):
+    """Library grid + Hamiltonian of a synthetic molecule (no oracle)."""
+    from paper_1306_2953_gb300 import api
+    spec = workload.system
+    atoms = wl.atom_positions(spec)
+    E = wl.kb_couplings(spec)
+    g = api.Grid.spheres(atoms, spec.radius, spec.h)
+    pr = api.Projectors(g, atoms, E, spec.r_c, spec.r_cut)
+    V = wl.local_potential(g.coords(), atoms)
+    return g, api.Hamiltonian(g, V, pr)
+
+
+def cpu_baseline(workload, nb_sample: int, budget_s: float = 20.0):
+    """The FP64 oracle's H psi (plain C loops, OpenMP on all host cores) on a
+    bounded sample: one block of nb_sample states of the same molecule."""
+    from oracle import grid as og, hamiltonian as oh
+    spec = workload.system
+    atoms = wl.atom_positions(spec)
+    E = wl.kb_couplings(spec)
+    g = og.sphere_union_grid(atoms, spec.radius, spec.h)
+    H = oh.Hamiltonian(g, wl.local_potential(g.coords, atoms), oh.make_projectors(g, atoms, E, spec.r_c, spec.r_cut))
+    psi = wl.random_block(g.npts, nb_sample, 1)
+    H.apply(psi)  # warm
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        H.apply(psi)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 50:
+            break
+    dt = (time.perf_counter() - t0) / n
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return g, dt, cores
+
+
+def algorithmic_bytes_f32(npts, n_entries, n_atoms, nst, nb=NB):
+    """Same byte model as rs_ham_apply_bytes for FP32, for nst states."""
+    s = 4
+    per_block = (npts * nb * 2 * s + npts * s + npts * 4 + n_entries * (4 + 4 * s) * 2 + (npts + 1) * 4
+                 + n_atoms * 4 * nb * s * 2 + (n_atoms + 1) * 4)
+    return per_block * (nst // nb)
+
+
+def run_reference(args, workload):
+    """The CPU oracle as the reference arm: its FP64 H psi on the host cores,
+    one block of 8 states of the same molecule per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import grid as og, hamiltonian as oh
+    spec = workload.system
+    atoms = wl.atom_positions(spec)
+    g = og.sphere_union_grid(atoms, spec.radius, spec.h)
+    pr = oh.make_projectors(g, atoms, wl.kb_couplings(spec), spec.r_c, spec.r_cut)
+    H = oh.Hamiltonian(g, wl.local_potential(g.coords, atoms), pr)
+    nb = 8
+    psi = wl.random_block(g.npts, nb, 1)
+    for _ in range(args.warmup):
+        H.apply(psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H.apply(psi)
+    dt = (time.perf_counter() - t0) / args.steps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    by = algorithmic_bytes_f32(g.npts, int(pr.sph_off[-1]), spec.n_atoms, nb, nb=nb)
+    v = by / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload.name, "npts": g.npts, "states_per_step": nb, "block": nb},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle H psi on one block of {nb} states of {workload.name} per step"},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=wl.MOL100.name, choices=[wl.MOL100.name, wl.MOL300.name])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    workload = wl.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, workload)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1306_2953_gb300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    g, H = build_system(workload)
+    npts = g.npts
+    nst = workload.n_states
+    psi_h = torch.from_numpy(wl.random_block(npts, nst, workload.seed).astype(np.float32))
+    psi = psi_h.to(dev)
+    hpsi = torch.empty_like(psi)
+    L = _lib.lib()
+    bytes_per_apply = H.apply_bytes(NB, _lib.RS_F32)
+    bytes_per_step = bytes_per_apply * (nst // NB)
+    import ctypes
+    pb, sb = ctypes.c_int64(), ctypes.c_int64()
+    _lib.call("rs_ham_launch_bytes", H._h, NB, _lib.RS_F32, ctypes.byref(pb), ctypes.byref(sb))
+
+    def step(src, dst):
+        for b in range(0, nst, NB):
+            H.apply(src[:, b:b + NB], dst[:, b:b + NB], nb=NB)
+
+    for _ in range(max(args.warmup, 3)):
+        step(psi, hpsi)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    _lib.call("rs_ham_timing", H._h, 1)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(psi, hpsi)
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    _lib.call("rs_ham_timing", H._h, 0)
+    ms = e0.elapsed_time(e1)
+    pms, sms, ncalls = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _lib.call("rs_ham_timing_read", H._h, ctypes.byref(pms), ctypes.byref(sms), ctypes.byref(ncalls))
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API: pinned host psi in, H psi back out
+    psi_pin = psi_h.pin_memory()
+    out_pin = torch.empty_like(psi_pin).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        psi.copy_(psi_pin, non_blocking=True)
+        step(psi, hpsi)
+        out_pin.copy_(hpsi, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = psi.numel() * 4
+
+    value = world * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    stencil_gbs = sb.value * ncalls.value / (sms.value * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload.name, "npts": npts, "states": nst, "block": NB,
+                       "psi_bytes": psi.numel() * 4, "l2": "inputs (psi, 0.73 GB) larger than L2 (129 MB)",
+                       "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "hbm", "kernel": "k_stencil (fused stencil + V + nonlocal gather)",
+                         "achieved": stencil_gbs, "peak": peak, "unit": "GB/s", "frac": stencil_gbs / peak,
+                         "peak_source": peak_kind, "traffic": None,
+                         "stencil_ms_per_launch": sms.value / max(ncalls.value, 1),
+                         "project_ms_per_launch": pms.value / max(ncalls.value, 1)},
+            "e2e": {"value": world * bytes_per_step / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": h2d},
+            "gpu_launches": int(2 * (nst // NB) * args.steps), "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gcpu, dt, cores = cpu_baseline(workload, NB)
+        by = bytes_per_apply  # the same FP32 block bytes, computed by the oracle in FP64
+        line["cpu_baseline"] = {"value": by / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                                "sample": f"FP64 oracle H psi on one block of {NB} states of {workload.name} "
+                                          f"({dt:.2f} s per block)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,245 @@
+/*
+ * rsdft.h -- C ABI of the GB300 real-space Kohn-Sham hot path.
+ *
+ * The operations follow Andrade & Aspuru-Guzik, "Real-space density
+ * functional theory on graphical processing units" (arXiv:1306.2953):
+ * blocks of orbitals stored point-major with the state index fastest
+ * (Sec. IV, Fig. 4b), the Kohn-Sham Hamiltonian applied in operator form
+ * (Sec. V, Eq. 3) as a 25-point star finite-difference kinetic term
+ * (Sec. V.A), a local potential (Sec. V.B) and Kleinman-Bylander nonlocal
+ * projectors (Sec. V.C, Eq. 4), and the overlap / Cholesky
+ * orthogonalisation and subspace diagonalisation of Sec. VI (Eqs. 5-8).
+ *
+ * Conventions
+ *  - Every call returns an int status: RS_OK (0) or a negative RS_E* code;
+ *    rs_last_error() gives a message for the calling thread.  No C++
+ *    exception crosses this boundary.
+ *  - Orbital blocks are row-major [npts][ld] arrays: the value of state s at
+ *    grid point p is at element p*ld + s; ld >= the number of states used.
+ *    Grid points are in the library's order (bricks of 4x4x4 lattice points,
+ *    Sec. V.A "small parallelepipedic grids"); rs_grid_ijk() gives each
+ *    point's integer lattice coordinates.
+ *  - dtype is RS_F64 (double) or RS_F32 (float).
+ *  - Pointers named *_dev are device pointers on the current CUDA device and
+ *    stay owned by the caller; handles own only their internal tables and
+ *    workspace.  Device pointers to orbital data must be 16-byte aligned and
+ *    ld*sizeof(element) a multiple of 16 bytes whenever the block size is at
+ *    least 16 bytes per point.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls marked "asynchronous" only enqueue work on it; calls
+ *    marked "blocking" synchronise it before returning.
+ */
+#ifndef RSDFT_H
+#define RSDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RS_OK = 0,
+    RS_EINVAL = -1,   /* bad argument (null pointer, size, alignment, block size) */
+    RS_ENOMEM = -2,   /* host or device allocation failed */
+    RS_ECUDA = -3,    /* a CUDA runtime call failed; no GPU; or the kernel image is missing */
+    RS_ENOTSPD = -4,  /* overlap matrix not positive definite (Cholesky failed) */
+    RS_ENOCONV = -5,  /* an iteration cap was hit */
+    RS_ENAN = -6      /* a non-finite value was detected */
+};
+
+enum { RS_F64 = 0, RS_F32 = 1 };
+enum { RS_PRECOND_NONE = 0, RS_PRECOND_FILTER = 1, RS_PRECOND_LEARNED = 2 };
+
+typedef struct rs_grid rs_grid;
+typedef struct rs_proj rs_proj;
+typedef struct rs_ham rs_ham;
+typedef struct rs_solver rs_solver;
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len).  Returns the message length. */
+int rs_last_error(char *buf, size_t len);
+
+/* Library version string, e.g. "rsdft 0.1 sm_103a". */
+const char *rs_version(void);
+
+/* ------------------------------------------------------------------ grid --
+ * Sec. II (Fig. 1): a uniform grid of spacing h whose shape is the union of
+ * spheres of `radius` around the atoms.  Lattice points are r = h*(i,j,k);
+ * a point is included iff for some atom A, (x-X)^2+(y-Y)^2+(z-Z)^2 <=
+ * radius^2, evaluated in IEEE double in that order with x = h*i (exact
+ * integer decisions; no contraction into FMA).  Host-only: no GPU needed.
+ *   xyz      host [n_atoms][3] atom positions (Bohr)
+ *   out      receives a new handle (free with rs_grid_destroy)
+ * Errors: RS_EINVAL for n_atoms < 1, radius <= 0, h <= 0, non-finite input,
+ * or a grid that would exceed 2^31-1 points or map entries. */
+int rs_grid_create_spheres(const double *xyz, int n_atoms, double radius, double h, rs_grid **out);
+
+/* Full n0 x n1 x n2 box (zero boundary conditions beyond it), point (i,j,k)
+ * at ((i-(n0-1)/2) h, (j-(n1-1)/2) h, (k-(n2-1)/2) h).  Host-only. */
+int rs_grid_create_box(int n0, int n1, int n2, double h, rs_grid **out);
+
+/* Number of points, lattice coordinate of map element (0,0,0), map
+ * dimensions (the bounding box plus a 4-point margin on every side) and the
+ * spacing.  Any output pointer may be NULL.  Host-only. */
+int rs_grid_info(const rs_grid *g, int64_t *npts, int32_t origin[3], int32_t dims[3], double *h);
+
+/* Integer lattice coordinates of every point, host [npts][3].  Host-only. */
+int rs_grid_ijk(const rs_grid *g, int32_t *ijk_out);
+
+/* Cartesian coordinates of every point, host [npts][3] (Bohr).  Host-only. */
+int rs_grid_coords(const rs_grid *g, double *xyz_out);
+
+/* The int32 point map over the bounding box, host [dims0][dims1][dims2]:
+ * the library index of the point at lattice coordinate origin+(a,b,c), or
+ * -1 where that lattice point is not a grid point (the compact neighbour
+ * table of Sec. V.A).  Host-only. */
+int rs_grid_point_map(const rs_grid *g, int32_t *map_out);
+
+int rs_grid_destroy(rs_grid *g);
+
+/* ------------------------------------------------------------ projectors --
+ * Kleinman-Bylander projectors of Sec. V.C, Eq. (4).  For every atom A the
+ * four projectors (s, p_x, p_y, p_z) are
+ *   g(d) = exp(-d^2/(2 r_c^2)),  gamma_s = N g,  gamma_px = N (x-X) g, ...
+ * on the grid points with d^2 <= r_cut^2 (same exact FP64 test as the grid),
+ * each normalised on its own point list so that dV*sum(gamma^2) = 1, with
+ * one coupling E[A][l] (l = s, p) in Hartree: V_nl = sum E |gamma><gamma|.
+ * Host-only. */
+typedef struct {
+    int n_atoms;
+    const double *xyz;   /* host [n_atoms][3] */
+    const double *E;     /* host [n_atoms][2]: (E_s, E_p) in Ha */
+    double r_c;          /* Gaussian width of the radial function (Bohr) */
+    double r_cut;        /* projector sphere radius (Bohr) */
+} rs_projector_spec;
+
+int rs_proj_create(const rs_grid *g, const rs_projector_spec *spec, rs_proj **out);
+
+/* Sizes of the sphere lists: n_atoms and the total number of entries. */
+int rs_proj_info(const rs_proj *pr, int32_t *n_atoms, int64_t *n_entries);
+
+/* Sphere lists: sph_off host [n_atoms+1], sph_idx host [n_entries] (library
+ * point ids, ascending within an atom), gamma host [n_entries][4]
+ * (s, px, py, pz).  Any output may be NULL. */
+int rs_proj_tables(const rs_proj *pr, int64_t *sph_off, int32_t *sph_idx, double *gamma);
+
+int rs_proj_destroy(rs_proj *pr);
+
+/* ----------------------------------------------------------- Hamiltonian --
+ * Builds H = -1/2 Lap + V + V_nl (Eq. 3) on the current CUDA device.
+ *   V_host   host [npts] local potential (Ha) in library point order
+ *   pr       projectors or NULL (no nonlocal term)
+ *   order    stencil half-width m in 1..4 (4 = the paper's 25-point star);
+ *            weights are the central second-derivative weights of Sec. V.A
+ * Copies every table to the device (blocking).  Errors: RS_EINVAL,
+ * RS_ENOMEM, RS_ECUDA (no device). */
+int rs_ham_create(const rs_grid *g, const double *V_host, const rs_proj *pr, int order, rs_ham **out);
+
+int rs_ham_destroy(rs_ham *h);
+
+/* hpsi = H psi for a block of nb orbitals (Sec. V; Figs. 9-11), in one pass:
+ * the projection integrals of Eq. (4) first, then one fused kernel that
+ * applies the 25-point stencil, adds V*psi and gathers the nonlocal term
+ * (race-free: every output point sums its covering atoms itself).
+ *   psi_dev   device [npts][ld_psi] (first nb columns used), dtype elements
+ *   hpsi_dev  device [npts][ld_hpsi]; must not overlap psi_dev
+ *   nb        1, 2, 4, 8, 16, 32 or 64 (a power of two, Sec. IV)
+ * Asynchronous.  Errors: RS_EINVAL (nb, ld, alignment, null), RS_ECUDA. */
+int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi, void *hpsi_dev, int64_t ld_hpsi,
+                       int nb, int dtype, void *stream);
+
+/* Algorithmic bytes one rs_ham_apply_block call moves (psi read once, hpsi
+ * written once, V, the point map and the projector tables), used for GB/s. */
+int64_t rs_ham_apply_bytes(const rs_ham *h, int nb, int dtype);
+
+/* Per-launch timing of rs_ham_apply_block (a native profiling aid): while
+ * enabled, every call records CUDA events on its stream around the
+ * projection launch and around the fused stencil launch.
+ * rs_ham_timing(h, 1) clears the record and starts; rs_ham_timing(h, 0)
+ * stops.  rs_ham_timing_read synchronises on the recorded events (blocking)
+ * and returns the summed milliseconds and the number of calls recorded. */
+int rs_ham_timing(rs_ham *h, int enable);
+int rs_ham_timing_read(rs_ham *h, double *project_ms, double *stencil_ms, int64_t *calls);
+
+/* Bytes of the two launches of one rs_ham_apply_block call, counted as in
+ * rs_ham_apply_bytes: project_bytes (sphere tables read, coefficients
+ * written) and stencil_bytes (psi read, hpsi written, V, map, point-major
+ * projector tables, coefficients read). */
+int rs_ham_launch_bytes(const rs_ham *h, int nb, int dtype, int64_t *project_bytes, int64_t *stencil_bytes);
+
+/* ------------------------------------------------------- linear algebra --
+ * Overlap S = dV * X^T Y (Sec. VI, Eq. 5; S_jk = <x_j|y_k>), computed by
+ * blocks of points and accumulated in FP64.
+ *   X_dev [npts][ldx] (nx columns), Y_dev [npts][ldy] (ny columns), dtype
+ *   S_dev device double [nx][lds]
+ * Asynchronous. */
+int rs_overlap_block(const rs_grid *g, const void *X_dev, int64_t ldx, int nx, const void *Y_dev, int64_t ldy,
+                     int ny, double *S_dev, int64_t lds, int dtype, void *stream);
+
+/* Device workspace (bytes) that rs_orthonormalize / rs_subspace_diag need
+ * for nst states. */
+int64_t rs_linalg_workspace_bytes(int nst);
+
+/* Orthonormalisation by Cholesky (Sec. VI, Eqs. 5-6): S = <Psi|Psi>,
+ * S = U^T U (FP64, on the device), Psi <- Psi U^-1, i.e. Eq. (6) read as
+ * phi_j = sum_k U_kj phibar_k.  Psi is updated in place.
+ *   work_dev  device workspace of rs_linalg_workspace_bytes(nst) bytes
+ *   Uinv_dev  optional device double [nst][nst] receiving U^-1 (or NULL)
+ * Blocking (reads the factorisation status).  Errors: RS_ENOTSPD when S is
+ * not positive definite (Psi left unchanged). */
+int rs_orthonormalize(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int dtype, void *work_dev,
+                      double *Uinv_dev, void *stream);
+
+/* Subspace diagonalisation (Sec. VI, Eqs. 7-8): HPsi = H Psi, h = <Psi|H|Psi>
+ * (symmetrised, FP64), h xi = xi diag(eps) with eps ascending (FP64 on the
+ * device), Psi <- Psi xi and HPsi <- HPsi xi.  Psi must be orthonormal.
+ *   HPsi_dev  device [npts][ld] receiving H Psi (rotated)
+ *   eps_dev   device double [nst]
+ *   xi_dev    optional device double [nst][nst] receiving xi (or NULL)
+ * Blocking.  Errors: RS_ENOCONV if the dense eigensolver hit its cap. */
+int rs_subspace_diag(rs_ham *h, void *Psi_dev, void *HPsi_dev, int64_t ld, int nst, int dtype, int nb,
+                     double *eps_dev, double *xi_dev, void *work_dev, void *stream);
+
+/* --------------------------------------------------------------- solver --
+ * Block conjugate-gradient eigensolver.  The paper's RMM-DIIS (Sec. III) is
+ * replaced by LOBPCG swept block by block with a per-block convergence rule
+ * (a block stops only when all its states are converged, Sec. VIII) and
+ * orthonormalisation + subspace diagonalisation after every sweep
+ * (Sec. VI).  Precision RS_F64 runs everything in FP64; RS_F32 runs H psi
+ * and the inner iterations in FP32 and keeps Cholesky, Rayleigh-Ritz,
+ * residual norms and eigenvalues in FP64. */
+typedef struct {
+    int nst;              /* states (a multiple of nb) */
+    int nb;               /* block size: power of two, 1..64 */
+    int dtype;            /* RS_F64 or RS_F32 */
+    int precond;          /* RS_PRECOND_* */
+    double tol;           /* residual-norm threshold per state */
+    double filter_alpha;  /* filter weight alpha (0.5) */
+} rs_solver_cfg;
+
+/* Creates a solver and allocates its device workspace (blocking).
+ * Psi0_dev: device [npts][nst] start vectors (dtype); they are copied,
+ * orthonormalised and subspace-diagonalised. */
+int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void *Psi0_dev, void *stream, rs_solver **out);
+
+/* One sweep over all blocks (see above).  eps_dev / resnorm_dev: device
+ * double [nst] (may be NULL); n_converged: host, states with residual norm
+ * <= tol (may be NULL).  Blocking (reads the convergence count). */
+int rs_eigensolver_step(rs_solver *s, double *eps_dev, double *resnorm_dev, int *n_converged, void *stream);
+
+/* The solver's current orbitals: device [npts][nst] (dtype), owned by the
+ * solver; valid until rs_solver_destroy. */
+int rs_solver_psi(rs_solver *s, void **psi_dev);
+
+/* Learned-preconditioner weights (FP32 master copy, layouts [8][1][27],
+ * [8][8][27], [1][8][27]); device pointers.  Used by RS_PRECOND_LEARNED. */
+int rs_solver_set_precond_weights(rs_solver *s, const float *w1_dev, const float *w2_dev, const float *w3_dev);
+
+int rs_solver_destroy(rs_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSDFT_H */

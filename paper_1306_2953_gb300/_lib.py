@@ -1,0 +1,113 @@
+"""ctypes binding of ``librsdft.so`` (declarations in include/rsdft.h).
+
+Argument marshalling only: every computation runs in the library.  The
+library must have been built (``python -m paper_1306_2953_gb300.build``);
+loading fails loudly otherwise -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsdft.so")
+
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENOTSPD, RS_ENOCONV, RS_ENAN = 0, -1, -2, -3, -4, -5, -6
+RS_F64, RS_F32 = 0, 1
+RS_PRECOND_NONE, RS_PRECOND_FILTER, RS_PRECOND_LEARNED = 0, 1, 2
+_NAMES = {RS_EINVAL: "RS_EINVAL", RS_ENOMEM: "RS_ENOMEM", RS_ECUDA: "RS_ECUDA", RS_ENOTSPD: "RS_ENOTSPD",
+          RS_ENOCONV: "RS_ENOCONV", RS_ENAN: "RS_ENAN"}
+
+
+class RsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ProjectorSpec(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("xyz", ctypes.c_void_p), ("E", ctypes.c_void_p),
+                ("r_c", ctypes.c_double), ("r_cut", ctypes.c_double)]
+
+
+class SolverCfg(ctypes.Structure):
+    _fields_ = [("nst", ctypes.c_int), ("nb", ctypes.c_int), ("dtype", ctypes.c_int), ("precond", ctypes.c_int),
+                ("tol", ctypes.c_double), ("filter_alpha", ctypes.c_double)]
+
+
+P = ctypes.c_void_p
+I32, I64, F64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); restype None means "int status, checked"
+SIGNATURES = {
+    "rs_last_error": (I32, [ctypes.c_char_p, ctypes.c_size_t]),
+    "rs_version": (ctypes.c_char_p, []),
+    "rs_grid_create_spheres": (None, [P, I32, F64, F64, PP]),
+    "rs_grid_create_box": (None, [I32, I32, I32, F64, PP]),
+    "rs_grid_info": (None, [P, P, P, P, P]),
+    "rs_grid_ijk": (None, [P, P]),
+    "rs_grid_coords": (None, [P, P]),
+    "rs_grid_point_map": (None, [P, P]),
+    "rs_grid_destroy": (None, [P]),
+    "rs_proj_create": (None, [P, ctypes.POINTER(ProjectorSpec), PP]),
+    "rs_proj_info": (None, [P, P, P]),
+    "rs_proj_tables": (None, [P, P, P, P]),
+    "rs_proj_destroy": (None, [P]),
+    "rs_ham_create": (None, [P, P, P, I32, PP]),
+    "rs_ham_destroy": (None, [P]),
+    "rs_ham_apply_block": (None, [P, P, I64, P, I64, I32, I32, P]),
+    "rs_ham_apply_bytes": (I64, [P, I32, I32]),
+    "rs_ham_timing": (None, [P, I32]),
+    "rs_ham_timing_read": (None, [P, P, P, P]),
+    "rs_ham_launch_bytes": (None, [P, I32, I32, P, P]),
+    "rs_overlap_block": (None, [P, P, I64, I32, P, I64, I32, P, I64, I32, P]),
+    "rs_linalg_workspace_bytes": (I64, [I32]),
+    "rs_orthonormalize": (None, [P, P, I64, I32, I32, P, P, P]),
+    "rs_subspace_diag": (None, [P, P, P, I64, I32, I32, I32, P, P, P, P]),
+    "rs_solver_create": (None, [P, ctypes.POINTER(SolverCfg), P, P, PP]),
+    "rs_eigensolver_step": (None, [P, P, P, P, P]),
+    "rs_solver_psi": (None, [P, PP]),
+    "rs_solver_set_precond_weights": (None, [P, P, P, P]),
+    "rs_solver_destroy": (None, [P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def exported_names() -> list[str]:
+    return list(SIGNATURES)
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1306_2953_gb300.build` "
+                                   "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.restype = I32 if res is None else res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().rs_last_error(buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
+def call(name: str, *args) -> int:
+    """Calls an int-status entry point and raises RsError on failure."""
+    rc = getattr(lib(), name)(*args)
+    if SIGNATURES[name][0] is None and rc != RS_OK:
+        raise RsError(rc, f"{name}: {last_error()}")
+    return rc

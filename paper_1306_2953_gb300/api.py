@@ -1,0 +1,185 @@
+"""Thin torch-facing wrappers over the C ABI (argument marshalling only).
+
+Host arrays are numpy; device arrays are torch CUDA tensors whose
+``data_ptr()`` is passed straight to the library together with the current
+torch stream.  Nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import RS_F32, RS_F64, call
+
+_c = ctypes.c_void_p
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return RS_F64
+    if t.dtype == torch.float32:
+        return RS_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+class Grid:
+    """Union-of-spheres or box grid (host tables; rs_grid_*)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @classmethod
+    def spheres(cls, xyz, radius: float, h: float) -> "Grid":
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        out = ctypes.c_void_p()
+        call("rs_grid_create_spheres", _ptr(xyz), len(xyz), float(radius), float(h), ctypes.byref(out))
+        return cls(out)
+
+    @classmethod
+    def box(cls, n0: int, n1: int, n2: int, h: float) -> "Grid":
+        out = ctypes.c_void_p()
+        call("rs_grid_create_box", n0, n1, n2, float(h), ctypes.byref(out))
+        return cls(out)
+
+    def info(self):
+        npts = ctypes.c_int64()
+        origin = (ctypes.c_int32 * 3)()
+        dims = (ctypes.c_int32 * 3)()
+        h = ctypes.c_double()
+        call("rs_grid_info", self._h, ctypes.byref(npts), origin, dims, ctypes.byref(h))
+        return npts.value, tuple(origin), tuple(dims), h.value
+
+    @property
+    def npts(self) -> int:
+        return self.info()[0]
+
+    @property
+    def h(self) -> float:
+        return self.info()[3]
+
+    @property
+    def dV(self) -> float:
+        return self.h ** 3
+
+    def ijk(self) -> np.ndarray:
+        out = np.empty((self.npts, 3), dtype=np.int32)
+        call("rs_grid_ijk", self._h, _ptr(out))
+        return out
+
+    def coords(self) -> np.ndarray:
+        out = np.empty((self.npts, 3), dtype=np.float64)
+        call("rs_grid_coords", self._h, _ptr(out))
+        return out
+
+    def point_map(self) -> np.ndarray:
+        _, _, dims, _ = self.info()
+        out = np.empty(dims, dtype=np.int32)
+        call("rs_grid_point_map", self._h, _ptr(out))
+        return out
+
+    def close(self):
+        if self._h:
+            _lib.lib().rs_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Projectors:
+    """Kleinman-Bylander projector tables (rs_proj_*)."""
+
+    def __init__(self, grid: Grid, xyz, E, r_c: float = 1.0, r_cut: float = 3.0):
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._E = np.ascontiguousarray(E, dtype=np.float64)
+        spec = _lib.ProjectorSpec(len(self._xyz), _ptr(self._xyz), _ptr(self._E), float(r_c), float(r_cut))
+        out = ctypes.c_void_p()
+        call("rs_proj_create", grid._h, ctypes.byref(spec), ctypes.byref(out))
+        self._h = out
+        self.grid = grid
+
+    def tables(self):
+        na = ctypes.c_int32()
+        ne = ctypes.c_int64()
+        call("rs_proj_info", self._h, ctypes.byref(na), ctypes.byref(ne))
+        off = np.empty(na.value + 1, dtype=np.int64)
+        idx = np.empty(ne.value, dtype=np.int32)
+        gam = np.empty((ne.value, 4), dtype=np.float64)
+        call("rs_proj_tables", self._h, _ptr(off), _ptr(idx), _ptr(gam))
+        return off, idx, gam
+
+    def close(self):
+        if self._h:
+            _lib.lib().rs_proj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian:
+    """H = -1/2 Lap + V + V_nl on the current CUDA device (rs_ham_*)."""
+
+    def __init__(self, grid: Grid, V, proj: Projectors | None = None, order: int = 4):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        out = ctypes.c_void_p()
+        call("rs_ham_create", grid._h, _ptr(V), proj._h if proj is not None else None, order, ctypes.byref(out))
+        self._h = out
+        self.grid = grid
+        self.proj = proj
+        self.npts = grid.npts
+
+    def apply(self, psi, hpsi=None, nb: int | None = None, stream=None):
+        """hpsi[:, :nb] = H psi[:, :nb] for device tensors [npts, ld]."""
+        import torch
+        if hpsi is None:
+            hpsi = torch.empty_like(psi)
+        nb = psi.shape[1] if nb is None else nb
+        assert psi.stride(1) == 1 and hpsi.stride(1) == 1
+        call("rs_ham_apply_block", self._h, _c(psi.data_ptr()), psi.stride(0), _c(hpsi.data_ptr()), hpsi.stride(0),
+             nb, dtype_code(psi), _stream(stream))
+        return hpsi
+
+    def apply_all(self, psi, hpsi=None, nb: int = 32, stream=None):
+        """H applied to every state of psi [npts, nst], nb states per call."""
+        import torch
+        if hpsi is None:
+            hpsi = torch.empty_like(psi)
+        nst = psi.shape[1]
+        for b in range(0, nst, nb):
+            self.apply(psi[:, b:b + nb], hpsi[:, b:b + nb], nb=min(nb, nst - b), stream=stream)
+        return hpsi
+
+    def apply_bytes(self, nb: int, dtype: int) -> int:
+        return int(_lib.lib().rs_ham_apply_bytes(self._h, nb, dtype))
+
+    def close(self):
+        if self._h:
+            _lib.lib().rs_ham_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,625 @@
+// Kohn-Sham Hamiltonian applied to a block of orbitals (Sec. V, Eq. 3).
+//
+// Two launches per block:
+//  1. k_project: the Kleinman-Bylander projection integrals of Eq. (4),
+//     c[A,q,s] = E[A,q] dV sum_{p in S_A} gamma_Aq(p) psi(p,s), one CTA per
+//     (atom, state group), a block-wide tree reduction over sphere points.
+//  2. k_stencil: the 25-point star kinetic stencil (Sec. V.A), the local
+//     potential (Sec. V.B) and the nonlocal sum of Eq. (4), fused.  Each CTA
+//     owns a TX x TY column of lattice points (axes 2 and 1 of the point
+//     map) and one group of SG states, and marches along axis 0.  Every
+//     thread keeps a 2x2 patch of columns for one state in registers with a
+//     9-deep queue along the march axis, so the axis-0 neighbours come from
+//     registers; the current plane (interior written from the queues, the
+//     4-point x/y halos staged by cp.async three planes deep) sits in shared
+//     memory for the axis-1/axis-2 neighbours.  The nonlocal term is a
+//     gather: each output point sums over the atoms whose spheres cover it,
+//     so overlapping spheres need neither atom colouring (Sec. V.C, Fig. 10)
+//     nor atomics, and the output is written exactly once.
+// Orbitals are [npts][ld] with the state index fastest (Sec. IV, Fig. 4b);
+// grid points are addressed through the int32 point map (Sec. V.A).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "device.h"
+
+#ifndef RS_STENCIL_MINB_F32
+#define RS_STENCIL_MINB_F32 2
+#endif
+
+namespace rs {
+
+// Planes beyond the queue's next entry whose rows are prefetched into L2.
+constexpr int PF_DIST = 4;
+
+template <typename T> struct HamDev {
+    const int32_t *map;
+    int d0, d1, d2;
+    const T *V;
+    const int32_t *cov_off, *cov_atom;
+    const T *cov_gam;   // [entries][4]
+    const int32_t *sph_off, *sph_idx;
+    const T *sph_gam;   // [entries][4]
+    const T *E;         // [atoms][4]
+    T dV;
+    T w[5];             // w[0] = 3 kin c_0, w[j] = kin c_j, kin = -1/(2h^2)
+};
+
+// ---------------------------------------------------------------- helpers --
+
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int sz = valid ? BYTES : 0;
+    if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES), "r"(sz)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename T> struct Four { T a, b, c, d; };
+__device__ __forceinline__ Four<float> load4(const float *p) {
+    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Four<double> load4(const double *p) {
+    double2 u = __ldg(reinterpret_cast<const double2 *>(p));
+    double2 v = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {u.x, u.y, v.x, v.y};
+}
+
+// ------------------------------------------------- projection integrals ---
+
+template <typename T, int SGP, int NT>
+__global__ void __launch_bounds__(NT) k_project(HamDev<T> d, const T *__restrict__ psi, int64_t ldp, int nb,
+                                                T *__restrict__ cproj) {
+    constexpr int R = NT / SGP;
+    __shared__ T red[4][NT];
+    const int A = blockIdx.x;
+    const int sg0 = blockIdx.y * SGP;
+    const int s = threadIdx.x % SGP, r = threadIdx.x / SGP;
+    const int o = __ldg(d.sph_off + A), e = __ldg(d.sph_off + A + 1);
+    const T *ps = psi + sg0 + s;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 4
+    for (int i = o + r; i < e; i += R) {
+        const int p = __ldg(d.sph_idx + i);
+        const T v = __ldg(ps + (int64_t)p * ldp);
+        const Four<T> g = load4(d.sph_gam + 4 * (int64_t)i);
+        a0 += g.a * v;
+        a1 += g.b * v;
+        a2 += g.c * v;
+        a3 += g.d * v;
+    }
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
+    red[3][threadIdx.x] = a3;
+    __syncthreads();
+    for (int st = R / 2; st > 0; st >>= 1) {
+        if (r < st) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st * SGP];
+        }
+        __syncthreads();
+    }
+    if (r == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            cproj[((int64_t)A * 4 + q) * nb + sg0 + s] = __ldg(d.E + 4 * A + q) * d.dV * red[q][s];
+    }
+}
+
+// ------------------------------------------- fused stencil + V + nonlocal ---
+
+template <typename T, int SG, int TX, int TY> struct StencilCfg {
+    static constexpr int W2 = TX + 8, W1 = TY + 8;
+    static constexpr int PLANE = W1 * W2 * SG;
+    static constexpr int NT = (TX / 2) * (TY / 2) * SG;
+    static constexpr int RING = 3;
+    static constexpr int CHB = (SG * (int)sizeof(T) >= 16) ? 16 : SG * (int)sizeof(T);
+    static constexpr int CHE = CHB / (int)sizeof(T);
+    static constexpr int CPR = SG / CHE;
+    static constexpr int NH = 8 * TY + 8 * TX;
+    static constexpr size_t SMEM = (size_t)RING * PLANE * sizeof(T);
+    static constexpr int MINB = sizeof(T) == 4 ? RS_STENCIL_MINB_F32 : 1;
+};
+
+template <typename T, int SG, int TX, int TY>
+__global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, SG, TX, TY>::MINB)
+    k_stencil(HamDev<T> d, const T *__restrict__ psi, int64_t ldp, T *__restrict__ hpsi, int64_t ldh,
+              const T *__restrict__ cproj, int nb, const int4 *__restrict__ work) {
+    using C = StencilCfg<T, SG, TX, TY>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+
+    const int tid = threadIdx.x;
+    const int s = tid % SG;
+    const int patch = tid / SG;
+    const int lx = 2 * (patch % (TX / 2));
+    const int ly = 2 * (patch / (TX / 2));
+    const int4 wk = work[blockIdx.x];
+    const int b1 = wk.x * TY, b2 = wk.y * TX;
+    const int za = wk.z, zb = wk.w;
+    const int sg0 = blockIdx.y * SG;
+    const T *psig = psi + sg0;
+
+    auto map_at = [&](int a0, int a1, int a2) -> int {
+        if ((unsigned)a0 >= (unsigned)d.d0 || (unsigned)a1 >= (unsigned)d.d1 || (unsigned)a2 >= (unsigned)d.d2)
+            return -1;
+        return __ldg(d.map + ((int64_t)a0 * d.d1 + a1) * d.d2 + a2);
+    };
+    auto load_val = [&](int r) -> T { return r >= 0 ? __ldg(psig + (int64_t)r * ldp + s) : T(0); };
+    auto issue_halo = [&](int z, int slot) {
+        T *base = sm + slot * C::PLANE;
+        for (int i = tid; i < C::NH * C::CPR; i += C::NT) {
+            const int hh = i / C::CPR, c = i % C::CPR;
+            int hy, hx;
+            if (hh < 8 * TY) {
+                hy = hh >> 3;
+                const int t = hh & 7;
+                hx = t < 4 ? t - 4 : TX + t - 4;
+            } else {
+                const int h2 = hh - 8 * TY;
+                hx = h2 % TX;
+                const int t = h2 / TX;
+                hy = t < 4 ? t - 4 : TY + t - 4;
+            }
+            const int r = map_at(z, b1 + hy, b2 + hx);
+            T *dst = base + ((hy + 4) * C::W2 + (hx + 4)) * SG + c * C::CHE;
+            const T *src = r >= 0 ? psig + (int64_t)r * ldp + c * C::CHE : psig;
+            cp_async<C::CHB>(dst, src, r >= 0);
+        }
+    };
+
+    T q[2][2][9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) q[dy][dx][k] = load_val(map_at(za - 4 + k, b1 + ly + dy, b2 + lx + dx));
+
+    issue_halo(za, 0);
+    cp_async_commit();
+    if (za + 1 < zb) issue_halo(za + 1, 1);
+    cp_async_commit();
+
+    const T w0 = d.w[0], w1 = d.w[1], w2 = d.w[2], w3 = d.w[3], w4 = d.w[4];
+    int slot = 0;
+    for (int z = za; z < zb; ++z) {
+        const int pslot = slot == 0 ? 2 : slot - 1;  // (slot + 2) % 3
+        if (z + 2 < zb) issue_halo(z + 2, pslot);
+        cp_async_commit();
+
+        T nq[2][2];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) nq[dy][dx] = load_val(map_at(z + 5, b1 + ly + dy, b2 + lx + dx));
+        if (s == 0) {
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int r = map_at(z + 5 + PF_DIST, b1 + ly + dy, b2 + lx + dx);
+                    if (r >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(psig + (int64_t)r * ldp));
+                }
+        }
+
+        T *P = sm + slot * C::PLANE;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) P[((ly + dy + 4) * C::W2 + lx + dx + 4) * SG + s] = q[dy][dx][4];
+        cp_async_wait<2>();
+        __syncthreads();
+
+        // axis-0 neighbours from the register queues
+        T acc[2][2];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                acc[dy][dx] = w0 * q[dy][dx][4] + w1 * (q[dy][dx][5] + q[dy][dx][3]) +
+                              w2 * (q[dy][dx][6] + q[dy][dx][2]) + w3 * (q[dy][dx][7] + q[dy][dx][1]) +
+                              w4 * (q[dy][dx][8] + q[dy][dx][0]);
+            }
+        // axis-2 neighbours: one row of 10 values per patch row (8 from shared memory)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            T v[10];
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+                if (k != 4 && k != 5) v[k] = P[((ly + dy + 4) * C::W2 + lx + k) * SG + s];
+            v[4] = q[dy][0][4];
+            v[5] = q[dy][1][4];
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx)
+                acc[dy][dx] += w1 * (v[5 + dx] + v[3 + dx]) + w2 * (v[6 + dx] + v[2 + dx]) +
+                               w3 * (v[7 + dx] + v[1 + dx]) + w4 * (v[8 + dx] + v[0 + dx]);
+        }
+        // axis-1 neighbours: one column of 10 values per patch column
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            T v[10];
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+                if (k != 4 && k != 5) v[k] = P[((ly + k) * C::W2 + lx + dx + 4) * SG + s];
+            v[4] = q[0][dx][4];
+            v[5] = q[1][dx][4];
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+                acc[dy][dx] += w1 * (v[5 + dy] + v[3 + dy]) + w2 * (v[6 + dy] + v[2 + dy]) +
+                               w3 * (v[7 + dy] + v[1 + dy]) + w4 * (v[8 + dy] + v[0 + dy]);
+        }
+        // local potential, nonlocal gather, store
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int r = map_at(z, b1 + ly + dy, b2 + lx + dx);
+                if (r < 0) continue;
+                T out = acc[dy][dx] + __ldg(d.V + r) * q[dy][dx][4];
+                const int e0 = __ldg(d.cov_off + r), e1 = __ldg(d.cov_off + r + 1);
+                for (int e = e0; e < e1; ++e) {
+                    const int A = __ldg(d.cov_atom + e);
+                    const Four<T> g = load4(d.cov_gam + 4 * (int64_t)e);
+                    const T *cp = cproj + (int64_t)A * 4 * nb + sg0 + s;
+                    out += g.a * __ldg(cp) + g.b * __ldg(cp + nb) + g.c * __ldg(cp + 2 * nb) + g.d * __ldg(cp + 3 * nb);
+                }
+                hpsi[(int64_t)r * ldh + sg0 + s] = out;
+            }
+
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) q[dy][dx][k] = q[dy][dx][k + 1];
+                q[dy][dx][8] = nq[dy][dx];
+            }
+        slot = slot == 2 ? 0 : slot + 1;
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+// ------------------------------------------------------------ host side ---
+
+namespace {
+
+struct WorkList {
+    DevBuf buf;
+    int count = 0;
+};
+
+// Tile shapes (TX along map axis 2, TY along map axis 1) per state-group size.
+struct Shape {
+    int sg, tx, ty;
+};
+const Shape kShapes[] = {{32, 8, 8}, {16, 16, 8}, {8, 16, 16}, {4, 32, 16}, {2, 32, 32}, {1, 64, 32}};
+const int kZChunk = 32;
+
+}  // namespace
+
+struct rs_ham {
+    int64_t npts = 0;
+    int32_t d[3] = {0, 0, 0};
+    double h = 0, dV = 0;
+    int order = 4;
+    int n_atoms = 0;
+    int64_t n_entries = 0;
+    int device = 0;
+    double w[5] = {0, 0, 0, 0, 0};
+    DevBuf map, V64, V32, cov_off, cov_atom, cov_gam64, cov_gam32, sph_off, sph_idx, sph_gam64, sph_gam32, E64, E32,
+        cproj, dummy;
+    std::map<std::pair<int, int>, WorkList *> work;
+    // optional per-launch timing (rs_ham_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;   // 3 per recorded call
+    size_t n_recorded = 0;
+    ~rs_ham() {
+        for (auto &kv : work) delete kv.second;
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+    }
+    // events for the next recorded call (nullptr when timing is off)
+    cudaEvent_t *next_events() {
+        if (!timing) return nullptr;
+        if (events.size() < 3 * (n_recorded + 1)) {
+            for (int i = 0; i < 3; ++i) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+                events.push_back(e);
+            }
+        }
+        return &events[3 * n_recorded++];
+    }
+    template <typename T> HamDev<T> view() const;
+};
+
+template <> HamDev<double> rs_ham::view<double>() const {
+    HamDev<double> v;
+    v.map = map.as<int32_t>();
+    v.d0 = d[0], v.d1 = d[1], v.d2 = d[2];
+    v.V = V64.as<double>();
+    v.cov_off = cov_off.as<int32_t>();
+    v.cov_atom = cov_atom.as<int32_t>();
+    v.cov_gam = cov_gam64.as<double>();
+    v.sph_off = sph_off.as<int32_t>();
+    v.sph_idx = sph_idx.as<int32_t>();
+    v.sph_gam = sph_gam64.as<double>();
+    v.E = E64.as<double>();
+    v.dV = dV;
+    for (int j = 0; j < 5; ++j) v.w[j] = w[j];
+    return v;
+}
+template <> HamDev<float> rs_ham::view<float>() const {
+    HamDev<float> v;
+    v.map = map.as<int32_t>();
+    v.d0 = d[0], v.d1 = d[1], v.d2 = d[2];
+    v.V = V32.as<float>();
+    v.cov_off = cov_off.as<int32_t>();
+    v.cov_atom = cov_atom.as<int32_t>();
+    v.cov_gam = cov_gam32.as<float>();
+    v.sph_off = sph_off.as<int32_t>();
+    v.sph_idx = sph_idx.as<int32_t>();
+    v.sph_gam = sph_gam32.as<float>();
+    v.E = E32.as<float>();
+    v.dV = (float)dV;
+    for (int j = 0; j < 5; ++j) v.w[j] = (float)w[j];
+    return v;
+}
+
+// Central second-derivative weights of half-width m (closed form):
+// c_j = 2 (-1)^(j+1) (m!)^2 / (j^2 (m-j)! (m+j)!), c_0 = -2 sum_{j>=1} c_j.
+static void fd_weights(int m, double c[5]) {
+    auto fact = [](int n) {
+        double f = 1;
+        for (int i = 2; i <= n; ++i) f *= i;
+        return f;
+    };
+    for (int j = 0; j < 5; ++j) c[j] = 0;
+    double sum = 0;
+    for (int j = 1; j <= m; ++j) {
+        c[j] = 2.0 * ((j & 1) ? 1.0 : -1.0) * fact(m) * fact(m) / ((double)j * j * fact(m - j) * fact(m + j));
+        sum += c[j];
+    }
+    c[0] = -2.0 * sum;
+}
+
+static int build_work(rs_ham *H, const rs_grid *g, int tx, int ty) {
+    const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+    const int n1 = (d1 + ty - 1) / ty, n2 = (d2 + tx - 1) / tx;
+    std::vector<int> zmin((size_t)n1 * n2, d0), zmax((size_t)n1 * n2, -1);
+    for (int a = 0; a < d0; ++a)
+        for (int b = 0; b < d1; ++b)
+            for (int c = 0; c < d2; ++c)
+                if (g->map[((size_t)a * d1 + b) * d2 + c] >= 0) {
+                    const size_t t = (size_t)(b / ty) * n2 + (c / tx);
+                    zmin[t] = std::min(zmin[t], a);
+                    zmax[t] = std::max(zmax[t], a);
+                }
+    std::vector<int4> items;
+    for (int t1 = 0; t1 < n1; ++t1)
+        for (int t2 = 0; t2 < n2; ++t2) {
+            const size_t t = (size_t)t1 * n2 + t2;
+            if (zmax[t] < 0) continue;
+            for (int z = zmin[t]; z <= zmax[t]; z += kZChunk) items.push_back(make_int4(t1, t2, z, std::min(z + kZChunk, zmax[t] + 1)));
+        }
+    // raster order over (tile row, tile column, z chunk): CTAs resident at the
+    // same time are spatial neighbours, so halo rows are re-read from L2
+    WorkList *wl = new (std::nothrow) WorkList;
+    if (!wl) return fail(RS_ENOMEM, "host allocation failed");
+    H->work[{tx, ty}] = wl;
+    wl->count = (int)items.size();
+    return wl->buf.upload(items.data(), items.size() * sizeof(int4));
+}
+
+extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_proj *pr, int order, rs_ham **out) {
+    if (!g || !V_host || !out) return fail(RS_EINVAL, "rs_ham_create: null argument");
+    if (order < 1 || order > 4) return fail(RS_EINVAL, "rs_ham_create: order must be in 1..4");
+    *out = nullptr;
+    int dev = 0;
+    RS_CUDA(cudaGetDevice(&dev));
+    rs_ham *H = new (std::nothrow) rs_ham;
+    if (!H) return fail(RS_ENOMEM, "host allocation failed");
+    auto bail = [&](int rc) {
+        delete H;
+        return rc;
+    };
+    H->device = dev;
+    H->npts = g->npts;
+    for (int i = 0; i < 3; ++i) H->d[i] = g->dims[i];
+    H->h = g->h;
+    H->dV = g->h * g->h * g->h;
+    H->order = order;
+    double c[5];
+    fd_weights(order, c);
+    const double kin = -0.5 / (g->h * g->h);
+    H->w[0] = 3.0 * kin * c[0];
+    for (int j = 1; j < 5; ++j) H->w[j] = kin * c[j];
+
+    int rc;
+    const int64_t np = g->npts;
+    if ((rc = H->map.upload(g->map.data(), g->map.size() * sizeof(int32_t)))) return bail(rc);
+    std::vector<float> v32((size_t)np);
+    for (int64_t p = 0; p < np; ++p) v32[p] = (float)V_host[p];
+    if ((rc = H->V64.upload(V_host, (size_t)np * sizeof(double)))) return bail(rc);
+    if ((rc = H->V32.upload(v32.data(), (size_t)np * sizeof(float)))) return bail(rc);
+
+    // projector tables: atom-major (projection) and point-major (gather)
+    const int na = pr ? pr->n_atoms : 0;
+    const int64_t ne = pr ? (int64_t)pr->idx.size() : 0;
+    if (ne > (int64_t)INT32_MAX) return bail(fail(RS_EINVAL, "too many projector entries"));
+    H->n_atoms = na;
+    H->n_entries = ne;
+    std::vector<int32_t> soff((size_t)na + 1, 0), coff((size_t)np + 1, 0), catom((size_t)std::max<int64_t>(ne, 1));
+    std::vector<double> cg64((size_t)std::max<int64_t>(ne, 1) * 4), sg64((size_t)std::max<int64_t>(ne, 1) * 4),
+        E64((size_t)std::max(na, 1) * 4);
+    for (int A = 0; A < na; ++A) soff[A + 1] = (int32_t)pr->off[A + 1];
+    for (int64_t e = 0; e < ne; ++e) coff[(size_t)pr->idx[e] + 1]++;
+    for (int64_t p = 0; p < np; ++p) coff[p + 1] += coff[p];
+    {
+        std::vector<int32_t> fill(coff.begin(), coff.end() - 1);
+        for (int A = 0; A < na; ++A)
+            for (int64_t e = pr->off[A]; e < pr->off[A + 1]; ++e) {
+                const int32_t slot = fill[pr->idx[e]]++;
+                catom[slot] = A;
+                for (int q = 0; q < 4; ++q) cg64[(size_t)slot * 4 + q] = pr->gam[e * 4 + q];
+            }
+    }
+    for (int64_t e = 0; e < ne * 4; ++e) sg64[e] = pr->gam[e];
+    for (int A = 0; A < na * 4; ++A) E64[A] = pr->E[A];
+    std::vector<float> cg32(cg64.begin(), cg64.end()), sg32(sg64.begin(), sg64.end()), E32(E64.begin(), E64.end());
+    std::vector<int32_t> sidx(pr && ne ? pr->idx : std::vector<int32_t>(1, 0));
+    if ((rc = H->sph_off.upload(soff.data(), soff.size() * 4)) || (rc = H->sph_idx.upload(sidx.data(), sidx.size() * 4)) ||
+        (rc = H->sph_gam64.upload(sg64.data(), sg64.size() * 8)) ||
+        (rc = H->sph_gam32.upload(sg32.data(), sg32.size() * 4)) || (rc = H->E64.upload(E64.data(), E64.size() * 8)) ||
+        (rc = H->E32.upload(E32.data(), E32.size() * 4)) || (rc = H->cov_off.upload(coff.data(), coff.size() * 4)) ||
+        (rc = H->cov_atom.upload(catom.data(), catom.size() * 4)) ||
+        (rc = H->cov_gam64.upload(cg64.data(), cg64.size() * 8)) ||
+        (rc = H->cov_gam32.upload(cg32.data(), cg32.size() * 4)))
+        return bail(rc);
+    if ((rc = H->cproj.alloc((size_t)std::max(na, 1) * 4 * 64 * sizeof(double)))) return bail(rc);
+    for (const Shape &s : kShapes)
+        if ((rc = build_work(H, g, s.tx, s.ty))) return bail(rc);
+    *out = H;
+    return RS_OK;
+}
+
+extern "C" int rs_ham_destroy(rs_ham *h) {
+    delete h;
+    return RS_OK;
+}
+
+template <typename T, int SG, int TX, int TY>
+static int launch_stencil(rs_ham *H, const HamDev<T> &d, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, int nb,
+                          cudaStream_t st) {
+    using C = StencilCfg<T, SG, TX, TY>;
+    static bool attr_done = false;  // per instantiation; set once per process
+    if (!attr_done) {
+        RS_CUDA(cudaFuncSetAttribute(k_stencil<T, SG, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_done = true;
+    }
+    const WorkList *wl = H->work.at({TX, TY});
+    if (wl->count == 0) return RS_OK;
+    dim3 grid((unsigned)wl->count, (unsigned)(nb / SG));
+    k_stencil<T, SG, TX, TY><<<grid, C::NT, C::SMEM, st>>>(d, psi, ldp, hpsi, ldh, H->cproj.as<T>(), nb,
+                                                            wl->buf.as<int4>());
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+template <typename T>
+static int apply_t(rs_ham *H, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, int nb, cudaStream_t st) {
+    const HamDev<T> d = H->view<T>();
+    cudaEvent_t *ev = H->next_events();
+    if (ev) RS_CUDA(cudaEventRecord(ev[0], st));
+    if (H->n_atoms > 0) {
+        const int sgp = std::min(nb, 32);
+        dim3 grid((unsigned)H->n_atoms, (unsigned)(nb / sgp));
+        T *cp = H->cproj.as<T>();
+        switch (sgp) {
+            case 1: k_project<T, 1, 1024><<<grid, 1024, 0, st>>>(d, psi, ldp, nb, cp); break;
+            case 2: k_project<T, 2, 1024><<<grid, 1024, 0, st>>>(d, psi, ldp, nb, cp); break;
+            case 4: k_project<T, 4, 1024><<<grid, 1024, 0, st>>>(d, psi, ldp, nb, cp); break;
+            case 8: k_project<T, 8, 1024><<<grid, 1024, 0, st>>>(d, psi, ldp, nb, cp); break;
+            case 16: k_project<T, 16, 1024><<<grid, 1024, 0, st>>>(d, psi, ldp, nb, cp); break;
+            default: k_project<T, 32, 1024><<<grid, 1024, 0, st>>>(d, psi, ldp, nb, cp); break;
+        }
+        RS_LAUNCH_CHECK();
+    }
+    if (ev) RS_CUDA(cudaEventRecord(ev[1], st));
+    constexpr int SGMAX = 128 / (int)sizeof(T);
+    const int sg = std::min(nb, SGMAX);
+    int rc;
+    switch (sg) {
+        case 1: rc = launch_stencil<T, 1, 64, 32>(H, d, psi, ldp, hpsi, ldh, nb, st); break;
+        case 2: rc = launch_stencil<T, 2, 32, 32>(H, d, psi, ldp, hpsi, ldh, nb, st); break;
+        case 4: rc = launch_stencil<T, 4, 32, 16>(H, d, psi, ldp, hpsi, ldh, nb, st); break;
+        case 8: rc = launch_stencil<T, 8, 16, 16>(H, d, psi, ldp, hpsi, ldh, nb, st); break;
+        case 16: rc = launch_stencil<T, 16, 16, 8>(H, d, psi, ldp, hpsi, ldh, nb, st); break;
+        default:
+            if constexpr (SGMAX >= 32) {
+                rc = launch_stencil<T, 32, 8, 8>(H, d, psi, ldp, hpsi, ldh, nb, st);
+                break;
+            }
+            return fail(RS_EINVAL, "unsupported state group");
+    }
+    if (rc == RS_OK && ev) RS_CUDA(cudaEventRecord(ev[2], st));
+    return rc;
+}
+
+extern "C" int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi, void *hpsi_dev, int64_t ld_hpsi,
+                                  int nb, int dtype, void *stream) {
+    if (!h || !psi_dev || !hpsi_dev) return fail(RS_EINVAL, "rs_ham_apply_block: null argument");
+    if (nb < 1 || nb > 64 || (nb & (nb - 1))) return fail(RS_EINVAL, "rs_ham_apply_block: nb must be a power of two <= 64");
+    if (ld_psi < nb || ld_hpsi < nb) return fail(RS_EINVAL, "rs_ham_apply_block: ld < nb");
+    if (dtype != RS_F64 && dtype != RS_F32) return fail(RS_EINVAL, "rs_ham_apply_block: bad dtype");
+    const int es = dtype == RS_F64 ? 8 : 4;
+    const int sgbytes = std::min(nb, 128 / es) * es;
+    const int need = std::min(sgbytes, 16);
+    if (((uintptr_t)psi_dev % need) || ((uintptr_t)hpsi_dev % need) || ((ld_psi * es) % need) || ((ld_hpsi * es) % need))
+        return fail(RS_EINVAL, "rs_ham_apply_block: misaligned pointer or leading dimension");
+    const char *a = (const char *)psi_dev, *b = (const char *)hpsi_dev;
+    const int64_t span_a = ((h->npts - 1) * ld_psi + nb) * es, span_b = ((h->npts - 1) * ld_hpsi + nb) * es;
+    if (a < b + span_b && b < a + span_a) return fail(RS_EINVAL, "rs_ham_apply_block: psi and hpsi overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == RS_F64)
+        return apply_t<double>(h, (const double *)psi_dev, ld_psi, (double *)hpsi_dev, ld_hpsi, nb, st);
+    return apply_t<float>(h, (const float *)psi_dev, ld_psi, (float *)hpsi_dev, ld_hpsi, nb, st);
+}
+
+extern "C" int64_t rs_ham_apply_bytes(const rs_ham *h, int nb, int dtype) {
+    int64_t a = 0, b = 0;
+    if (rs_ham_launch_bytes(h, nb, dtype, &a, &b) != RS_OK) return -1;
+    return a + b;
+}
+
+extern "C" int rs_ham_launch_bytes(const rs_ham *h, int nb, int dtype, int64_t *project_bytes, int64_t *stencil_bytes) {
+    if (!h) return fail(RS_EINVAL, "rs_ham_launch_bytes: null handle");
+    const int64_t s = dtype == RS_F64 ? 8 : 4;
+    const int64_t np = h->npts, ne = h->n_entries, nc = (int64_t)h->n_atoms * 4 * nb * s;
+    if (project_bytes) *project_bytes = ne * (4 + 4 * s) + (h->n_atoms + 1) * 4 + nc;
+    if (stencil_bytes) *stencil_bytes = np * nb * 2 * s + np * s + np * 4 + ne * (4 + 4 * s) + (np + 1) * 4 + nc;
+    return RS_OK;
+}
+
+extern "C" int rs_ham_timing(rs_ham *h, int enable) {
+    if (!h) return fail(RS_EINVAL, "rs_ham_timing: null handle");
+    if (enable) h->n_recorded = 0;
+    h->timing = enable != 0;
+    return RS_OK;
+}
+
+extern "C" int rs_ham_timing_read(rs_ham *h, double *project_ms, double *stencil_ms, int64_t *calls) {
+    if (!h) return fail(RS_EINVAL, "rs_ham_timing_read: null handle");
+    double pm = 0, sm = 0;
+    for (size_t i = 0; i < h->n_recorded; ++i) {
+        cudaEvent_t *e = &h->events[3 * i];
+        RS_CUDA(cudaEventSynchronize(e[2]));
+        float a = 0, b = 0;
+        RS_CUDA(cudaEventElapsedTime(&a, e[0], e[1]));
+        RS_CUDA(cudaEventElapsedTime(&b, e[1], e[2]));
+        pm += a;
+        sm += b;
+    }
+    if (project_ms) *project_ms = pm;
+    if (stencil_ms) *stencil_ms = sm;
+    if (calls) *calls = (int64_t)h->n_recorded;
+    return RS_OK;
+}

@@ -1,0 +1,541 @@
+// Dense linear algebra of Sec. VI on the device: overlaps (Eq. 5), Cholesky
+// orthogonalisation (Eq. 6) and subspace diagonalisation (Eqs. 7-8).
+//
+// Tall-skinny contractions over grid points:
+//   k_gram    S = dV X^T Y, split over blocks of points ("blocks of points",
+//             Sec. VI) and accumulated in FP64.  FP64 data: FP64 FMA.  FP32
+//             data: every product is formed exactly as a float pair (fma
+//             error term) and accumulated as a compensated float pair, so
+//             the FP64 result is accurate to ~2^-44 relative while running
+//             on the FP32 pipes (FP64 throughput on this part is 1/64 of
+//             FP32).
+//   k_rowmul  Y = alpha X C + beta Y applied row by row (each CTA owns whole
+//             rows), so the in-place update Psi <- Psi C needs no copy.
+// Small dense kernels (n <= a few hundred, FP64 unless stated):
+//   k_chol    S = U^T U, right-looking, one CTA, status on failure
+//   k_trinv   U^-1 by back substitution, one thread per column
+//   k_gemm_nn small C = alpha op(A) op(B) + beta C, tiled over many CTAs
+//   k_jacobi  cyclic Jacobi with the parallel (round-robin) ordering, one
+//             CTA, FP32 or FP64
+//   RefSyEv   FP64 refinement of FP32 eigenvectors by the iterative
+//             refinement of Ogita & Aishima (2018)
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device.h"
+#include "linalg.h"
+
+namespace rs {
+
+// ------------------------------------------------------------- k_gram ---
+
+constexpr int G_TM = 64, G_TN = 64, G_TK = 16, G_NT = 256;
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+// FP64 data: plain FP64 accumulation.  FP32 data: compensated float pairs.
+template <typename T> struct GramAcc;
+template <> struct GramAcc<double> {
+    double v = 0;
+    __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct GramAcc<float> {
+    float hi = 0, lo = 0;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float pe = fmaf(a, b, -p);   // exact: a*b = p + pe
+        float s, e;
+        two_sum(hi, p, s, e);
+        hi = s;
+        lo += e + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// S[i][j] += dV * sum_{p in chunk} X[p][i] Y[p][j]; grid (ceil(nx/64), ceil(ny/64), splits)
+template <typename T>
+__global__ void __launch_bounds__(G_NT) k_gram(const T *__restrict__ X, int64_t ldx, int nx, const T *__restrict__ Y,
+                                               int64_t ldy, int ny, int64_t npts, int64_t chunk, double dV,
+                                               double *__restrict__ S, int64_t lds) {
+    __shared__ T xs[G_TK][G_TM + 1];
+    __shared__ T ys[G_TK][G_TN + 1];
+    const int i0 = blockIdx.x * G_TM, j0 = blockIdx.y * G_TN;
+    const int64_t p0 = (int64_t)blockIdx.z * chunk;
+    const int64_t p1 = min(npts, p0 + chunk);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 4x4 micro tile at (4ty.., 4tx..)
+    GramAcc<T> acc[4][4];
+    for (int64_t pk = p0; pk < p1; pk += G_TK) {
+        for (int e = threadIdx.x; e < G_TK * G_TM; e += G_NT) {
+            const int k = e / G_TM, c = e % G_TM;
+            const int64_t p = pk + k;
+            xs[k][c] = (p < p1 && i0 + c < nx) ? X[p * ldx + i0 + c] : T(0);
+            ys[k][c] = (p < p1 && j0 + c < ny) ? Y[p * ldy + j0 + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < G_TK; ++k) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = xs[k][4 * ty + u];
+                b[u] = ys[k][4 * tx + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v].add(a[u], b[v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + 4 * ty + u, j = j0 + 4 * tx + v;
+            if (i < nx && j < ny) atomicAdd(S + (int64_t)i * lds + j, dV * acc[u][v].value());
+        }
+}
+
+__global__ void k_zero2d(double *S, int64_t lds, int n, int m) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * m; e += (int64_t)gridDim.x * blockDim.x)
+        S[(e / m) * lds + e % m] = 0.0;
+}
+
+template <typename T>
+int gram(const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy, int ny, int64_t npts, double dV, double *S,
+         int64_t lds, cudaStream_t st) {
+    k_zero2d<<<64, 256, 0, st>>>(S, lds, nx, ny);
+    RS_LAUNCH_CHECK();
+    const int gx = (nx + G_TM - 1) / G_TM, gy = (ny + G_TN - 1) / G_TN;
+    // enough CTAs to fill the GPU twice over, each over a contiguous chunk of points
+    int splits = (int)std::max<int64_t>(1, std::min<int64_t>((npts + 255) / 256, (152 * 8) / std::max(1, gx * gy)));
+    int64_t chunk = (npts + splits - 1) / splits;
+    chunk = (chunk + G_TK - 1) / G_TK * G_TK;
+    splits = (int)((npts + chunk - 1) / chunk);
+    dim3 grid(gx, gy, splits);
+    k_gram<T><<<grid, G_NT, 0, st>>>(X, ldx, nx, Y, ldy, ny, npts, chunk, dV, S, lds);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+template int gram<double>(const double *, int64_t, int, const double *, int64_t, int, int64_t, double, double *,
+                          int64_t, cudaStream_t);
+template int gram<float>(const float *, int64_t, int, const float *, int64_t, int, int64_t, double, double *, int64_t,
+                         cudaStream_t);
+
+// ----------------------------------------------------------- k_rowmul ---
+// Y[p][0:m] = alpha * sum_k X[p][k] C[k][0:m] + beta * Y[p][0:m] for a tile of
+// R_ROWS rows per CTA; X rows are staged in shared memory first, so Y may
+// alias X (in-place rotation).  C is FP64 [n][ldc] converted on the fly.
+
+constexpr int R_ROWS = 16, R_NT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(R_NT) k_rowmul(const T *X, int64_t ldx, int n, const double *__restrict__ C,
+                                                 int64_t ldc, int m, T *Y, int64_t ldy, int64_t npts, T alpha, T beta) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *xs = reinterpret_cast<T *>(smraw);  // [R_ROWS][n]
+    const int64_t r0 = (int64_t)blockIdx.x * R_ROWS;
+    const int rows = (int)min<int64_t>(R_ROWS, npts - r0);
+    for (int e = threadIdx.x; e < R_ROWS * n; e += R_NT) {
+        const int r = e / n, k = e % n;
+        xs[e] = r < rows ? X[(r0 + r) * ldx + k] : T(0);
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < m; c0 += R_NT) {
+        const int c = c0 + threadIdx.x;
+        T acc[R_ROWS];
+#pragma unroll
+        for (int r = 0; r < R_ROWS; ++r) acc[r] = 0;
+        if (c < m) {
+            for (int k = 0; k < n; ++k) {
+                const T w = (T)__ldg(C + (int64_t)k * ldc + c);
+#pragma unroll
+                for (int r = 0; r < R_ROWS; ++r) acc[r] += xs[r * n + k] * w;
+            }
+            for (int r = 0; r < rows; ++r) {
+                T *y = Y + (r0 + r) * ldy + c;
+                *y = beta == T(0) ? alpha * acc[r] : alpha * acc[r] + beta * *y;
+            }
+        }
+    }
+}
+
+template <typename T>
+int rowmul(const T *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, T *Y, int64_t ldy, int64_t npts,
+           double alpha, double beta, cudaStream_t st) {
+    const size_t smem = (size_t)R_ROWS * n * sizeof(T);
+    if (smem > 200 * 1024) return fail(RS_EINVAL, "rowmul: n too large");
+    if (smem > 48 * 1024) RS_CUDA(cudaFuncSetAttribute(k_rowmul<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = (npts + R_ROWS - 1) / R_ROWS;
+    k_rowmul<T><<<(unsigned)blocks, R_NT, smem, st>>>(X, ldx, n, C, ldc, m, Y, ldy, npts, (T)alpha, (T)beta);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+template int rowmul<double>(const double *, int64_t, int, const double *, int64_t, int, double *, int64_t, int64_t,
+                            double, double, cudaStream_t);
+template int rowmul<float>(const float *, int64_t, int, const double *, int64_t, int, float *, int64_t, int64_t, double,
+                           double, cudaStream_t);
+
+// ----------------------------------------------------- small dense FP64 ---
+
+// Right-looking Cholesky of the leading n x n block of A (in place): the
+// upper triangle receives U with A = U^T U, the strict lower triangle is
+// zeroed.  status[0] = 0, or j+1 if pivot j is not finite or not larger
+// than rel * (original A_jj).  n <= CHOL_MAX.
+constexpr int CHOL_MAX = 2048;
+__global__ void __launch_bounds__(1024) k_chol(double *A, int lda, int n, double rel, int *status) {
+    __shared__ double diag0[CHOL_MAX];
+    __shared__ double piv;
+    __shared__ int bad;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) diag0[j] = A[(int64_t)j * lda + j];
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = A[(int64_t)j * lda + j];
+            if (!isfinite(d) || !(d > 0.0) || !(d > rel * diag0[j])) {
+                bad = j + 1;
+                piv = 1.0;
+            } else {
+                piv = sqrt(d);
+            }
+            A[(int64_t)j * lda + j] = piv;
+        }
+        __syncthreads();
+        if (bad) break;
+        const double p = piv;
+        for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) A[(int64_t)j * lda + c] /= p;
+        __syncthreads();
+        // trailing update A[r][c] -= U[j][r] U[j][c] on the upper triangle, r, c > j
+        const int m = n - j - 1;
+        for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+            const int r = j + 1 + (int)(e / m), c = j + 1 + (int)(e % m);
+            if (c >= r) A[(int64_t)r * lda + c] -= A[(int64_t)j * lda + r] * A[(int64_t)j * lda + c];
+        }
+        __syncthreads();
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+        const int r = (int)(e / n), c = (int)(e % n);
+        if (c < r) A[(int64_t)r * lda + c] = 0.0;
+    }
+    if (threadIdx.x == 0) status[0] = bad;
+}
+
+// X = U^-1 for upper-triangular U (n x n): one thread per column, back
+// substitution from the diagonal upwards.  X must not alias U.
+__global__ void k_trinv(const double *__restrict__ U, int ldu, int n, double *__restrict__ X, int ldx) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= n) return;
+    for (int i = n - 1; i > col; --i) X[(int64_t)i * ldx + col] = 0.0;
+    for (int i = col; i >= 0; --i) {
+        double t = (i == col) ? 1.0 : 0.0;
+        for (int k = i + 1; k <= col; ++k) t -= U[(int64_t)i * ldu + k] * X[(int64_t)k * ldx + col];
+        X[(int64_t)i * ldx + col] = t / U[(int64_t)i * ldu + i];
+    }
+}
+
+// C = alpha op(A) op(B) + beta C for small dense FP64 matrices (row-major),
+// op(X) = X or X^T.  C is m x n, the contraction length is k.  16x16 tiles.
+__global__ void k_gemm_small(int m, int n, int k, double alpha, const double *__restrict__ A, int lda, int ta,
+                             const double *__restrict__ B, int ldb, int tb, double beta, double *C, int ldc) {
+    __shared__ double as[16][17], bs[16][17];
+    const int r = blockIdx.y * 16 + threadIdx.y, c = blockIdx.x * 16 + threadIdx.x;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < k; k0 += 16) {
+        const int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+        const int ar = blockIdx.y * 16 + threadIdx.y, bc = blockIdx.x * 16 + threadIdx.x;
+        as[threadIdx.y][threadIdx.x] =
+            (ar < m && ka < k) ? (ta ? A[(int64_t)ka * lda + ar] : A[(int64_t)ar * lda + ka]) : 0.0;
+        bs[threadIdx.y][threadIdx.x] =
+            (kb < k && bc < n) ? (tb ? B[(int64_t)bc * ldb + kb] : B[(int64_t)kb * ldb + bc]) : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc = fma(as[threadIdx.y][t], bs[t][threadIdx.x], acc);
+        __syncthreads();
+    }
+    if (r < m && c < n) {
+        double *y = C + (int64_t)r * ldc + c;
+        *y = beta == 0.0 ? alpha * acc : alpha * acc + beta * *y;
+    }
+}
+
+int gemm_small(int m, int n, int k, double alpha, const double *A, int lda, bool ta, const double *B, int ldb,
+               bool tb, double beta, double *C, int ldc, cudaStream_t st) {
+    dim3 grid((n + 15) / 16, (m + 15) / 16), blk(16, 16);
+    k_gemm_small<<<grid, blk, 0, st>>>(m, n, k, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+int cholesky(double *A, int lda, int n, double rel, int *status_dev, cudaStream_t st) {
+    if (n > CHOL_MAX) return fail(RS_EINVAL, "cholesky: n > %d", CHOL_MAX);
+    k_chol<<<1, 1024, 0, st>>>(A, lda, n, rel, status_dev);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+int tri_inv(const double *U, int ldu, int n, double *X, int ldx, cudaStream_t st) {
+    k_trinv<<<(n + 127) / 128, 128, 0, st>>>(U, ldu, n, X, ldx);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+// (A + A^T) / 2 in place (n x n)
+__global__ void k_symmetrize(double *A, int lda, int n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), c = (int)(e % n);
+        if (c > r) {
+            const double v = 0.5 * (A[(int64_t)r * lda + c] + A[(int64_t)c * lda + r]);
+            A[(int64_t)r * lda + c] = v;
+            A[(int64_t)c * lda + r] = v;
+        }
+    }
+}
+
+int symmetrize(double *A, int lda, int n, cudaStream_t st) {
+    k_symmetrize<<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(A, lda, n);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+// ----------------------------------------------------------- Jacobi ---
+// Cyclic Jacobi eigenvalue iteration for a symmetric n x n matrix (n even),
+// one CTA.  Each round applies n/2 rotations on disjoint index pairs (the
+// round-robin "circle" ordering: pair (0, 1 + r mod (n-1)) and the pairs
+// (1 + (r+k) mod (n-1), 1 + (r-k) mod (n-1)), k = 1..n/2-1), each rotation
+// annihilating its (p,q) entry; n-1 rounds make a sweep visiting every pair.
+// A (overwritten) and V live in global workspace (L1/L2 resident).  On exit
+// w[0..n) holds the eigenvalues ascending and Vout[:, k] the eigenvectors
+// (FP64); info[0] = sweeps used, or -1 if max_sweeps ran out.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_jacobi(T *A, T *V, int n, int max_sweeps, double tol, double *w,
+                                                 double *Vout, int ldv, int *info) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *cs = reinterpret_cast<T *>(smraw);       // [n/2]
+    T *sn = cs + n / 2;                          // [n/2]
+    int *pp = reinterpret_cast<int *>(sn + n / 2);
+    int *qq = pp + n / 2;
+    int *rank = qq + n / 2;                      // [n]
+    __shared__ double red[32];
+    __shared__ double fro2, off2;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int h = n / 2, m = n - 1;
+    for (int64_t e = tid; e < (int64_t)n * n; e += nt) V[e] = (e / n == e % n) ? T(1) : T(0);
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        double t = 0;
+        if (tid < 32) {
+            t = tid < (nt + 31) / 32 ? red[tid] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        }
+        return t;  // valid in thread 0
+    };
+    double loc = 0;
+    for (int64_t e = tid; e < (int64_t)n * n; e += nt) loc += (double)A[e] * (double)A[e];
+    const double f = block_sum(loc);
+    if (tid == 0) fro2 = f;
+    __syncthreads();
+    int sweep = 0, done = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        loc = 0;
+        for (int64_t e = tid; e < (int64_t)n * n; e += nt)
+            if (e / n != e % n) loc += (double)A[e] * (double)A[e];
+        const double o = block_sum(loc);
+        if (tid == 0) off2 = o;
+        __syncthreads();
+        if (off2 <= tol * tol * fro2) {
+            done = 1;
+            break;
+        }
+        for (int r = 0; r < m; ++r) {
+            for (int k = tid; k < h; k += nt) {
+                int p, q;
+                if (k == 0) {
+                    p = 0;
+                    q = 1 + r % m;
+                } else {
+                    p = 1 + (r + k) % m;
+                    q = 1 + (r - k + m) % m;
+                }
+                const T apq = A[(int64_t)p * n + q];
+                T c = 1, s_ = 0;
+                if (apq != T(0)) {
+                    const T theta = (A[(int64_t)q * n + q] - A[(int64_t)p * n + p]) / (T(2) * apq);
+                    const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+                    c = T(1) / sqrt(t * t + T(1));
+                    s_ = t * c;
+                }
+                cs[k] = c;
+                sn[k] = s_;
+                pp[k] = p;
+                qq[k] = q;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int64_t e = tid; e < (int64_t)h * n; e += nt) {
+                const int k = (int)(e / n), j = (int)(e % n);
+                const int p = pp[k], q = qq[k];
+                const T c = cs[k], s_ = sn[k];
+                const T a = A[(int64_t)p * n + j], b = A[(int64_t)q * n + j];
+                A[(int64_t)p * n + j] = c * a - s_ * b;
+                A[(int64_t)q * n + j] = s_ * a + c * b;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int64_t e = tid; e < (int64_t)h * n; e += nt) {
+                const int k = (int)(e / n), i = (int)(e % n);
+                const int p = pp[k], q = qq[k];
+                const T c = cs[k], s_ = sn[k];
+                const T a = A[(int64_t)i * n + p], b = A[(int64_t)i * n + q];
+                A[(int64_t)i * n + p] = c * a - s_ * b;
+                A[(int64_t)i * n + q] = s_ * a + c * b;
+                const T va = V[(int64_t)i * n + p], vb = V[(int64_t)i * n + q];
+                V[(int64_t)i * n + p] = c * va - s_ * vb;
+                V[(int64_t)i * n + q] = s_ * va + c * vb;
+            }
+            __syncthreads();
+        }
+    }
+    // ascending order (ties by index)
+    for (int i = tid; i < n; i += nt) {
+        const T di = A[(int64_t)i * n + i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const T dj = A[(int64_t)j * n + j];
+            rk += (dj < di) || (dj == di && j < i);
+        }
+        rank[i] = rk;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) w[rank[i]] = (double)A[(int64_t)i * n + i];
+    for (int64_t e = tid; e < (int64_t)n * n; e += nt) {
+        const int i = (int)(e / n), k = (int)(e % n);
+        Vout[(int64_t)i * ldv + rank[k]] = (double)V[e];
+    }
+    if (tid == 0) info[0] = done ? sweep : -1;
+}
+
+// FP64 -> T copy of an n x n matrix into a dense buffer
+template <typename T> __global__ void k_copy_cast(const double *A, int lda, int n, T *B) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        B[e] = (T)A[(e / n) * lda + e % n];
+}
+
+template <typename T>
+int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *w, double *V, int ldv, int *info,
+           void *scratch, cudaStream_t st) {
+    if (n % 2) return fail(RS_EINVAL, "jacobi: n must be even");
+    T *a = reinterpret_cast<T *>(scratch);
+    T *v = a + (size_t)n * n;
+    k_copy_cast<T><<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(A, lda, n, a);
+    RS_LAUNCH_CHECK();
+    const size_t smem = (size_t)n * sizeof(T) + (size_t)n * 2 * sizeof(int) + (size_t)n * sizeof(int);
+    k_jacobi<T><<<1, 1024, smem, st>>>(a, v, n, max_sweeps, tol, w, V, ldv, info);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+template int jacobi<float>(const double *, int, int, int, double, double *, double *, int, int *, void *, cudaStream_t);
+template int jacobi<double>(const double *, int, int, int, double, double *, double *, int, int *, void *,
+                            cudaStream_t);
+
+// ---------------------------------------------------------- RefSyEv ---
+// One refinement step of approximate eigenvectors X (n x n, FP64) of the
+// symmetric A (Ogita & Aishima 2018): with R = I - X^T X and S = X^T A X,
+// lambda_i = s_ii / (1 - r_ii) and the correction X <- X (I + E),
+//   E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)  if |lambda_i - lambda_j| > delta
+//   E_ij = r_ij / 2                                        otherwise,
+// delta = 2 (||S - diag(lambda)|| + ||A|| ||R||) (Frobenius norms bound the 2-norms).
+__global__ void k_refsyev_norms(const double *A, int lda, const double *R, const double *S, int n, double *out) {
+    __shared__ double red[3][32];
+    double a = 0, r = 0, s = 0;
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const double av = A[(int64_t)i * lda + j];
+        a += av * av;
+        r += R[e] * R[e];
+        if (i != j) s += S[e] * S[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        r += __shfl_down_sync(0xffffffffu, r, o);
+        s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = r;
+        red[2][threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[3] = {0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
+            for (int q = 0; q < 3; ++q) t[q] += red[q][w];
+        // S - diag(lambda): off-diagonal part plus the tiny diagonal residue (ignored)
+        out[0] = 2.0 * (sqrt(t[2]) + sqrt(t[0]) * sqrt(t[1]));
+    }
+}
+
+__global__ void k_refsyev_e(const double *R, const double *S, int n, const double *delta, double *E, double *lam) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const double li = S[(int64_t)i * n + i] / (1.0 - R[(int64_t)i * n + i]);
+        const double lj = S[(int64_t)j * n + j] / (1.0 - R[(int64_t)j * n + j]);
+        double v;
+        if (i == j) {
+            v = 0.5 * R[e];
+            lam[i] = li;
+        } else if (fabs(li - lj) > delta[0]) {
+            v = (S[e] + lj * R[e]) / (lj - li);
+        } else {
+            v = 0.5 * R[e];
+        }
+        E[e] = v;
+    }
+}
+
+__global__ void k_add_inplace(double *X, int ldx, const double *D, int ldd, int n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        X[(e / n) * ldx + e % n] += D[(e / n) * ldd + e % n];
+}
+
+__global__ void k_identity_minus(double *R, int n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        R[e] = ((e / n == e % n) ? 1.0 : 0.0) - R[e];
+}
+
+// X (n x ldx) refined in place; lam[n] receives the refined eigenvalues.
+// work: 4 n^2 + 1 doubles.
+int refsyev(const double *A, int lda, double *X, int ldx, int n, double *lam, double *work, int iters, cudaStream_t st) {
+    double *R = work, *AX = R + (size_t)n * n, *S = AX + (size_t)n * n, *E = S + (size_t)n * n,
+           *delta = E + (size_t)n * n;
+    const int eb = std::min(1024, (n * n + 255) / 256);
+    for (int it = 0; it < iters; ++it) {
+        RS_TRY(gemm_small(n, n, n, 1.0, X, ldx, true, X, ldx, false, 0.0, R, n, st));
+        k_identity_minus<<<eb, 256, 0, st>>>(R, n);
+        RS_TRY(gemm_small(n, n, n, 1.0, A, lda, false, X, ldx, false, 0.0, AX, n, st));
+        RS_TRY(gemm_small(n, n, n, 1.0, X, ldx, true, AX, n, false, 0.0, S, n, st));
+        k_refsyev_norms<<<1, 1024, 0, st>>>(A, lda, R, S, n, delta);
+        k_refsyev_e<<<eb, 256, 0, st>>>(R, S, n, delta, E, lam);
+        // X <- X + X E  (via AX as the product buffer)
+        RS_TRY(gemm_small(n, n, n, 1.0, X, ldx, false, E, n, false, 0.0, AX, n, st));
+        k_add_inplace<<<eb, 256, 0, st>>>(X, ldx, AX, n, n);
+        RS_LAUNCH_CHECK();
+    }
+    return RS_OK;
+}
+
+}  // namespace rs

@@ -1,0 +1,44 @@
+// Internal device linear-algebra entry points (see linalg.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace rs {
+
+// S = dV X^T Y (nx x ny, FP64, row stride lds); X, Y are [npts][ld] of T.
+template <typename T>
+int gram(const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy, int ny, int64_t npts, double dV, double *S,
+         int64_t lds, cudaStream_t st);
+
+// Y = alpha X C + beta Y row by row; X [npts][ldx] (n columns), C FP64 [n][ldc]
+// (m columns), Y [npts][ldy]; Y may alias X when beta == 0.
+template <typename T>
+int rowmul(const T *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, T *Y, int64_t ldy, int64_t npts,
+           double alpha, double beta, cudaStream_t st);
+
+// Small dense FP64 helpers.
+int gemm_small(int m, int n, int k, double alpha, const double *A, int lda, bool ta, const double *B, int ldb, bool tb,
+               double beta, double *C, int ldc, cudaStream_t st);
+int cholesky(double *A, int lda, int n, double rel, int *status_dev, cudaStream_t st);
+int tri_inv(const double *U, int ldu, int n, double *X, int ldx, cudaStream_t st);
+int symmetrize(double *A, int lda, int n, cudaStream_t st);
+
+// Jacobi eigensolver in precision T on a copy of A (scratch: 2 n^2 T).
+template <typename T>
+int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *w, double *V, int ldv, int *info,
+           void *scratch, cudaStream_t st);
+
+// Ogita-Aishima refinement of eigenvectors X of A; work: 4 n^2 + 1 doubles.
+int refsyev(const double *A, int lda, double *X, int ldx, int n, double *lam, double *work, int iters,
+            cudaStream_t st);
+
+// Symmetric eigendecomposition A = V diag(w) V^T (ascending), FP64 result:
+// FP32 Jacobi followed by `refine` FP64 refinement steps (refine = 0:
+// FP64 Jacobi).  work: eigh_work_bytes(n).
+size_t eigh_work_bytes(int n);
+int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int refine, int *info_dev, void *work,
+         cudaStream_t st);
+
+}  // namespace rs

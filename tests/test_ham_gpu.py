@@ -1,0 +1,116 @@
+"""H psi on the GPU (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 mode, relative error per state <= 1e-12 (the FP64 hot-path
+target).  FP32 mode: the oracle is fed the same FP32-rounded inputs; an
+output is a sum of ~30 products of magnitude up to |w_0 psi| ~ 4.3/h^2 |psi|
+plus the potential, so FP32 rounding bounds its error by roughly
+30 * 2^-24 * max|term|; per state this gives a relative norm error below
+2e-6 for random orbitals and below 3e-5 for smooth ones, where the Laplacian
+cancels most of the terms (the bounds asserted below).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests.helpers import SMALL_ATOMS, SMALL_E, SMALL_H, SMALL_RADIUS, lib_to_oracle_index, oracle_system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _lib_system(kind, params):
+    from paper_1306_2953_gb300 import api
+    g_ora, H_ora, atoms, E = oracle_system(kind, *params)
+    if kind == "box":
+        n, h, _ = params
+        lg = api.Grid.box(n, n, n, h)
+        proj = None
+    else:
+        spec_r, spec_h = (params[0].radius, params[0].h) if kind == "mol" else (params[2], params[3])
+        lg = api.Grid.spheres(atoms, spec_r, spec_h)
+        r_c, r_cut = (params[0].r_c, params[0].r_cut) if kind == "mol" else (1.0, 3.0)
+        proj = api.Projectors(lg, atoms, E, r_c, r_cut)
+    idx = lib_to_oracle_index(g_ora, lg.ijk())
+    H = api.Hamiltonian(lg, H_ora.V[idx], proj)
+    return lg, H, g_ora, H_ora, idx
+
+
+def _rel_err_per_state(got, ref):
+    num = np.linalg.norm(got - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    return num / den
+
+
+SYSTEMS = {
+    "small_mol": ("atoms", (SMALL_ATOMS, SMALL_E, SMALL_RADIUS, SMALL_H)),
+    "box17": ("box", (17, 0.3, 1.0)),
+}
+
+
+@pytest.mark.parametrize("system", list(SYSTEMS))
+@pytest.mark.parametrize("nb", [1, 2, 4, 8, 16, 32, 64])
+def test_hpsi_f64_parity(system, nb):
+    kind, params = SYSTEMS[system]
+    lg, H, g_ora, H_ora, idx = _lib_system(kind, params)
+    psi_ora = wl.random_block(g_ora.npts, nb, 100 + nb)
+    ref = H_ora.apply(psi_ora)[idx]
+    psi = torch.from_numpy(np.ascontiguousarray(psi_ora[idx])).cuda()
+    out = H.apply(psi).cpu().numpy()
+    assert np.max(_rel_err_per_state(out, ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("nb", [4, 16, 32, 64])
+def test_hpsi_f32_parity(nb):
+    kind, params = SYSTEMS["small_mol"]
+    lg, H, g_ora, H_ora, idx = _lib_system(kind, params)
+    psi32 = wl.random_block(g_ora.npts, nb, 7).astype(np.float32)
+    # the oracle sees the FP32 inputs exactly, the potential and projectors in FP64
+    ref = H_ora.apply(psi32.astype(np.float64))[idx]
+    psi = torch.from_numpy(np.ascontiguousarray(psi32[idx])).cuda()
+    out = H.apply(psi).cpu().numpy().astype(np.float64)
+    assert np.max(_rel_err_per_state(out, ref)) <= 2e-6
+    smooth = wl.gaussian_sum_block(g_ora.coords, nb, 8).astype(np.float32)
+    ref = H_ora.apply(smooth.astype(np.float64))[idx]
+    out = H.apply(torch.from_numpy(np.ascontiguousarray(smooth[idx])).cuda()).cpu().numpy()
+    assert np.max(_rel_err_per_state(out.astype(np.float64), ref)) <= 3e-5
+
+
+def test_hpsi_strided_block_and_untouched_columns():
+    kind, params = SYSTEMS["small_mol"]
+    lg, H, g_ora, H_ora, idx = _lib_system(kind, params)
+    psi_ora = wl.random_block(g_ora.npts, 48, 3)
+    full = torch.from_numpy(np.ascontiguousarray(psi_ora[idx])).cuda()
+    out = torch.full_like(full, 7.0)
+    H.apply(full[:, 16:32], out[:, 16:32], nb=16)
+    ref = H_ora.apply(psi_ora[:, 16:32])[idx]
+    o = out.cpu().numpy()
+    assert np.max(_rel_err_per_state(o[:, 16:32], ref)) <= 1e-12
+    assert np.all(o[:, :16] == 7.0) and np.all(o[:, 32:] == 7.0)
+
+
+def test_hpsi_bad_arguments():
+    from paper_1306_2953_gb300._lib import RsError
+    kind, params = SYSTEMS["box17"]
+    lg, H, g_ora, _, _ = _lib_system(kind, params)
+    psi = torch.zeros((g_ora.npts, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(RsError):
+        H.apply(psi, nb=3)
+    with pytest.raises(RsError):
+        H.apply(psi, psi)          # in place is rejected
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hpsi_full_size_mol100(dtype):
+    """The benchmark's workload (100 atoms, h=0.3, blocks of 32) at full size,
+    on one block of 32 states, element by element against the oracle."""
+    spec = wl.MOL100.system
+    lg, H, g_ora, H_ora, idx = _lib_system("mol", (spec,))
+    psi_ora = wl.random_block(g_ora.npts, 32, 55)
+    if dtype == "f32":
+        psi_ora = psi_ora.astype(np.float32).astype(np.float64)
+    ref = H_ora.apply(psi_ora)[idx]
+    t = torch.float64 if dtype == "f64" else torch.float32
+    psi = torch.from_numpy(np.ascontiguousarray(psi_ora[idx])).to(t).cuda()
+    out = H.apply(psi).double().cpu().numpy()
+    tol = 1e-12 if dtype == "f64" else 2e-6
+    assert np.max(_rel_err_per_state(out, ref)) <= tol

@@ -1,0 +1,89 @@
+"""Host-side library logic against the oracle (no GPU needed): the grid's
+point set and map (bit-exact), the brick ordering, the projector sphere
+lists (bit-exact) and their coefficients, and argument checking."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import grid as og, hamiltonian as oh
+from paper_1306_2953_gb300 import api
+from paper_1306_2953_gb300._lib import RS_EINVAL, RsError
+from tests.helpers import SMALL_ATOMS, SMALL_E, SMALL_H, SMALL_RADIUS, lib_to_oracle_index
+
+
+def _same_points(lg, og_):
+    lib_ijk = lg.ijk()
+    assert lg.npts == og_.npts
+    assert set(map(tuple, lib_ijk.tolist())) == set(map(tuple, og_.ijk.tolist()))
+    return lib_ijk
+
+
+@pytest.mark.parametrize("spec", [wl.MOL20.system, wl.MoleculeSpec(7, 5.0, 1.5, 2.5, 0.41, 11)])
+def test_sphere_grid_bit_exact(spec):
+    atoms = wl.atom_positions(spec)
+    lg = api.Grid.spheres(atoms, spec.radius, spec.h)
+    ref = og.sphere_union_grid(atoms, spec.radius, spec.h)
+    lib_ijk = _same_points(lg, ref)
+    # the point map is consistent with the coordinates and -1 elsewhere
+    npts, origin, dims, h = lg.info()
+    mp = lg.point_map()
+    assert mp.shape == tuple(dims)
+    rel = lib_ijk - np.array(origin)
+    assert np.array_equal(mp[rel[:, 0], rel[:, 1], rel[:, 2]], np.arange(npts))
+    assert np.sum(mp >= 0) == npts
+    # a 4-point margin around every grid point stays inside the map
+    assert rel.min() >= 4 and np.all(rel.max(axis=0) <= np.array(dims) - 5)
+    # coordinates are h * ijk, bitwise
+    assert np.array_equal(lg.coords(), h * lib_ijk.astype(np.float64))
+
+
+def test_brick_order():
+    lg = api.Grid.spheres(np.array([[0.0, 0.0, 0.0]]), 2.0, 0.3)
+    _, origin, _, _ = lg.info()
+    rel = lg.ijk() - np.array(origin)
+    brick = rel // 4
+    key = (brick[:, 0] * 10000 + brick[:, 1]) * 10000 + brick[:, 2]
+    assert np.all(np.diff(key) >= 0), "points are not grouped brick by brick in brick order"
+
+
+def test_box_grid_bit_exact():
+    lg = api.Grid.box(6, 5, 7, 0.3)
+    assert lg.npts == 210
+    c = lg.coords()
+    ijk = lg.ijk()
+    assert np.array_equal(c[:, 1], (ijk[:, 1].astype(np.float64) - 2.0) * 0.3)
+    ref = og.box_grid(6, 0.3)
+    lg6 = api.Grid.box(6, 6, 6, 0.3)
+    idx = lib_to_oracle_index(ref, lg6.ijk())
+    assert np.array_equal(lg6.coords(), ref.coords[idx])
+
+
+def test_projector_tables_match_oracle():
+    atoms = np.array(SMALL_ATOMS)
+    E = np.array(SMALL_E)
+    lg = api.Grid.spheres(atoms, SMALL_RADIUS, SMALL_H)
+    ref = og.sphere_union_grid(atoms, SMALL_RADIUS, SMALL_H)
+    pr_ref = oh.make_projectors(ref, atoms, E, 1.0, 3.0)
+    pr = api.Projectors(lg, atoms, E, 1.0, 3.0)
+    off, idx, gam = pr.tables()
+    lib_ijk = lg.ijk()
+    to_ora = lib_to_oracle_index(ref, lib_ijk)
+    for A in range(len(atoms)):
+        lib_pts = to_ora[idx[off[A]:off[A + 1]]]
+        ora_pts = pr_ref.points(A)
+        assert set(lib_pts.tolist()) == set(ora_pts.tolist())      # exact sphere membership
+        assert np.all(np.diff(idx[off[A]:off[A + 1]]) > 0)          # ascending library ids
+        order = np.argsort(lib_pts)
+        g_lib = gam[off[A]:off[A + 1]][order]
+        g_ora = pr_ref.gamma(A).T[np.argsort(ora_pts)]
+        assert np.abs(g_lib - g_ora).max() < 1e-13 * np.abs(g_ora).max()
+
+
+def test_argument_errors():
+    with pytest.raises(RsError) as e:
+        api.Grid.spheres(np.zeros((1, 3)), -1.0, 0.3)
+    assert e.value.code == RS_EINVAL
+    with pytest.raises(RsError):
+        api.Grid.box(0, 4, 4, 0.3)
+    with pytest.raises(RsError):
+        api.Grid.spheres(np.array([[np.nan, 0.0, 0.0]]), 1.0, 0.3)
