@@ -183,3 +183,105 @@ class Hamiltonian:
             self.close()
         except Exception:
             pass
+
+
+def linalg_workspace(nst: int, device=None):
+    import torch
+    nbytes = int(_lib.lib().rs_linalg_workspace_bytes(nst))
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def overlap(grid: Grid, X, Y, stream=None):
+    """S = dV X^T Y (FP64, device) for device tensors X [npts, nx], Y [npts, ny]."""
+    import torch
+    S = torch.empty((X.shape[1], Y.shape[1]), dtype=torch.float64, device=X.device)
+    call("rs_overlap_block", grid._h, _c(X.data_ptr()), X.stride(0), X.shape[1], _c(Y.data_ptr()), Y.stride(0),
+         Y.shape[1], _c(S.data_ptr()), S.stride(0), dtype_code(X), _stream(stream))
+    return S
+
+
+def orthonormalize(grid: Grid, Psi, work=None, stream=None):
+    """Psi <- Psi U^-1 in place (Cholesky, Sec. VI); returns U^-1 (FP64)."""
+    import torch
+    nst = Psi.shape[1]
+    work = linalg_workspace(nst, Psi.device) if work is None else work
+    Ui = torch.empty((nst, nst), dtype=torch.float64, device=Psi.device)
+    call("rs_orthonormalize", grid._h, _c(Psi.data_ptr()), Psi.stride(0), nst, dtype_code(Psi), _c(work.data_ptr()),
+         _c(Ui.data_ptr()), _stream(stream))
+    return Ui
+
+
+def subspace_diag(ham: Hamiltonian, Psi, HPsi=None, nb: int = 32, work=None, stream=None):
+    """Rayleigh-Ritz in place (Sec. VI); returns (eps, xi, HPsi)."""
+    import torch
+    nst = Psi.shape[1]
+    HPsi = torch.empty_like(Psi) if HPsi is None else HPsi
+    work = linalg_workspace(nst, Psi.device) if work is None else work
+    eps = torch.empty(nst, dtype=torch.float64, device=Psi.device)
+    xi = torch.empty((nst, nst), dtype=torch.float64, device=Psi.device)
+    call("rs_subspace_diag", ham._h, _c(Psi.data_ptr()), _c(HPsi.data_ptr()), Psi.stride(0), nst, dtype_code(Psi),
+         min(nb, nst), _c(eps.data_ptr()), _c(xi.data_ptr()), _c(work.data_ptr()), _stream(stream))
+    return eps, xi, HPsi
+
+
+class Solver:
+    """Block CG (LOBPCG) eigensolver (rs_solver_*)."""
+
+    def __init__(self, ham: Hamiltonian, Psi0, nb: int, tol: float, precond: int = _lib.RS_PRECOND_FILTER,
+                 filter_alpha: float = 0.5, stream=None):
+        cfg = _lib.SolverCfg(Psi0.shape[1], nb, dtype_code(Psi0), precond, float(tol), float(filter_alpha))
+        assert Psi0.is_contiguous()
+        out = ctypes.c_void_p()
+        call("rs_solver_create", ham._h, ctypes.byref(cfg), _c(Psi0.data_ptr()), _stream(stream), ctypes.byref(out))
+        self._h = out
+        self.ham = ham
+        self.nst = Psi0.shape[1]
+        self.dtype = Psi0.dtype
+        self.device = Psi0.device
+
+    def step(self, stream=None):
+        """One sweep; returns (eps, resnorm, n_converged) with device FP64 tensors."""
+        import torch
+        eps = torch.empty(self.nst, dtype=torch.float64, device=self.device)
+        res = torch.empty(self.nst, dtype=torch.float64, device=self.device)
+        nconv = ctypes.c_int()
+        call("rs_eigensolver_step", self._h, _c(eps.data_ptr()), _c(res.data_ptr()), ctypes.byref(nconv),
+             _stream(stream))
+        return eps, res, nconv.value
+
+    def psi(self):
+        """The solver's orbitals as a torch tensor view [npts, nst] (no copy)."""
+        import torch
+        p = ctypes.c_void_p()
+        call("rs_solver_psi", self._h, ctypes.byref(p))
+        return _device_view(p.value, (self.ham.npts, self.nst), self.dtype, self.device)
+
+    def set_precond_weights(self, w1, w2, w3):
+        call("rs_solver_set_precond_weights", self._h, _c(w1.data_ptr()), _c(w2.data_ptr()), _c(w3.data_ptr()))
+
+    def close(self):
+        if self._h:
+            _lib.lib().rs_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view(ptr: int, shape, dtype, device):
+    """A torch tensor aliasing library-owned device memory (copy it before
+    the owner is destroyed)."""
+    import torch
+
+    class _Holder:
+        def __init__(self, p, shape, typestr, strides):
+            self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (p, False),
+                                             "version": 2, "strides": strides}
+
+    es = torch.tensor([], dtype=dtype).element_size()
+    typestr = "<f8" if es == 8 else "<f4"
+    strides = (shape[1] * es, es)
+    return torch.as_tensor(_Holder(ptr, shape, typestr, strides), device=device)

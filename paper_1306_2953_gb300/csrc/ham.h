@@ -1,0 +1,21 @@
+// Internal accessors of the Hamiltonian handle shared with the solver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rsdft.h"
+
+namespace rs {
+
+int64_t ham_npts(const rs_ham *h);
+double ham_dV(const rs_ham *h);
+
+// W = K R with the face-neighbour smoothing filter
+//   (K r)(p) = alpha r(p) + (1 - alpha)/6 sum_{6 face neighbours} r(n),
+// r = 0 off the grid; R, W are [npts][ld] blocks of nb columns (dtype).
+int ham_filter(const rs_ham *h, const void *R, int64_t ldr, void *W, int64_t ldw, int nb, int dtype, double alpha,
+               cudaStream_t st);
+
+}  // namespace rs

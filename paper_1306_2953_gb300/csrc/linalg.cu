@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(R_NT) k_rowmul(const T *X, int64_t ldx, int n,
     extern __shared__ __align__(16) unsigned char smraw[];
     T *xs = reinterpret_cast<T *>(smraw);  // [R_ROWS][n]
     const int64_t r0 = (int64_t)blockIdx.x * R_ROWS;
-    const int rows = (int)min<int64_t>(R_ROWS, npts - r0);
+    const int rows = (int)(npts - r0 < R_ROWS ? npts - r0 : R_ROWS);
     for (int e = threadIdx.x; e < R_ROWS * n; e += R_NT) {
         const int r = e / n, k = e % n;
         xs[e] = r < rows ? X[(r0 + r) * ldx + k] : T(0);
@@ -535,6 +535,79 @@ int refsyev(const double *A, int lda, double *X, int ldx, int n, double *lam, do
         k_add_inplace<<<eb, 256, 0, st>>>(X, ldx, AX, n, n);
         RS_LAUNCH_CHECK();
     }
+    return RS_OK;
+}
+
+// ------------------------------------------------------------- eigh ---
+
+__global__ void k_pad_copy(const double *A, int lda, int n, int ne, double *B, double big) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)ne * ne;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ne), j = (int)(e % ne);
+        B[e] = (i < n && j < n) ? A[(int64_t)i * lda + j] : (i == j ? big : 0.0);
+    }
+}
+
+__global__ void k_pad_big(const double *A, int lda, int n, double *big) {
+    __shared__ double red[32];
+    double m = 0;
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+        const double v = A[(e / n) * lda + e % n];
+        m += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+        big[0] = 2.0 * sqrt(t) + 1.0;   // above every eigenvalue of A
+    }
+}
+
+__global__ void k_copy_block(const double *A, int lda, int m, int n, double *B, int ldb) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        B[(e / n) * ldb + e % n] = A[(e / n) * lda + e % n];
+}
+
+size_t eigh_work_bytes(int n) {
+    const size_t ne = (size_t)n + (n & 1);
+    // padded A, Jacobi scratch (2 ne^2), Jacobi vectors, eigenvalues, refinement (4 n^2 + 1), scalars
+    return sizeof(double) * (ne * ne * 4 + ne + 4 * (size_t)n * n + 64);
+}
+
+int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int refine, int *info_dev, void *work,
+         cudaStream_t st) {
+    const int ne = n + (n & 1);
+    double *Ap = reinterpret_cast<double *>(work);
+    double *jscr = Ap + (size_t)ne * ne;
+    double *Vp = jscr + 2 * (size_t)ne * ne;
+    double *wp = Vp + (size_t)ne * ne;
+    double *rwork = wp + ne;
+    double *big = rwork + 4 * (size_t)n * n + 1;
+    const int eb = std::min(1024, (ne * ne + 255) / 256);
+    if (ne != n) {
+        k_pad_big<<<1, 1024, 0, st>>>(A, lda, n, big);
+        RS_LAUNCH_CHECK();
+    }
+    // the pad entry's value is read on the device through `big`
+    k_pad_copy<<<eb, 256, 0, st>>>(A, lda, n, ne, Ap, 0.0);
+    RS_LAUNCH_CHECK();
+    if (ne != n) {
+        k_copy_block<<<1, 32, 0, st>>>(big, 1, 1, 1, Ap + (size_t)(ne - 1) * ne + (ne - 1), 1);
+        RS_LAUNCH_CHECK();
+    }
+    if (refine > 0) {
+        RS_TRY(jacobi<float>(Ap, ne, ne, 30, 2e-6, wp, Vp, ne, info_dev, jscr, st));
+    } else {
+        RS_TRY(jacobi<double>(Ap, ne, ne, 60, 1e-15, wp, Vp, ne, info_dev, jscr, st));
+    }
+    // leading n x n block: eigenvectors of A (the pad entry is decoupled and sorts last)
+    k_copy_block<<<eb, 256, 0, st>>>(Vp, ne, n, n, V, ldv);
+    k_copy_block<<<1, 256, 0, st>>>(wp, ne, 1, n, w, n);
+    RS_LAUNCH_CHECK();
+    if (refine > 0) RS_TRY(refsyev(A, lda, V, ldv, n, w, rwork, refine, st));
     return RS_OK;
 }
 

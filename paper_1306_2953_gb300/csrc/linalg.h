@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "rsdft.h"
+
 namespace rs {
 
 // S = dV X^T Y (nx x ny, FP64, row stride lds); X, Y are [npts][ld] of T.
@@ -40,5 +42,31 @@ int refsyev(const double *A, int lda, double *X, int ldx, int n, double *lam, do
 size_t eigh_work_bytes(int n);
 int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int refine, int *info_dev, void *work,
          cudaStream_t st);
+
+// Layout of the workspace of orthonormalize / subspace_diag for n states.
+struct LaWork {
+    double *S, *U, *Ui, *xi, *eig;
+    void *eigw;
+    int *status;
+    LaWork(void *base, int n) {
+        double *d = reinterpret_cast<double *>(base);
+        S = d;
+        U = S + (size_t)n * n;
+        Ui = U + (size_t)n * n;
+        xi = Ui + (size_t)n * n;
+        eig = xi + (size_t)n * n;
+        status = reinterpret_cast<int *>(eig + n);
+        eigw = reinterpret_cast<void *>(eig + n + 8);
+    }
+    static size_t bytes(int n) { return sizeof(double) * ((size_t)4 * n * n + n + 8) + eigh_work_bytes(n) + 256; }
+};
+
+// Psi (n columns) <- Psi C in place (C FP64 n x n).
+int rotate_inplace(void *Psi, int64_t ld, int n, const double *C, int64_t npts, int dtype, cudaStream_t st);
+// Psi <- Psi U^-1 with <Psi|Psi> = U^T U; w.Ui keeps U^-1.  Blocking; RS_ENOTSPD on failure.
+int orthonormalize_impl(int64_t npts, double dV, void *Psi, int64_t ld, int n, int dtype, void *work, cudaStream_t st);
+// HPsi = H Psi, h = <Psi|H|Psi>, h xi = xi diag(eps), Psi <- Psi xi, HPsi <- HPsi xi; w.xi keeps xi.
+int subspace_diag_impl(rs_ham *h, void *Psi, void *HPsi, int64_t ld, int n, int dtype, int nb, void *work,
+                       double *eps_dev, cudaStream_t st);
 
 }  // namespace rs

@@ -1,0 +1,22 @@
+// Preconditioners of the block eigensolver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rsdft.h"
+
+namespace rs {
+
+class Precond {
+   public:
+    virtual ~Precond() = default;
+    // W = K R for a block of nb residual columns; R [npts][ldr], W [npts][ldw].
+    virtual int apply(const rs_ham *h, const void *R, int64_t ldr, void *W, int64_t ldw, int nb, int dtype,
+                      cudaStream_t st) = 0;
+    virtual int set_weights(const float *w1, const float *w2, const float *w3);
+    static Precond *create(int kind, double filter_alpha);
+};
+
+}  // namespace rs

@@ -1,0 +1,367 @@
+// Block conjugate-gradient eigensolver (rs_solver_*, rs_eigensolver_step).
+//
+// The paper's eigensolver is RMM-DIIS working on blocks of orbitals with a
+// filter preconditioner (Sec. III) and per-block convergence (Sec. VIII).
+// This solver is LOBPCG (Knyazev 2001) applied block by block, followed by
+// the orthogonalisation and subspace diagonalisation of Sec. VI after every
+// sweep.  For each block X of nb states:
+//   lambda = <x|Hx>/<x|x>, R = HX - X lambda, ||r|| (FP64);  a block whose
+//   states all satisfy ||r|| <= tol is left alone (Sec. VIII);
+//   W = K R (preconditioner);  Y = [W, P] orthogonalised against the states
+//   up to and including the block by classical Gram-Schmidt done twice, its
+//   columns normalised;  Rayleigh-Ritz on Z = [X, Y] with FP64 Gram matrices
+//   (Cholesky with P dropped when the Gram matrix is ill-conditioned);
+//   X <- Z C, P <- Z[:, nb:] C[nb:, :].
+// After the sweep P follows Psi through U^-1 and xi.
+// Precision: RS_F64 keeps everything in FP64.  RS_F32 stores orbitals in
+// FP32 and runs H psi, the preconditioner and the rotations in FP32, while
+// Gram matrices, residual norms, Cholesky, Rayleigh-Ritz and eigenvalues are
+// FP64 (exact products with compensated accumulation, see linalg.cu).
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "device.h"
+#include "ham.h"
+#include "linalg.h"
+#include "precond.h"
+
+using namespace rs;
+
+namespace rs {
+
+// out[k] += sum_p A[p][k] B[p][k] for k < ncols (out zeroed by the caller)
+template <typename T>
+__global__ void k_coldots(const T *__restrict__ A, int64_t lda, const T *__restrict__ B, int64_t ldb, int ncols,
+                          int64_t npts, double *out) {
+    __shared__ double red[256];
+    const int rows = blockDim.x / ncols;
+    const int k = threadIdx.x % ncols, r = threadIdx.x / ncols;
+    double acc = 0.0, comp = 0.0;  // Kahan-compensated FP64 sum of exact products
+    if (r < rows) {
+        for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+            const double v = (double)A[p * lda + k] * (double)B[p * ldb + k];
+            const double y = v - comp;
+            const double t = acc + y;
+            comp = (t - acc) - y;
+            acc = t;
+        }
+    }
+    red[threadIdx.x] = r < rows ? acc : 0.0;
+    __syncthreads();
+    if (r == 0) {
+        double s = 0;
+        for (int q = 0; q < rows; ++q) s += red[q * ncols + k];
+        atomicAdd(out + k, s);
+    }
+}
+
+template <typename T>
+__global__ void k_residual(const T *__restrict__ X, int64_t ldx, const T *__restrict__ HX, int64_t ldh,
+                           const double *__restrict__ num, const double *__restrict__ den, T *__restrict__ R,
+                           int64_t ldr, int ncols, int64_t npts) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = t / ncols;
+    const int k = (int)(t % ncols);
+    if (p >= npts) return;
+    const T lam = (T)(num[k] / den[k]);
+    R[p * ldr + k] = HX[p * ldh + k] - lam * X[p * ldx + k];
+}
+
+__global__ void k_resnorm(const double *rr, int n, double dV, double *res) {
+    const int k = threadIdx.x;
+    if (k < n) res[k] = sqrt(dV * rr[k]);
+}
+
+template <typename T>
+__global__ void k_scale_cols(T *Y, int64_t ldy, int ncols, int64_t npts, const double *nrm2, double dV) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = t / ncols;
+    const int k = (int)(t % ncols);
+    if (p >= npts) return;
+    const double n2 = dV * nrm2[k];
+    if (n2 > 0) Y[p * ldy + k] = (T)((double)Y[p * ldy + k] / sqrt(n2));
+}
+
+template <typename T>
+__global__ void k_copy_cols(const T *__restrict__ S, int64_t lds, T *__restrict__ D, int64_t ldd, int ncols,
+                            int64_t npts) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = t / ncols;
+    const int k = (int)(t % ncols);
+    if (p >= npts) return;
+    D[p * ldd + k] = S[p * lds + k];
+}
+
+__global__ void k_copy_leading(const double *A, int lda, int n, double *B, int ldb) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x)
+        B[(e / n) * ldb + e % n] = A[(e / n) * lda + e % n];
+}
+
+}  // namespace rs
+
+struct rs_solver {
+    rs_ham *h = nullptr;
+    rs_solver_cfg cfg{};
+    int64_t npts = 0;
+    double dV = 0;
+    int es = 8;
+    int nblk = 0;
+    DevBuf psi, hpsi, P, Z, HZ, R, small, la, eig, res;
+    std::vector<char> has_p;
+    Precond *pc = nullptr;
+    // small FP64 buffers (inside `small`)
+    double *dots = nullptr, *M = nullptr, *G = nullptr, *A = nullptr, *U = nullptr, *Ui = nullptr, *T1 = nullptr,
+           *At = nullptr, *Yv = nullptr, *mu = nullptr, *C = nullptr;
+    int *status = nullptr;
+    void *eighw = nullptr;
+    ~rs_solver() { delete pc; }
+};
+
+namespace {
+
+template <typename T> struct Ops {
+    static int coldots(const void *A, int64_t lda, const void *B, int64_t ldb, int ncols, int64_t npts, double *out,
+                       cudaStream_t st) {
+        const int rows = 256 / ncols;
+        const int64_t need = (npts + rows - 1) / rows;
+        const unsigned blocks = (unsigned)std::min<int64_t>(need, 152 * 8);
+        k_coldots<T><<<blocks, 256, 0, st>>>((const T *)A, lda, (const T *)B, ldb, ncols, npts, out);
+        RS_LAUNCH_CHECK();
+        return RS_OK;
+    }
+};
+
+int coldots(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, int ncols, int64_t npts, double *out,
+            cudaStream_t st) {
+    RS_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * ncols, st));
+    if (dtype == RS_F64) return Ops<double>::coldots(A, lda, B, ldb, ncols, npts, out, st);
+    return Ops<float>::coldots(A, lda, B, ldb, ncols, npts, out, st);
+}
+
+unsigned elem_blocks(int64_t npts, int ncols) { return (unsigned)((npts * ncols + 255) / 256); }
+
+int copy_cols(int dtype, const void *S, int64_t lds, void *D, int64_t ldd, int ncols, int64_t npts, cudaStream_t st) {
+    if (dtype == RS_F64)
+        k_copy_cols<double><<<elem_blocks(npts, ncols), 256, 0, st>>>((const double *)S, lds, (double *)D, ldd, ncols, npts);
+    else
+        k_copy_cols<float><<<elem_blocks(npts, ncols), 256, 0, st>>>((const float *)S, lds, (float *)D, ldd, ncols, npts);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+int gram_any(int dtype, const void *X, int64_t ldx, int nx, const void *Y, int64_t ldy, int ny, int64_t npts, double dV,
+             double *S, int64_t lds, cudaStream_t st) {
+    if (dtype == RS_F64)
+        return gram<double>((const double *)X, ldx, nx, (const double *)Y, ldy, ny, npts, dV, S, lds, st);
+    return gram<float>((const float *)X, ldx, nx, (const float *)Y, ldy, ny, npts, dV, S, lds, st);
+}
+
+int rowmul_any(int dtype, const void *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, void *Y, int64_t ldy,
+               int64_t npts, double alpha, double beta, cudaStream_t st) {
+    if (dtype == RS_F64)
+        return rowmul<double>((const double *)X, ldx, n, C, ldc, m, (double *)Y, ldy, npts, alpha, beta, st);
+    return rowmul<float>((const float *)X, ldx, n, C, ldc, m, (float *)Y, ldy, npts, alpha, beta, st);
+}
+
+const char *off(const DevBuf &b, int64_t elems, int es) { return (const char *)b.p + (size_t)elems * es; }
+char *offw(DevBuf &b, int64_t elems, int es) { return (char *)b.p + (size_t)elems * es; }
+
+// One LOBPCG update of block b.  Blocking (reads the block's residuals and
+// the Cholesky status).
+int block_step(rs_solver *S, int b, cudaStream_t st) {
+    const rs_solver_cfg &c = S->cfg;
+    const int nb = c.nb, nst = c.nst, dt = c.dtype, es = S->es;
+    const int64_t np = S->npts;
+    const int64_t ldz = 3 * nb;
+    const void *X = off(S->psi, (int64_t)b * nb, es);
+    const void *HX = off(S->hpsi, (int64_t)b * nb, es);
+    double *num = S->dots, *den = S->dots + 64, *rr = S->dots + 128, *nrm = S->dots + 256;
+    // 1. Rayleigh quotients, residuals and their norms
+    RS_TRY(coldots(dt, X, nst, HX, nst, nb, np, num, st));
+    RS_TRY(coldots(dt, X, nst, X, nst, nb, np, den, st));
+    if (dt == RS_F64)
+        k_residual<double><<<elem_blocks(np, nb), 256, 0, st>>>((const double *)X, nst, (const double *)HX, nst, num,
+                                                                den, S->R.as<double>(), nb, nb, np);
+    else
+        k_residual<float><<<elem_blocks(np, nb), 256, 0, st>>>((const float *)X, nst, (const float *)HX, nst, num, den,
+                                                               S->R.as<float>(), nb, nb, np);
+    RS_LAUNCH_CHECK();
+    RS_TRY(coldots(dt, S->R.p, nb, S->R.p, nb, nb, np, rr, st));
+    double *resb = S->res.as<double>() + (size_t)b * nb;
+    k_resnorm<<<1, 64, 0, st>>>(rr, nb, S->dV, resb);
+    RS_LAUNCH_CHECK();
+    std::vector<double> res(nb);
+    RS_CUDA(cudaMemcpyAsync(res.data(), resb, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    bool conv = true;
+    for (double r : res) {
+        if (!std::isfinite(r)) return fail(RS_ENAN, "eigensolver: non-finite residual in block %d", b);
+        conv = conv && r <= c.tol;
+    }
+    if (conv) return RS_OK;
+
+    // 2. W = K R into Z[:, nb:2nb]; X, P_b, HX into Z / HZ
+    RS_TRY(S->pc->apply(S->h, S->R.p, nb, offw(S->Z, nb, es), ldz, nb, dt, st));
+    RS_TRY(copy_cols(dt, X, nst, S->Z.p, ldz, nb, np, st));
+    RS_TRY(copy_cols(dt, HX, nst, S->HZ.p, ldz, nb, np, st));
+    const bool use_p = S->has_p[b] != 0;
+    if (use_p) RS_TRY(copy_cols(dt, off(S->P, (int64_t)b * nb, es), nst, offw(S->Z, 2 * nb, es), ldz, nb, np, st));
+    const int ny = use_p ? 2 * nb : nb;
+    void *Y = offw(S->Z, nb, es);
+
+    // 3. classical Gram-Schmidt, twice, against Psi[:, :(b+1) nb]
+    const int nq = (b + 1) * nb;
+    for (int pass = 0; pass < 2; ++pass) {
+        RS_TRY(gram_any(dt, S->psi.p, nst, nq, Y, ldz, ny, np, S->dV, S->M, ny, st));
+        RS_TRY(rowmul_any(dt, S->psi.p, nst, nq, S->M, ny, ny, Y, ldz, np, -1.0, 1.0, st));
+    }
+    RS_TRY(coldots(dt, Y, ldz, Y, ldz, ny, np, nrm, st));
+    if (dt == RS_F64)
+        k_scale_cols<double><<<elem_blocks(np, ny), 256, 0, st>>>((double *)Y, ldz, ny, np, nrm, S->dV);
+    else
+        k_scale_cols<float><<<elem_blocks(np, ny), 256, 0, st>>>((float *)Y, ldz, ny, np, nrm, S->dV);
+    RS_LAUNCH_CHECK();
+
+    // 4. H Y
+    RS_TRY(rs_ham_apply_block(S->h, Y, ldz, offw(S->HZ, nb, es), ldz, nb, dt, st));
+    if (use_p) RS_TRY(rs_ham_apply_block(S->h, offw(S->Z, 2 * nb, es), ldz, offw(S->HZ, 2 * nb, es), ldz, nb, dt, st));
+
+    // 5. Rayleigh-Ritz on Z = [X, Y]
+    int n = nb + ny;
+    RS_TRY(gram_any(dt, S->Z.p, ldz, n, S->Z.p, ldz, n, np, S->dV, S->G, n, st));
+    RS_TRY(gram_any(dt, S->Z.p, ldz, n, S->HZ.p, ldz, n, np, S->dV, S->A, n, st));
+    RS_TRY(symmetrize(S->G, n, n, st));
+    RS_TRY(symmetrize(S->A, n, n, st));
+    int bad = 1;
+    for (int attempt = 0; attempt < 2 && bad; ++attempt) {
+        if (attempt == 1) {
+            if (n == 2 * nb) break;
+            n = 2 * nb;  // drop P
+        }
+        k_copy_leading<<<64, 256, 0, st>>>(S->G, nb + ny, n, S->U, n);
+        RS_LAUNCH_CHECK();
+        RS_TRY(cholesky(S->U, n, n, 1e-12, S->status, st));
+        RS_CUDA(cudaMemcpyAsync(&bad, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+    }
+    if (bad) return RS_OK;  // no usable search space this sweep; the block keeps X
+    const int lda = nb + ny;
+    RS_TRY(tri_inv(S->U, n, n, S->Ui, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, S->Ui, n, true, S->A, lda, false, 0.0, S->T1, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, S->T1, n, false, S->Ui, n, false, 0.0, S->At, n, st));
+    RS_TRY(symmetrize(S->At, n, n, st));
+    RS_TRY(eigh(S->At, n, n, S->mu, S->Yv, n, 3, S->status, S->eighw, st));
+    RS_TRY(gemm_small(n, nb, n, 1.0, S->Ui, n, false, S->Yv, n, false, 0.0, S->C, nb, st));
+
+    // 6. X <- Z C, P <- Z[:, nb:n] C[nb:n, :]
+    RS_TRY(rowmul_any(dt, S->Z.p, ldz, n, S->C, nb, nb, offw(S->psi, (int64_t)b * nb, es), nst, np, 1.0, 0.0, st));
+    RS_TRY(rowmul_any(dt, offw(S->Z, nb, es), ldz, n - nb, S->C + (size_t)nb * nb, nb, nb,
+                      offw(S->P, (int64_t)b * nb, es), nst, np, 1.0, 0.0, st));
+    S->has_p[b] = 1;
+    return RS_OK;
+}
+
+}  // namespace
+
+extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void *Psi0_dev, void *stream,
+                                rs_solver **out) {
+    if (!h || !cfg || !Psi0_dev || !out) return fail(RS_EINVAL, "rs_solver_create: null argument");
+    const rs_solver_cfg c = *cfg;
+    if (c.nb < 1 || c.nb > 64 || (c.nb & (c.nb - 1))) return fail(RS_EINVAL, "rs_solver_create: nb must be a power of two <= 64");
+    if (c.nst < c.nb || c.nst % c.nb) return fail(RS_EINVAL, "rs_solver_create: nst must be a multiple of nb");
+    if (c.dtype != RS_F64 && c.dtype != RS_F32) return fail(RS_EINVAL, "rs_solver_create: bad dtype");
+    if (c.precond < RS_PRECOND_NONE || c.precond > RS_PRECOND_LEARNED) return fail(RS_EINVAL, "rs_solver_create: bad precond");
+    if (!(c.tol > 0)) return fail(RS_EINVAL, "rs_solver_create: tol must be > 0");
+    *out = nullptr;
+    rs_solver *S = new (std::nothrow) rs_solver;
+    if (!S) return fail(RS_ENOMEM, "host allocation failed");
+    auto bail = [&](int rc) {
+        delete S;
+        return rc;
+    };
+    S->h = h;
+    S->cfg = c;
+    S->npts = ham_npts(h);
+    S->dV = ham_dV(h);
+    S->es = c.dtype == RS_F64 ? 8 : 4;
+    S->nblk = c.nst / c.nb;
+    S->has_p.assign(S->nblk, 0);
+    const size_t big = (size_t)S->npts * c.nst * S->es, zb = (size_t)S->npts * 3 * c.nb * S->es;
+    int rc;
+    if ((rc = S->psi.alloc(big)) || (rc = S->hpsi.alloc(big)) || (rc = S->P.alloc(big)) || (rc = S->Z.alloc(zb)) ||
+        (rc = S->HZ.alloc(zb)) || (rc = S->R.alloc((size_t)S->npts * c.nb * S->es)) ||
+        (rc = S->la.alloc(LaWork::bytes(c.nst))) || (rc = S->eig.alloc(sizeof(double) * c.nst)) ||
+        (rc = S->res.alloc(sizeof(double) * c.nst)))
+        return bail(rc);
+    const int n3 = 3 * c.nb;
+    const size_t smallbytes = sizeof(double) * (512 + (size_t)c.nst * 2 * c.nb + 7 * (size_t)n3 * n3 + n3 + (size_t)n3 * c.nb) +
+                              64 + eigh_work_bytes(n3);
+    if ((rc = S->small.alloc(smallbytes))) return bail(rc);
+    double *d = S->small.as<double>();
+    S->dots = d;
+    S->M = d + 512;
+    S->G = S->M + (size_t)c.nst * 2 * c.nb;
+    S->A = S->G + (size_t)n3 * n3;
+    S->U = S->A + (size_t)n3 * n3;
+    S->Ui = S->U + (size_t)n3 * n3;
+    S->T1 = S->Ui + (size_t)n3 * n3;
+    S->At = S->T1 + (size_t)n3 * n3;
+    S->Yv = S->At + (size_t)n3 * n3;
+    S->mu = S->Yv + (size_t)n3 * n3;
+    S->C = S->mu + n3;
+    S->status = reinterpret_cast<int *>(S->C + (size_t)n3 * c.nb);
+    S->eighw = reinterpret_cast<void *>(S->C + (size_t)n3 * c.nb + 8);
+    S->pc = Precond::create(c.precond, c.filter_alpha);
+    if (!S->pc) return bail(fail(RS_EINVAL, "rs_solver_create: preconditioner %d unavailable", c.precond));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(S->psi.p, Psi0_dev, big, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(S->P.p, 0, big, st) != cudaSuccess || cudaMemsetAsync(S->res.p, 0, sizeof(double) * c.nst, st) != cudaSuccess)
+        return bail(fail(RS_ECUDA, "rs_solver_create: copy failed"));
+    if ((rc = orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st))) return bail(rc);
+    if ((rc = subspace_diag_impl(h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st)))
+        return bail(rc);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(RS_ECUDA, "rs_solver_create: sync failed"));
+    *out = S;
+    return RS_OK;
+}
+
+extern "C" int rs_eigensolver_step(rs_solver *S, double *eps_dev, double *resnorm_dev, int *n_converged, void *stream) {
+    if (!S) return fail(RS_EINVAL, "rs_eigensolver_step: null solver");
+    cudaStream_t st = (cudaStream_t)stream;
+    const rs_solver_cfg &c = S->cfg;
+    for (int b = 0; b < S->nblk; ++b) RS_TRY(block_step(S, b, st));
+    RS_TRY(orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st));
+    LaWork w(S->la.p, c.nst);
+    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.Ui, S->npts, c.dtype, st));
+    RS_TRY(subspace_diag_impl(S->h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st));
+    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.xi, S->npts, c.dtype, st));
+    if (eps_dev) RS_CUDA(cudaMemcpyAsync(eps_dev, S->eig.p, sizeof(double) * c.nst, cudaMemcpyDeviceToDevice, st));
+    if (resnorm_dev) RS_CUDA(cudaMemcpyAsync(resnorm_dev, S->res.p, sizeof(double) * c.nst, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> res(c.nst);
+    RS_CUDA(cudaMemcpyAsync(res.data(), S->res.p, sizeof(double) * c.nst, cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    if (n_converged) {
+        int k = 0;
+        for (double r : res) k += r <= c.tol;
+        *n_converged = k;
+    }
+    return RS_OK;
+}
+
+extern "C" int rs_solver_psi(rs_solver *S, void **psi_dev) {
+    if (!S || !psi_dev) return fail(RS_EINVAL, "rs_solver_psi: null argument");
+    *psi_dev = S->psi.p;
+    return RS_OK;
+}
+
+extern "C" int rs_solver_set_precond_weights(rs_solver *S, const float *w1, const float *w2, const float *w3) {
+    if (!S || !w1 || !w2 || !w3) return fail(RS_EINVAL, "rs_solver_set_precond_weights: null argument");
+    return S->pc->set_weights(w1, w2, w3);
+}
+
+extern "C" int rs_solver_destroy(rs_solver *S) {
+    delete S;
+    return RS_OK;
+}

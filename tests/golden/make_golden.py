@@ -1,0 +1,75 @@
+"""Writes the oracle's reference eigenvalues used by the GPU eigensolver tests
+and the benchmark's time-to-accuracy measurement.
+
+    python tests/golden/make_golden.py ho32_h0.3 mol20_h0.35 [mol100_h0.3 ...]
+
+Calls only the FP64 CPU oracle (``oracle/``) on the seeded synthetic
+workloads of ``workloads``: block CG from the workload's random start
+vectors, converged to a residual norm of 1e-9 (eigenvalue error ~1e-18
+times the inverse gap), plus, for the harmonic oscillator, the separable
+closed form.  Output: tests/golden/eigs_<workload>.json.
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+from oracle import eigensolver, grid as og, hamiltonian as oh  # noqa: E402
+from oracle.stencil import fd_weights  # noqa: E402
+
+
+def build(w: wl.Workload):
+    s = w.system
+    if isinstance(s, wl.BoxSpec):
+        g = og.box_grid(s.n, s.h)
+        return g, oh.Hamiltonian(g, wl.harmonic_potential(g.coords, s.omega))
+    atoms = wl.atom_positions(s)
+    g = og.sphere_union_grid(atoms, s.radius, s.h)
+    pr = oh.make_projectors(g, atoms, wl.kb_couplings(s), s.r_c, s.r_cut)
+    return g, oh.Hamiltonian(g, wl.local_potential(g.coords, atoms), pr)
+
+
+def separable_levels(s: wl.BoxSpec, k: int) -> list[float]:
+    c = fd_weights(4)
+    x = (np.arange(s.n) - (s.n - 1) / 2) * s.h
+    T = np.zeros((s.n, s.n))
+    for i in range(s.n):
+        for j in range(-4, 5):
+            if 0 <= i + j < s.n:
+                T[i, i + j] += -0.5 * c[abs(j)] / s.h ** 2
+    e = np.linalg.eigvalsh(T + np.diag(0.5 * s.omega ** 2 * x ** 2))
+    return sorted((e[:, None, None] + e[None, :, None] + e[None, None, :]).ravel())[:k]
+
+
+def main(names):
+    for name in names:
+        w = wl.WORKLOADS[name]
+        g, H = build(w)
+        t0 = time.time()
+        psi0 = wl.random_block(g.npts, w.n_states, w.seed)
+        log = []
+        solver = eigensolver.BlockCG(H, psi0, w.block, tol=1e-9)
+        eps = solver.solve(max_iter=3000, judged=w.judged,
+                           callback=lambda s: log.append(float(np.max(s.resnorm[:w.judged]))))
+        out = {"workload": name, "npts": g.npts, "n_states": w.n_states, "judged": w.judged,
+               "eigenvalues": [float(v) for v in eps], "residual_tol": 1e-9, "iterations": solver.iterations,
+               "max_residual": float(np.max(solver.resnorm[:w.judged])), "cpu_seconds": time.time() - t0,
+               "source": "oracle/eigensolver.py BlockCG (FP64), written by tests/golden/make_golden.py"}
+        if isinstance(w.system, wl.BoxSpec):
+            out["separable_closed_form"] = [float(v) for v in separable_levels(w.system, w.judged)]
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"eigs_{name}.json")
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+        print(name, g.npts, solver.iterations, f"{time.time() - t0:.1f}s", out["max_residual"])
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
