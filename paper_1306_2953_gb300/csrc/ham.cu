@@ -20,23 +20,23 @@
 // grid points are addressed through the int32 point map (Sec. V.A).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <new>
 #include <utility>
 #include <vector>
 
 #include "device.h"
+#include "ham.h"
 
 #ifndef RS_STENCIL_MINB_F32
-#define RS_STENCIL_MINB_F32 2
+#define RS_STENCIL_MINB_F32 1
 #endif
 
 namespace rs {
 
-// Planes beyond the queue's next entry whose rows are prefetched into L2.
-constexpr int PF_DIST = 4;
-
 template <typename T> struct HamDev {
+    const int4 *pinfo;  // per point: nonlocal entry range [x, y) and V (z: float bits; z,w: double bits)
     const int32_t *map;
     int d0, d1, d2;
     const T *V;
@@ -50,6 +50,10 @@ template <typename T> struct HamDev {
 };
 
 // ---------------------------------------------------------------- helpers --
+
+template <typename T> __device__ __forceinline__ T point_v(int4 inf);
+template <> __device__ __forceinline__ float point_v<float>(int4 inf) { return __int_as_float(inf.z); }
+template <> __device__ __forceinline__ double point_v<double>(int4 inf) { return __hiloint2double(inf.w, inf.z); }
 
 template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -121,6 +125,9 @@ __global__ void __launch_bounds__(NT) k_project(HamDev<T> d, const T *__restrict
 
 // ------------------------------------------- fused stencil + V + nonlocal ---
 
+// Maximum number of planes of one work item (the z chunk).
+constexpr int ZCHUNK = 32;
+
 template <typename T, int SG, int TX, int TY> struct StencilCfg {
     static constexpr int W2 = TX + 8, W1 = TY + 8;
     static constexpr int PLANE = W1 * W2 * SG;
@@ -130,7 +137,11 @@ template <typename T, int SG, int TX, int TY> struct StencilCfg {
     static constexpr int CHE = CHB / (int)sizeof(T);
     static constexpr int CPR = SG / CHE;
     static constexpr int NH = 8 * TY + 8 * TX;
-    static constexpr size_t SMEM = (size_t)RING * PLANE * sizeof(T);
+    static constexpr int HPT = (NH * CPR + NT - 1) / NT;     // halo copies per thread and plane
+    static constexpr int NI = TX * TY;
+    static constexpr bool STAGE = NI <= 128;                  // stage interior rows in shared memory
+    static constexpr int NROW = STAGE ? (ZCHUNK + 9) * NI : 0;
+    static constexpr size_t SMEM = (size_t)RING * PLANE * sizeof(T) + (size_t)NROW * sizeof(int);
     static constexpr int MINB = sizeof(T) == 4 ? RS_STENCIL_MINB_F32 : 1;
 };
 
@@ -141,6 +152,7 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
     using C = StencilCfg<T, SG, TX, TY>;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
+    int *rows = reinterpret_cast<int *>(smraw + (size_t)C::RING * C::PLANE * sizeof(T));
 
     const int tid = threadIdx.x;
     const int s = tid % SG;
@@ -158,28 +170,58 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
             return -1;
         return __ldg(d.map + ((int64_t)a0 * d.d1 + a1) * d.d2 + a2);
     };
+    // interior point rows of planes za-4 .. zb+4, staged once per work item
+    if constexpr (C::STAGE) {
+        const int nrow = (zb - za + 9) * C::NI;
+        for (int e = tid; e < nrow; e += C::NT) {
+            const int pl = e / C::NI, pos = e % C::NI;
+            rows[e] = map_at(za - 4 + pl, b1 + pos / TX, b2 + pos % TX);
+        }
+    }
+    auto row_of = [&](int z, int iy, int ix) -> int {
+        if constexpr (C::STAGE) return rows[(z - za + 4) * C::NI + iy * TX + ix];
+        return map_at(z, b1 + iy, b2 + ix);
+    };
     auto load_val = [&](int r) -> T { return r >= 0 ? __ldg(psig + (int64_t)r * ldp + s) : T(0); };
-    auto issue_halo = [&](int z, int slot) {
-        T *base = sm + slot * C::PLANE;
-        for (int i = tid; i < C::NH * C::CPR; i += C::NT) {
-            const int hh = i / C::CPR, c = i % C::CPR;
-            int hy, hx;
-            if (hh < 8 * TY) {
-                hy = hh >> 3;
-                const int t = hh & 7;
-                hx = t < 4 ? t - 4 : TX + t - 4;
-            } else {
-                const int h2 = hh - 8 * TY;
-                hx = h2 % TX;
-                const int t = h2 / TX;
-                hy = t < 4 ? t - 4 : TY + t - 4;
-            }
-            const int r = map_at(z, b1 + hy, b2 + hx);
-            T *dst = base + ((hy + 4) * C::W2 + (hx + 4)) * SG + c * C::CHE;
-            const T *src = r >= 0 ? psig + (int64_t)r * ldp + c * C::CHE : psig;
-            cp_async<C::CHB>(dst, src, r >= 0);
+
+    // this thread's halo copies j < HPT: copy index i = tid + j NT -> (hy, hx, chunk)
+    auto halo_pos = [&](int i, int &hy, int &hx, int &c) {
+        const int hh = i / C::CPR;
+        c = i % C::CPR;
+        if (hh < 8 * TY) {
+            hy = hh >> 3;
+            const int t = hh & 7;
+            hx = t < 4 ? t - 4 : TX + t - 4;
+        } else {
+            const int h2 = hh - 8 * TY;
+            hx = h2 % TX;
+            const int t = h2 / TX;
+            hy = t < 4 ? t - 4 : TY + t - 4;
         }
     };
+    int hr[C::HPT];
+    auto halo_rows = [&](int z) {
+#pragma unroll
+        for (int j = 0; j < C::HPT; ++j) {
+            const int i = tid + j * C::NT;
+            int hy, hx, c;
+            halo_pos(i, hy, hx, c);
+            hr[j] = i < C::NH * C::CPR ? map_at(z, b1 + hy, b2 + hx) : -1;
+        }
+    };
+    auto issue_halo = [&](int slot) {
+        T *base = sm + slot * C::PLANE;
+#pragma unroll
+        for (int j = 0; j < C::HPT; ++j) {
+            const int i = tid + j * C::NT;
+            if (i >= C::NH * C::CPR) continue;
+            int hy, hx, c;
+            halo_pos(i, hy, hx, c);
+            const T *src = hr[j] >= 0 ? psig + (int64_t)hr[j] * ldp + c * C::CHE : psig;
+            cp_async<C::CHB>(base + ((hy + 4) * C::W2 + (hx + 4)) * SG + c * C::CHE, src, hr[j] >= 0);
+        }
+    };
+    __syncthreads();
 
     T q[2][2][9];
 #pragma unroll
@@ -187,34 +229,28 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx) q[dy][dx][k] = load_val(map_at(za - 4 + k, b1 + ly + dy, b2 + lx + dx));
+            for (int dx = 0; dx < 2; ++dx) q[dy][dx][k] = load_val(row_of(za - 4 + k, ly + dy, lx + dx));
 
-    issue_halo(za, 0);
+    halo_rows(za);
+    issue_halo(0);
     cp_async_commit();
-    if (za + 1 < zb) issue_halo(za + 1, 1);
+    halo_rows(za + 1);
+    if (za + 1 < zb) issue_halo(1);
     cp_async_commit();
+    halo_rows(za + 2);
 
     const T w0 = d.w[0], w1 = d.w[1], w2 = d.w[2], w3 = d.w[3], w4 = d.w[4];
     int slot = 0;
     for (int z = za; z < zb; ++z) {
         const int pslot = slot == 0 ? 2 : slot - 1;  // (slot + 2) % 3
-        if (z + 2 < zb) issue_halo(z + 2, pslot);
+        if (z + 2 < zb) issue_halo(pslot);
         cp_async_commit();
 
         T nq[2][2];
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx) nq[dy][dx] = load_val(map_at(z + 5, b1 + ly + dy, b2 + lx + dx));
-        if (s == 0) {
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int r = map_at(z + 5 + PF_DIST, b1 + ly + dy, b2 + lx + dx);
-                    if (r >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(psig + (int64_t)r * ldp));
-                }
-        }
+            for (int dx = 0; dx < 2; ++dx) nq[dy][dx] = load_val(row_of(z + 5, ly + dy, lx + dx));
 
         T *P = sm + slot * C::PLANE;
 #pragma unroll
@@ -267,11 +303,11 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const int r = map_at(z, b1 + ly + dy, b2 + lx + dx);
+                const int r = row_of(z, ly + dy, lx + dx);
                 if (r < 0) continue;
-                T out = acc[dy][dx] + __ldg(d.V + r) * q[dy][dx][4];
-                const int e0 = __ldg(d.cov_off + r), e1 = __ldg(d.cov_off + r + 1);
-                for (int e = e0; e < e1; ++e) {
+                const int4 inf = __ldg(d.pinfo + r);
+                T out = acc[dy][dx] + point_v<T>(inf) * q[dy][dx][4];
+                for (int e = inf.x; e < inf.y; ++e) {
                     const int A = __ldg(d.cov_atom + e);
                     const Four<T> g = load4(d.cov_gam + 4 * (int64_t)e);
                     const T *cp = cproj + (int64_t)A * 4 * nb + sg0 + s;
@@ -288,10 +324,34 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
                 for (int k = 0; k < 8; ++k) q[dy][dx][k] = q[dy][dx][k + 1];
                 q[dy][dx][8] = nq[dy][dx];
             }
+        halo_rows(z + 3);
         slot = slot == 2 ? 0 : slot + 1;
         __syncthreads();
     }
     cp_async_wait<0>();
+}
+
+// ----------------------------------------------- face-neighbour filter ---
+// W = alpha R + beta sum_{6 face neighbours} R (zero off the grid); one thread
+// per (point, state), state fastest.
+template <typename T>
+__global__ void k_filter(const int32_t *__restrict__ map, const int32_t *__restrict__ loc, int64_t npts, int d1, int d2,
+                         const T *__restrict__ R, int64_t ldr, T *__restrict__ W, int64_t ldw, int nb, T alpha,
+                         T beta) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = t / nb;
+    const int s = (int)(t % nb);
+    if (p >= npts) return;
+    const int64_t L = __ldg(loc + p);
+    const int64_t plane = (int64_t)d1 * d2;
+    const int64_t offs[6] = {1, -1, d2, -(int64_t)d2, plane, -plane};
+    T acc = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int q = __ldg(map + L + offs[k]);
+        if (q >= 0) acc += __ldg(R + (int64_t)q * ldr + s);
+    }
+    W[p * ldw + s] = alpha * __ldg(R + p * ldr + s) + beta * acc;
 }
 
 }  // namespace rs
@@ -312,7 +372,7 @@ struct Shape {
     int sg, tx, ty;
 };
 const Shape kShapes[] = {{32, 8, 8}, {16, 16, 8}, {8, 16, 16}, {4, 32, 16}, {2, 32, 32}, {1, 64, 32}};
-const int kZChunk = 32;
+const int kZChunk = ZCHUNK;
 
 }  // namespace
 
@@ -325,7 +385,7 @@ struct rs_ham {
     int64_t n_entries = 0;
     int device = 0;
     double w[5] = {0, 0, 0, 0, 0};
-    DevBuf map, V64, V32, cov_off, cov_atom, cov_gam64, cov_gam32, sph_off, sph_idx, sph_gam64, sph_gam32, E64, E32,
+    DevBuf pinfo64, pinfo32, map, loc, V64, V32, cov_off, cov_atom, cov_gam64, cov_gam32, sph_off, sph_idx, sph_gam64, sph_gam32, E64, E32,
         cproj, dummy;
     std::map<std::pair<int, int>, WorkList *> work;
     // optional per-launch timing (rs_ham_timing)
@@ -353,6 +413,7 @@ struct rs_ham {
 
 template <> HamDev<double> rs_ham::view<double>() const {
     HamDev<double> v;
+    v.pinfo = pinfo64.as<int4>();
     v.map = map.as<int32_t>();
     v.d0 = d[0], v.d1 = d[1], v.d2 = d[2];
     v.V = V64.as<double>();
@@ -369,6 +430,7 @@ template <> HamDev<double> rs_ham::view<double>() const {
 }
 template <> HamDev<float> rs_ham::view<float>() const {
     HamDev<float> v;
+    v.pinfo = pinfo32.as<int4>();
     v.map = map.as<int32_t>();
     v.d0 = d[0], v.d1 = d[1], v.d2 = d[2];
     v.V = V32.as<float>();
@@ -456,6 +518,13 @@ extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_pr
     int rc;
     const int64_t np = g->npts;
     if ((rc = H->map.upload(g->map.data(), g->map.size() * sizeof(int32_t)))) return bail(rc);
+    {
+        std::vector<int32_t> loc((size_t)g->npts);
+        for (int64_t p = 0; p < g->npts; ++p)
+            loc[p] = (int32_t)(((int64_t)(g->ijk[3 * p] - g->origin[0]) * g->dims[1] + (g->ijk[3 * p + 1] - g->origin[1])) *
+                                   g->dims[2] + (g->ijk[3 * p + 2] - g->origin[2]));
+        if ((rc = H->loc.upload(loc.data(), loc.size() * sizeof(int32_t)))) return bail(rc);
+    }
     std::vector<float> v32((size_t)np);
     for (int64_t p = 0; p < np; ++p) v32[p] = (float)V_host[p];
     if ((rc = H->V64.upload(V_host, (size_t)np * sizeof(double)))) return bail(rc);
@@ -495,6 +564,20 @@ extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_pr
         (rc = H->cov_gam32.upload(cg32.data(), cg32.size() * 4)))
         return bail(rc);
     if ((rc = H->cproj.alloc((size_t)std::max(na, 1) * 4 * 64 * sizeof(double)))) return bail(rc);
+    {
+        std::vector<int4> p64((size_t)np), p32((size_t)np);
+        for (int64_t p = 0; p < np; ++p) {
+            int64_t bits;
+            memcpy(&bits, &V_host[p], 8);
+            int32_t fbits;
+            memcpy(&fbits, &v32[p], 4);
+            p64[p] = make_int4(coff[p], coff[p + 1], (int32_t)(bits & 0xffffffffll), (int32_t)(bits >> 32));
+            p32[p] = make_int4(coff[p], coff[p + 1], fbits, 0);
+        }
+        if ((rc = H->pinfo64.upload(p64.data(), p64.size() * sizeof(int4))) ||
+            (rc = H->pinfo32.upload(p32.data(), p32.size() * sizeof(int4))))
+            return bail(rc);
+    }
     for (const Shape &s : kShapes)
         if ((rc = build_work(H, g, s.tx, s.ty))) return bail(rc);
     *out = H;
@@ -623,3 +706,25 @@ extern "C" int rs_ham_timing_read(rs_ham *h, double *project_ms, double *stencil
     if (calls) *calls = (int64_t)h->n_recorded;
     return RS_OK;
 }
+
+namespace rs {
+
+int64_t ham_npts(const rs_ham *h) { return h->npts; }
+double ham_dV(const rs_ham *h) { return h->dV; }
+
+int ham_filter(const rs_ham *h, const void *R, int64_t ldr, void *W, int64_t ldw, int nb, int dtype, double alpha,
+               cudaStream_t st) {
+    const int64_t n = h->npts * nb;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const double beta = (1.0 - alpha) / 6.0;
+    if (dtype == RS_F64)
+        k_filter<double><<<blocks, 256, 0, st>>>(h->map.as<int32_t>(), h->loc.as<int32_t>(), h->npts, h->d[1], h->d[2],
+                                                 (const double *)R, ldr, (double *)W, ldw, nb, alpha, beta);
+    else
+        k_filter<float><<<blocks, 256, 0, st>>>(h->map.as<int32_t>(), h->loc.as<int32_t>(), h->npts, h->d[1], h->d[2],
+                                                (const float *)R, ldr, (float *)W, ldw, nb, (float)alpha, (float)beta);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+}  // namespace rs
