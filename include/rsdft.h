@@ -229,13 +229,69 @@ int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void *Psi0_dev, 
  * <= tol (may be NULL).  Blocking (reads the convergence count). */
 int rs_eigensolver_step(rs_solver *s, double *eps_dev, double *resnorm_dev, int *n_converged, void *stream);
 
+/* ------------------------------------------------ learned preconditioner --
+ * Not in the paper (its preconditioner is the filter of Sec. III).  The
+ * network maps a residual r to y = L3(relu(L2(relu(L1(r/rms(r)))))) * rms(r)
+ * with bias-free 3^3 lattice cross-correlations 1 -> 8 -> 8 -> 1, every
+ * layer's output zero off the grid, inputs stored in BF16, weights used in
+ * BF16 (rounded from an FP32 master copy) and FP32 accumulation.  Weights:
+ * one FP32 array of 2160 values, [8][1][27] | [8][8][27] | [1][8][27], tap
+ * t = 9 (a+1) + 3 (b+1) + (c+1) for the lattice offset (a, b, c) along the
+ * point-map axes. */
+
+/* Workspace bytes of rs_shifted_poisson_cg. */
+int64_t rs_cg_workspace_bytes(int64_t npts, int ncols, int dtype);
+
+/* Training targets: exactly n_iter conjugate-gradient iterations from X = 0
+ * on (-1/2 Lap + sigma) X = B, one independent system per column.  h must be
+ * a Hamiltonian built with V = sigma everywhere and no projectors; B_dev, X_dev
+ * [npts][ld] (ncols columns, a power of two <= 64).  Asynchronous. */
+int rs_shifted_poisson_cg(rs_ham *h, const void *B_dev, void *X_dev, int64_t ld, int ncols, int n_iter, int dtype,
+                          void *work_dev, void *stream);
+
+/* The network on dense D^3 tiles (training-side kernels): y = network(x)
+ * with x rounded to BF16 and zero outside mask; when grad_dev or loss_host is
+ * given, loss = sum over valid-and-mask points of (y - target)^2 / count and
+ * grad_dev = d loss / d w (FP32 [2160]).
+ *   w_dev [2160] FP32 master weights; x_dev, target_dev, y_dev [ntiles][D^3]
+ *   FP32; mask_dev [ntiles][D^3] and valid_dev [D^3] bytes (0/1).
+ * Blocking. */
+int rs_convnet_tiles(const float *w_dev, const float *x_dev, const uint8_t *mask_dev, const float *target_dev,
+                     const uint8_t *valid_dev, int ntiles, int D, float *y_dev, float *grad_dev, double *loss_host,
+                     void *stream);
+
+/* W = K R on the grid for nb FP32 residual columns (R, W [npts][ld]) with
+ * the network weights w_dev (FP32 master copy, rounded to BF16 here).
+ * Uses device memory owned by h for activations (held until h is destroyed,
+ * grown on demand).  Asynchronous.  The solver applies the same kernels. */
+int rs_precond_apply(rs_ham *h, const float *w_dev, const float *R_dev, int64_t ldr, float *W_dev, int64_t ldw, int nb,
+                     void *stream);
+
+typedef struct {
+    int n_tiles;     /* training tiles cut from the (residual, target) columns */
+    int tile;        /* interior edge (16); tiles carry 3 more points of halo */
+    int epochs;
+    int batch;       /* tiles per Adam step */
+    float lr;        /* Adam learning rate (1e-3) */
+    uint64_t seed;   /* tile positions (splitmix64) */
+} rs_train_cfg;
+
+/* Trains the network on tiles cut around random grid points of the column
+ * pairs (R, X) (FP32 [npts][ld], ncols columns: residuals and their CG
+ * solutions), inputs and targets scaled by the residual's rms.  w_dev holds
+ * the initial FP32 master weights and receives the trained ones; loss_host
+ * (may be NULL) receives the mean loss of every epoch.  Blocking. */
+int rs_precond_train(rs_ham *h, const rs_grid *g, const float *R_dev, const float *X_dev, int64_t ld, int ncols,
+                     const rs_train_cfg *cfg, float *w_dev, float *loss_host, void *stream);
+
 /* The solver's current orbitals: device [npts][nst] (dtype), owned by the
  * solver; valid until rs_solver_destroy. */
 int rs_solver_psi(rs_solver *s, void **psi_dev);
 
-/* Learned-preconditioner weights (FP32 master copy, layouts [8][1][27],
- * [8][8][27], [1][8][27]); device pointers.  Used by RS_PRECOND_LEARNED. */
-int rs_solver_set_precond_weights(rs_solver *s, const float *w1_dev, const float *w2_dev, const float *w3_dev);
+/* Weights of the learned preconditioner (RS_PRECOND_LEARNED, FP32 F32-mode
+ * solvers only): w_dev is the 2160-value FP32 array described above (copied).
+ * Until weights are set the learned preconditioner refuses to run. */
+int rs_solver_set_precond_weights(rs_solver *s, const float *w_dev);
 
 int rs_solver_destroy(rs_solver *s);
 

@@ -31,6 +31,11 @@ class ProjectorSpec(ctypes.Structure):
                 ("r_c", ctypes.c_double), ("r_cut", ctypes.c_double)]
 
 
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("n_tiles", ctypes.c_int), ("tile", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 class SolverCfg(ctypes.Structure):
     _fields_ = [("nst", ctypes.c_int), ("nb", ctypes.c_int), ("dtype", ctypes.c_int), ("precond", ctypes.c_int),
                 ("tol", ctypes.c_double), ("filter_alpha", ctypes.c_double)]
@@ -69,7 +74,12 @@ SIGNATURES = {
     "rs_solver_create": (None, [P, ctypes.POINTER(SolverCfg), P, P, PP]),
     "rs_eigensolver_step": (None, [P, P, P, P, P]),
     "rs_solver_psi": (None, [P, PP]),
-    "rs_solver_set_precond_weights": (None, [P, P, P, P]),
+    "rs_solver_set_precond_weights": (None, [P, P]),
+    "rs_cg_workspace_bytes": (I64, [I64, I32, I32]),
+    "rs_shifted_poisson_cg": (None, [P, P, P, I64, I32, I32, I32, P, P]),
+    "rs_precond_apply": (None, [P, P, P, I64, P, I64, I32, P]),
+    "rs_convnet_tiles": (None, [P, P, P, P, P, I32, I32, P, P, P, P]),
+    "rs_precond_train": (None, [P, P, P, P, I64, I32, ctypes.POINTER(TrainCfg), P, P, P]),
     "rs_solver_destroy": (None, [P]),
 }
 

@@ -285,3 +285,51 @@ def _device_view(ptr: int, shape, dtype, device):
     typestr = "<f8" if es == 8 else "<f4"
     strides = (shape[1] * es, es)
     return torch.as_tensor(_Holder(ptr, shape, typestr, strides), device=device)
+
+
+def shifted_poisson_cg(ham_sigma: Hamiltonian, B, n_iter: int = 200, stream=None):
+    """n_iter CG iterations on (-1/2 Lap + sigma) X = B per column (ham_sigma
+    built with V = sigma and no projectors); returns X."""
+    import torch
+    X = torch.empty_like(B)
+    nb = B.shape[1]
+    nbytes = int(_lib.lib().rs_cg_workspace_bytes(B.shape[0], nb, dtype_code(B)))
+    work = torch.empty(nbytes, dtype=torch.uint8, device=B.device)
+    call("rs_shifted_poisson_cg", ham_sigma._h, _c(B.data_ptr()), _c(X.data_ptr()), B.stride(0), nb, n_iter,
+         dtype_code(B), _c(work.data_ptr()), _stream(stream))
+    return X
+
+
+def convnet_tiles(w, x, mask, target=None, valid=None, grad=True, stream=None):
+    """The conv net on dense tiles [ntiles, D, D, D]; returns (y, grad, loss)."""
+    import torch
+    ntiles, D = x.shape[0], x.shape[1]
+    y = torch.empty_like(x)
+    g = torch.empty(2160, dtype=torch.float32, device=x.device) if grad else None
+    loss = ctypes.c_double(0.0)
+    want_loss = target is not None
+    call("rs_convnet_tiles", _c(w.data_ptr()), _c(x.data_ptr()), _c(mask.data_ptr()),
+         _c(target.data_ptr()) if target is not None else None, _c(valid.data_ptr()) if valid is not None else None,
+         ntiles, D, _c(y.data_ptr()), _c(g.data_ptr()) if g is not None else None,
+         ctypes.byref(loss) if want_loss else None, _stream(stream))
+    return y, g, (loss.value if want_loss else None)
+
+
+def precond_apply(ham: Hamiltonian, w, R, stream=None):
+    """Learned preconditioner W = K R for FP32 residual columns R [npts, nb]."""
+    import torch
+    W = torch.empty_like(R)
+    call("rs_precond_apply", ham._h, _c(w.data_ptr()), _c(R.data_ptr()), R.stride(0), _c(W.data_ptr()), W.stride(0),
+         R.shape[1], _stream(stream))
+    return W
+
+
+def precond_train(ham: Hamiltonian, R, X, w, n_tiles: int, epochs: int, batch: int = 64, lr: float = 1e-3,
+                  seed: int = 1, tile: int = 16, stream=None):
+    """Trains the network weights w (FP32 [2160], updated in place) on tiles
+    of (R, X) column pairs; returns the per-epoch mean losses."""
+    cfg = _lib.TrainCfg(n_tiles, tile, epochs, batch, lr, seed)
+    losses = (ctypes.c_float * max(epochs, 1))()
+    call("rs_precond_train", ham._h, ham.grid._h, _c(R.data_ptr()), _c(X.data_ptr()), R.stride(0), R.shape[1],
+         ctypes.byref(cfg), _c(w.data_ptr()), losses, _stream(stream))
+    return list(losses)[:epochs]

@@ -386,7 +386,7 @@ struct rs_ham {
     int device = 0;
     double w[5] = {0, 0, 0, 0, 0};
     DevBuf pinfo64, pinfo32, map, loc, V64, V32, cov_off, cov_atom, cov_gam64, cov_gam32, sph_off, sph_idx, sph_gam64, sph_gam32, E64, E32,
-        cproj, dummy;
+        cproj, dummy, scratch;
     std::map<std::pair<int, int>, WorkList *> work;
     // optional per-launch timing (rs_ham_timing)
     bool timing = false;
@@ -710,6 +710,14 @@ extern "C" int rs_ham_timing_read(rs_ham *h, double *project_ms, double *stencil
 namespace rs {
 
 int64_t ham_npts(const rs_ham *h) { return h->npts; }
+const int32_t *ham_map(const rs_ham *h) { return h->map.as<int32_t>(); }
+const int32_t *ham_loc(const rs_ham *h) { return h->loc.as<int32_t>(); }
+int ham_dim(const rs_ham *h, int axis) { return h->d[axis]; }
+DevBuf *ham_scratch(rs_ham *h, size_t bytes) {
+    if (h->scratch.bytes >= bytes) return &h->scratch;
+    if (h->scratch.alloc(bytes) != RS_OK) return nullptr;
+    return &h->scratch;
+}
 double ham_dV(const rs_ham *h) { return h->dV; }
 
 int ham_filter(const rs_ham *h, const void *R, int64_t ldr, void *W, int64_t ldw, int nb, int dtype, double alpha,

@@ -11,6 +11,12 @@ namespace rs {
 
 int64_t ham_npts(const rs_ham *h);
 double ham_dV(const rs_ham *h);
+const int32_t *ham_map(const rs_ham *h);   // device point map [d0][d1][d2]
+const int32_t *ham_loc(const rs_ham *h);   // device linear map index of every point
+int ham_dim(const rs_ham *h, int axis);
+struct DevBuf;
+// Device scratch owned by h, grown to at least `bytes` (nullptr on failure).
+DevBuf *ham_scratch(rs_ham *h, size_t bytes);
 
 // W = K R with the face-neighbour smoothing filter
 //   (K r)(p) = alpha r(p) + (1 - alpha)/6 sum_{6 face neighbours} r(n),

@@ -20,6 +20,10 @@ template <typename T>
 int rowmul(const T *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, T *Y, int64_t ldy, int64_t npts,
            double alpha, double beta, cudaStream_t st);
 
+// out[k] = sum_p A[p][k] B[p][k] (FP64, exact products, compensated sum), k < ncols <= 256.
+int coldots(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, int ncols, int64_t npts, double *out,
+            cudaStream_t st);
+
 // Small dense FP64 helpers.
 int gemm_small(int m, int n, int k, double alpha, const double *A, int lda, bool ta, const double *B, int ldb, bool tb,
                double beta, double *C, int ldc, cudaStream_t st);

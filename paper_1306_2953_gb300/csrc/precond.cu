@@ -5,11 +5,12 @@
 
 #include "device.h"
 #include "ham.h"
+#include "learned.h"
 #include "precond.h"
 
 namespace rs {
 
-int Precond::set_weights(const float *, const float *, const float *) {
+int Precond::set_weights(const float *, cudaStream_t) {
     return fail(RS_EINVAL, "this preconditioner has no weights");
 }
 
@@ -33,12 +34,47 @@ class Filter : public Precond {
     double alpha;
 };
 
+// The learned network (learned.cu); FP32 residuals only.
+class Learned : public Precond {
+   public:
+    int init(int64_t npts, int nb) {
+        RS_TRY(w.alloc(sizeof(float) * LEARNED_WEIGHTS));
+        RS_TRY(wq.alloc(sizeof(float) * LEARNED_WEIGHTS));
+        RS_TRY(dots.alloc(sizeof(double) * 128));
+        return act.alloc(sizeof(float) * (size_t)learned_act_floats(npts, nb));
+    }
+    int set_weights(const float *w_dev, cudaStream_t st) override {
+        RS_CUDA(cudaMemcpyAsync(w.p, w_dev, sizeof(float) * LEARNED_WEIGHTS, cudaMemcpyDeviceToDevice, st));
+        RS_TRY(learned_round_weights(w.as<float>(), wq.as<float>(), st));
+        ready = true;
+        return RS_OK;
+    }
+    int apply(const rs_ham *h, const void *R, int64_t ldr, void *W, int64_t ldw, int nb, int dtype,
+              cudaStream_t st) override {
+        if (!ready) return fail(RS_EINVAL, "learned preconditioner: weights not set");
+        if (dtype != RS_F32) return fail(RS_EINVAL, "learned preconditioner: FP32 residuals only");
+        return learned_apply(h, (const float *)R, ldr, (float *)W, ldw, nb, wq.as<float>(), act.as<float>(),
+                             dots.as<double>(), st);
+    }
+    DevBuf w, wq, act, dots;
+    bool ready = false;
+};
+
 }  // namespace
 
-Precond *Precond::create(int kind, double filter_alpha) {
+Precond *Precond::create(int kind, double filter_alpha, int64_t npts, int nb, int dtype) {
     switch (kind) {
         case RS_PRECOND_NONE: return new (std::nothrow) Identity();
         case RS_PRECOND_FILTER: return new (std::nothrow) Filter(filter_alpha);
+        case RS_PRECOND_LEARNED: {
+            if (dtype != RS_F32) return nullptr;
+            Learned *l = new (std::nothrow) Learned();
+            if (l && l->init(npts, nb) != RS_OK) {
+                delete l;
+                return nullptr;
+            }
+            return l;
+        }
         default: return nullptr;
     }
 }

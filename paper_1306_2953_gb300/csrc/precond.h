@@ -15,8 +15,8 @@ class Precond {
     // W = K R for a block of nb residual columns; R [npts][ldr], W [npts][ldw].
     virtual int apply(const rs_ham *h, const void *R, int64_t ldr, void *W, int64_t ldw, int nb, int dtype,
                       cudaStream_t st) = 0;
-    virtual int set_weights(const float *w1, const float *w2, const float *w3);
-    static Precond *create(int kind, double filter_alpha);
+    virtual int set_weights(const float *w_dev, cudaStream_t st);
+    static Precond *create(int kind, double filter_alpha, int64_t npts, int nb, int dtype);
 };
 
 }  // namespace rs

@@ -99,6 +99,20 @@ __global__ void k_copy_leading(const double *A, int lda, int n, double *B, int l
         B[(e / n) * ldb + e % n] = A[(e / n) * lda + e % n];
 }
 
+int coldots(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, int ncols, int64_t npts, double *out,
+            cudaStream_t st) {
+    RS_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * ncols, st));
+    const int rows = 256 / ncols;
+    const int64_t need = (npts + rows - 1) / rows;
+    const unsigned blocks = (unsigned)std::min<int64_t>(need, 152 * 8);
+    if (dtype == RS_F64)
+        k_coldots<double><<<blocks, 256, 0, st>>>((const double *)A, lda, (const double *)B, ldb, ncols, npts, out);
+    else
+        k_coldots<float><<<blocks, 256, 0, st>>>((const float *)A, lda, (const float *)B, ldb, ncols, npts, out);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
 }  // namespace rs
 
 struct rs_solver {
@@ -120,25 +134,6 @@ struct rs_solver {
 };
 
 namespace {
-
-template <typename T> struct Ops {
-    static int coldots(const void *A, int64_t lda, const void *B, int64_t ldb, int ncols, int64_t npts, double *out,
-                       cudaStream_t st) {
-        const int rows = 256 / ncols;
-        const int64_t need = (npts + rows - 1) / rows;
-        const unsigned blocks = (unsigned)std::min<int64_t>(need, 152 * 8);
-        k_coldots<T><<<blocks, 256, 0, st>>>((const T *)A, lda, (const T *)B, ldb, ncols, npts, out);
-        RS_LAUNCH_CHECK();
-        return RS_OK;
-    }
-};
-
-int coldots(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, int ncols, int64_t npts, double *out,
-            cudaStream_t st) {
-    RS_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * ncols, st));
-    if (dtype == RS_F64) return Ops<double>::coldots(A, lda, B, ldb, ncols, npts, out, st);
-    return Ops<float>::coldots(A, lda, B, ldb, ncols, npts, out, st);
-}
 
 unsigned elem_blocks(int64_t npts, int ncols) { return (unsigned)((npts * ncols + 255) / 256); }
 
@@ -313,7 +308,7 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
     S->C = S->mu + n3;
     S->status = reinterpret_cast<int *>(S->C + (size_t)n3 * c.nb);
     S->eighw = reinterpret_cast<void *>(S->C + (size_t)n3 * c.nb + 8);
-    S->pc = Precond::create(c.precond, c.filter_alpha);
+    S->pc = Precond::create(c.precond, c.filter_alpha, S->npts, c.nb, c.dtype);
     if (!S->pc) return bail(fail(RS_EINVAL, "rs_solver_create: preconditioner %d unavailable", c.precond));
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(S->psi.p, Psi0_dev, big, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
@@ -356,9 +351,11 @@ extern "C" int rs_solver_psi(rs_solver *S, void **psi_dev) {
     return RS_OK;
 }
 
-extern "C" int rs_solver_set_precond_weights(rs_solver *S, const float *w1, const float *w2, const float *w3) {
-    if (!S || !w1 || !w2 || !w3) return fail(RS_EINVAL, "rs_solver_set_precond_weights: null argument");
-    return S->pc->set_weights(w1, w2, w3);
+extern "C" int rs_solver_set_precond_weights(rs_solver *S, const float *w_dev) {
+    if (!S || !w_dev) return fail(RS_EINVAL, "rs_solver_set_precond_weights: null argument");
+    RS_TRY(S->pc->set_weights(w_dev, nullptr));
+    RS_CUDA(cudaDeviceSynchronize());
+    return RS_OK;
 }
 
 extern "C" int rs_solver_destroy(rs_solver *S) {
