@@ -192,6 +192,27 @@ int64_t rs_linalg_workspace_bytes(int nst);
 int rs_orthonormalize(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int dtype, void *work_dev,
                       double *Uinv_dev, void *stream);
 
+/* Allocation-free variant of rs_orthonormalize (no counterpart in the paper:
+ * it exists for callers of this library that cannot allocate device memory
+ * when they need the operation -- code being captured into a CUDA graph that
+ * must not contain allocation nodes, plugins whose host framework owns every
+ * device buffer, or loops that forbid cudaMalloc after start-up).
+ * Same operation and arguments as rs_orthonormalize minus the workspace and
+ * the U^-1 output; the scratch lives in one fixed __device__ array inside
+ * this library, sized for nst <= 256 states (about 2 MB, held by every GPU
+ * that loads the library until the process exits).
+ *  - nst > 256 is rejected with RS_EINVAL.
+ *  - The call allocates nothing (no cudaMalloc / cudaFree, no allocating
+ *    library routine).
+ *  - The first call on each device looks up the array's device address on
+ *    that device (cudaGetSymbolAddress); make that first call outside any
+ *    stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (from
+ *    different host threads or streams) race and must be serialised by the
+ *    caller.  The call writes every scratch word it reads before reading it.
+ * Blocking.  Errors: RS_EINVAL, RS_ENOTSPD (Psi left unchanged), RS_ECUDA. */
+int rs_orthonormalize_noalloc(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int dtype, void *stream);
+
 /* Subspace diagonalisation (Sec. VI, Eqs. 7-8): HPsi = H Psi, h = <Psi|H|Psi>
  * (symmetrised, FP64), h xi = xi diag(eps) with eps ascending (FP64 on the
  * device), Psi <- Psi xi and HPsi <- HPsi xi.  Psi must be orthonormal.

@@ -70,6 +70,7 @@ SIGNATURES = {
     "rs_overlap_block": (None, [P, P, I64, I32, P, I64, I32, P, I64, I32, P]),
     "rs_linalg_workspace_bytes": (I64, [I32]),
     "rs_orthonormalize": (None, [P, P, I64, I32, I32, P, P, P]),
+    "rs_orthonormalize_noalloc": (None, [P, P, I64, I32, I32, P]),
     "rs_subspace_diag": (None, [P, P, P, I64, I32, I32, I32, P, P, P, P]),
     "rs_solver_create": (None, [P, ctypes.POINTER(SolverCfg), P, P, PP]),
     "rs_eigensolver_step": (None, [P, P, P, P, P]),
