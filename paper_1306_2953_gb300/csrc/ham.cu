@@ -3,7 +3,8 @@
 // Two launches per block:
 //  1. k_project: the Kleinman-Bylander projection integrals of Eq. (4),
 //     c[A,q,s] = E[A,q] dV sum_{p in S_A} gamma_Aq(p) psi(p,s), one CTA per
-//     (atom, state group), a block-wide tree reduction over sphere points.
+//     (atom, state group), a block-wide tree reduction over sphere points;
+//     stored [atom][state][q] so that one 16-byte load gives a state's four.
 //  2. k_stencil: the 25-point star kinetic stencil (Sec. V.A), the local
 //     potential (Sec. V.B) and the nonlocal sum of Eq. (4), fused.  Each CTA
 //     owns a TX x TY column of lattice points (axes 2 and 1 of the point
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(NT) k_project(HamDev<T> d, const T *__restrict
     if (r == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            cproj[((int64_t)A * 4 + q) * nb + sg0 + s] = __ldg(d.E + 4 * A + q) * d.dV * red[q][s];
+            cproj[((int64_t)A * nb + sg0 + s) * 4 + q] = __ldg(d.E + 4 * A + q) * d.dV * red[q][s];
     }
 }
 
@@ -310,8 +311,8 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
                 for (int e = inf.x; e < inf.y; ++e) {
                     const int A = __ldg(d.cov_atom + e);
                     const Four<T> g = load4(d.cov_gam + 4 * (int64_t)e);
-                    const T *cp = cproj + (int64_t)A * 4 * nb + sg0 + s;
-                    out += g.a * __ldg(cp) + g.b * __ldg(cp + nb) + g.c * __ldg(cp + 2 * nb) + g.d * __ldg(cp + 3 * nb);
+                    const Four<T> c4 = load4(cproj + ((int64_t)A * nb + sg0 + s) * 4);
+                    out += g.a * c4.a + g.b * c4.b + g.c * c4.c + g.d * c4.d;
                 }
                 hpsi[(int64_t)r * ldh + sg0 + s] = out;
             }
@@ -325,6 +326,265 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
                 q[dy][dx][8] = nq[dy][dx];
             }
         halo_rows(z + 3);
+        slot = slot == 2 ? 0 : slot + 1;
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+// ------------------------------- FP32 kernel with per-chunk NL staging ---
+// The same march as k_stencil for FP32 blocks of 32 states on 8 x 8 tiles, with
+// everything irregular about a work item staged in shared memory once, at its
+// start: interior and halo point rows, each output point's potential, and the
+// nonlocal entries (projector values and atom) of all its output points (the
+// host bounds the entries of a work item by V3_CAP).  In the march the only
+// global traffic is psi (queue refill, halo copies), the projection
+// coefficients (L1-resident) and the H psi stores.
+
+constexpr int V3_CAP = 3584;   // nonlocal entries per work item
+constexpr int V3_TX = 8, V3_TY = 8, V3_SG = 32;
+
+struct V3Cfg {
+    static constexpr int TX = V3_TX, TY = V3_TY, SG = V3_SG;
+    static constexpr int W2 = TX + 8, W1 = TY + 8;
+    static constexpr int PLANE = W1 * W2 * SG;
+    static constexpr int NT = (TX / 2) * (TY / 2) * SG;   // 512
+    static constexpr int RING = 3;
+    static constexpr int CPR = 8;                          // 16-byte copies per 128-byte row
+    static constexpr int NH = 8 * TY + 8 * TX;
+    static constexpr int HPT = (NH * CPR + NT - 1) / NT;
+    static constexpr int NI = TX * TY;
+    static constexpr size_t OFF_ROWS = (size_t)RING * PLANE * 4;
+    static constexpr size_t OFF_HROWS = OFF_ROWS + (size_t)(ZCHUNK + 9) * NI * 4;
+    static constexpr size_t OFF_PV = OFF_HROWS + (size_t)ZCHUNK * NH * 4;
+    static constexpr size_t OFF_PE = OFF_PV + (size_t)ZCHUNK * NI * 4;
+    static constexpr size_t OFF_EG = OFF_PE + (size_t)ZCHUNK * NI * 4;
+    static constexpr size_t OFF_EA = OFF_EG + (size_t)V3_CAP * 16;
+    static constexpr size_t OFF_SCAN = OFF_EA + (size_t)V3_CAP * 4;
+    static constexpr size_t SMEM = OFF_SCAN + 32 * 4;
+};
+
+__global__ void __launch_bounds__(V3Cfg::NT, 1)
+    k_stencil_v3(HamDev<float> d, const float *__restrict__ psi, int64_t ldp, float *__restrict__ hpsi, int64_t ldh,
+                 const float *__restrict__ cproj, int nb, const int4 *__restrict__ work) {
+    using C = V3Cfg;
+    constexpr int TX = C::TX, TY = C::TY, SG = C::SG;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *sm = reinterpret_cast<float *>(smraw);
+    int *rows = reinterpret_cast<int *>(smraw + C::OFF_ROWS);
+    int *hrows = reinterpret_cast<int *>(smraw + C::OFF_HROWS);
+    float *pv = reinterpret_cast<float *>(smraw + C::OFF_PV);
+    int *pe = reinterpret_cast<int *>(smraw + C::OFF_PE);
+    float4 *eg = reinterpret_cast<float4 *>(smraw + C::OFF_EG);
+    int *ea = reinterpret_cast<int *>(smraw + C::OFF_EA);
+    int *wsum = reinterpret_cast<int *>(smraw + C::OFF_SCAN);
+
+    const int tid = threadIdx.x;
+    const int s = tid % SG;
+    const int patch = tid / SG;
+    const int lx = 2 * (patch % (TX / 2));
+    const int ly = 2 * (patch / (TX / 2));
+    const int4 wk = work[blockIdx.x];
+    const int b1 = wk.x * TY, b2 = wk.y * TX;
+    const int za = wk.z, zb = wk.w;
+    const int nz = zb - za;
+    const int sg0 = blockIdx.y * SG;
+    const float *psig = psi + sg0;
+
+    auto map_at = [&](int a0, int a1, int a2) -> int {
+        if ((unsigned)a0 >= (unsigned)d.d0 || (unsigned)a1 >= (unsigned)d.d1 || (unsigned)a2 >= (unsigned)d.d2)
+            return -1;
+        return __ldg(d.map + ((int64_t)a0 * d.d1 + a1) * d.d2 + a2);
+    };
+    auto halo_pos = [&](int hh, int &hy, int &hx) {
+        if (hh < 8 * TY) {
+            hy = hh >> 3;
+            const int t = hh & 7;
+            hx = t < 4 ? t - 4 : TX + t - 4;
+        } else {
+            const int h2 = hh - 8 * TY;
+            hx = h2 % TX;
+            const int t = h2 / TX;
+            hy = t < 4 ? t - 4 : TY + t - 4;
+        }
+    };
+
+    // ---- stage the work item's rows
+    for (int e = tid; e < (nz + 9) * C::NI; e += C::NT) {
+        const int pl = e / C::NI, pos = e % C::NI;
+        rows[e] = map_at(za - 4 + pl, b1 + pos / TX, b2 + pos % TX);
+    }
+    for (int e = tid; e < nz * C::NH; e += C::NT) {
+        int hy, hx;
+        halo_pos(e % C::NH, hy, hx);
+        hrows[e] = map_at(za + e / C::NH, b1 + hy, b2 + hx);
+    }
+    __syncthreads();
+    // ---- potential and nonlocal entry counts of the output points; exclusive scan
+    constexpr int PPT = ZCHUNK * C::NI / C::NT;   // output points per thread (4)
+    int cnt[PPT], e0[PPT], tot = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int lp = tid * PPT + k;
+        cnt[k] = 0;
+        e0[k] = 0;
+        float v = 0.f;
+        if (lp < nz * C::NI) {
+            const int r = rows[(lp / C::NI + 4) * C::NI + lp % C::NI];
+            if (r >= 0) {
+                const int4 inf = __ldg(d.pinfo + r);
+                e0[k] = inf.x;
+                cnt[k] = inf.y - inf.x;
+                v = __int_as_float(inf.z);
+            }
+            pv[lp] = v;
+        }
+        tot += cnt[k];
+    }
+    // block-wide exclusive scan of tot
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((tid & 31) >= o) incl += y;
+    }
+    if ((tid & 31) == 31) wsum[tid >> 5] = incl;
+    __syncthreads();
+    if (tid < 32) {
+        int x = tid < C::NT / 32 ? wsum[tid] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (tid >= o) x += y;
+        }
+        wsum[tid] = x;  // inclusive per-warp totals
+    }
+    __syncthreads();
+    int start = incl - tot + ((tid >> 5) ? wsum[(tid >> 5) - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int lp = tid * PPT + k;
+        if (lp < nz * C::NI) pe[lp] = (start << 4) | cnt[k];
+        for (int j = 0; j < cnt[k]; ++j) {
+            if (start + j < V3_CAP) {
+                const float4 gv = __ldg(reinterpret_cast<const float4 *>(d.cov_gam) + e0[k] + j);
+                eg[start + j] = gv;
+                ea[start + j] = __ldg(d.cov_atom + e0[k] + j) * nb;
+            }
+        }
+        start += cnt[k];
+    }
+
+    auto row_of = [&](int z, int iy, int ix) -> int { return rows[(z - za + 4) * C::NI + iy * TX + ix]; };
+    auto load_val = [&](int r) -> float { return r >= 0 ? __ldg(psig + (int64_t)r * ldp + s) : 0.f; };
+    auto issue_halo = [&](int z, int slot) {
+        float *base = sm + slot * C::PLANE;
+        const int *hr = hrows + (z - za) * C::NH;
+#pragma unroll
+        for (int j = 0; j < C::HPT; ++j) {
+            const int i = tid + j * C::NT;
+            if (i >= C::NH * C::CPR) continue;
+            const int hh = i / C::CPR, c = i % C::CPR;
+            int hy, hx;
+            halo_pos(hh, hy, hx);
+            const int r = hr[hh];
+            const float *src = r >= 0 ? psig + (int64_t)r * ldp + c * 4 : psig;
+            cp_async<16>(base + ((hy + 4) * C::W2 + (hx + 4)) * SG + c * 4, src, r >= 0);
+        }
+    };
+    __syncthreads();
+
+    float q[2][2][9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) q[dy][dx][k] = load_val(row_of(za - 4 + k, ly + dy, lx + dx));
+    issue_halo(za, 0);
+    cp_async_commit();
+    if (za + 1 < zb) issue_halo(za + 1, 1);
+    cp_async_commit();
+
+    const float w0 = d.w[0], w1 = d.w[1], w2 = d.w[2], w3 = d.w[3], w4 = d.w[4];
+    const float *cpl = cproj + (int64_t)(sg0 + s) * 4;
+    int slot = 0;
+    for (int z = za; z < zb; ++z) {
+        const int pslot = slot == 0 ? 2 : slot - 1;
+        if (z + 2 < zb) issue_halo(z + 2, pslot);
+        cp_async_commit();
+        float nq[2][2];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) nq[dy][dx] = load_val(row_of(z + 5, ly + dy, lx + dx));
+        float *P = sm + slot * C::PLANE;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) P[((ly + dy + 4) * C::W2 + lx + dx + 4) * SG + s] = q[dy][dx][4];
+        cp_async_wait<2>();
+        __syncthreads();
+
+        float acc[2][2];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx)
+                acc[dy][dx] = w0 * q[dy][dx][4] + w1 * (q[dy][dx][5] + q[dy][dx][3]) + w2 * (q[dy][dx][6] + q[dy][dx][2]) +
+                              w3 * (q[dy][dx][7] + q[dy][dx][1]) + w4 * (q[dy][dx][8] + q[dy][dx][0]);
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            float v[10];
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+                if (k != 4 && k != 5) v[k] = P[((ly + dy + 4) * C::W2 + lx + k) * SG + s];
+            v[4] = q[dy][0][4];
+            v[5] = q[dy][1][4];
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx)
+                acc[dy][dx] += w1 * (v[5 + dx] + v[3 + dx]) + w2 * (v[6 + dx] + v[2 + dx]) + w3 * (v[7 + dx] + v[1 + dx]) +
+                               w4 * (v[8 + dx] + v[0 + dx]);
+        }
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            float v[10];
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+                if (k != 4 && k != 5) v[k] = P[((ly + k) * C::W2 + lx + dx + 4) * SG + s];
+            v[4] = q[0][dx][4];
+            v[5] = q[1][dx][4];
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+                acc[dy][dx] += w1 * (v[5 + dy] + v[3 + dy]) + w2 * (v[6 + dy] + v[2 + dy]) + w3 * (v[7 + dy] + v[1 + dy]) +
+                               w4 * (v[8 + dy] + v[0 + dy]);
+        }
+        const int pbase = (z - za) * C::NI;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int pos = (ly + dy) * TX + lx + dx;
+                const int r = rows[(z - za + 4) * C::NI + pos];
+                if (r < 0) continue;
+                const int code = pe[pbase + pos];
+                float out = acc[dy][dx] + pv[pbase + pos] * q[dy][dx][4];
+                const int e1 = min((code >> 4) + (code & 15), V3_CAP);
+                for (int e = code >> 4; e < e1; ++e) {
+                    const float4 gv = eg[e];
+                    const float4 c4 = __ldg(reinterpret_cast<const float4 *>(cpl + (int64_t)ea[e] * 4) );
+                    out += gv.x * c4.x + gv.y * c4.y + gv.z * c4.z + gv.w * c4.w;
+                }
+                hpsi[(int64_t)r * ldh + sg0 + s] = out;
+            }
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) q[dy][dx][k] = q[dy][dx][k + 1];
+                q[dy][dx][8] = nq[dy][dx];
+            }
         slot = slot == 2 ? 0 : slot + 1;
         __syncthreads();
     }
@@ -388,11 +648,13 @@ struct rs_ham {
     DevBuf pinfo64, pinfo32, map, loc, V64, V32, cov_off, cov_atom, cov_gam64, cov_gam32, sph_off, sph_idx, sph_gam64, sph_gam32, E64, E32,
         cproj, dummy, scratch;
     std::map<std::pair<int, int>, WorkList *> work;
+    WorkList *work_v3 = nullptr;   // FP32 32-state kernel with bounded nonlocal entries per item
     // optional per-launch timing (rs_ham_timing)
     bool timing = false;
     std::vector<cudaEvent_t> events;   // 3 per recorded call
     size_t n_recorded = 0;
     ~rs_ham() {
+        delete work_v3;
         for (auto &kv : work) delete kv.second;
         for (cudaEvent_t e : events) cudaEventDestroy(e);
     }
@@ -491,6 +753,60 @@ static int build_work(rs_ham *H, const rs_grid *g, int tx, int ty) {
     return wl->buf.upload(items.data(), items.size() * sizeof(int4));
 }
 
+// Work items of k_stencil_v3: 8 x 8 tile columns cut into chunks of at most
+// ZCHUNK planes and at most V3_CAP nonlocal entries.  Returns false (no list)
+// when some point is covered by more than 15 projector spheres.
+static int build_work_v3(rs_ham *H, const rs_grid *g, const std::vector<int32_t> &coff, bool *ok) {
+    const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+    const int tx = V3_TX, ty = V3_TY;
+    *ok = false;
+    for (int64_t p = 0; p < g->npts; ++p)
+        if (coff[p + 1] - coff[p] > 15) return RS_OK;
+    const int n1 = (d1 + ty - 1) / ty, n2 = (d2 + tx - 1) / tx;
+    std::vector<int4> items;
+    for (int t1 = 0; t1 < n1; ++t1)
+        for (int t2 = 0; t2 < n2; ++t2) {
+            int za = -1, entries = 0;
+            for (int a = 0; a < d0; ++a) {
+                int e = 0, any = 0;
+                for (int b = t1 * ty; b < std::min(d1, (t1 + 1) * ty); ++b)
+                    for (int c = t2 * tx; c < std::min(d2, (t2 + 1) * tx); ++c) {
+                        const int32_t p = g->map[((size_t)a * d1 + b) * d2 + c];
+                        if (p >= 0) {
+                            any = 1;
+                            e += coff[p + 1] - coff[p];
+                        }
+                    }
+                if (za >= 0 && (a - za == ZCHUNK || entries + e > V3_CAP)) {
+                    items.push_back(make_int4(t1, t2, za, a));
+                    za = -1;
+                    entries = 0;
+                }
+                if (any && za < 0) za = a;
+                if (za >= 0) entries += e;
+            }
+            if (za >= 0) {
+                // trim trailing empty planes
+                int zb = d0;
+                while (zb > za) {
+                    bool any = false;
+                    for (int b = t1 * ty; b < std::min(d1, (t1 + 1) * ty) && !any; ++b)
+                        for (int c = t2 * tx; c < std::min(d2, (t2 + 1) * tx) && !any; ++c)
+                            any = g->map[((size_t)(zb - 1) * d1 + b) * d2 + c] >= 0;
+                    if (any) break;
+                    --zb;
+                }
+                items.push_back(make_int4(t1, t2, za, zb));
+            }
+        }
+    WorkList *wl = new (std::nothrow) WorkList;
+    if (!wl) return fail(RS_ENOMEM, "host allocation failed");
+    H->work_v3 = wl;
+    wl->count = (int)items.size();
+    *ok = true;
+    return wl->buf.upload(items.data(), items.size() * sizeof(int4));
+}
+
 extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_proj *pr, int order, rs_ham **out) {
     if (!g || !V_host || !out) return fail(RS_EINVAL, "rs_ham_create: null argument");
     if (order < 1 || order > 4) return fail(RS_EINVAL, "rs_ham_create: order must be in 1..4");
@@ -580,6 +896,8 @@ extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_pr
     }
     for (const Shape &s : kShapes)
         if ((rc = build_work(H, g, s.tx, s.ty))) return bail(rc);
+    bool v3ok = false;
+    if ((rc = build_work_v3(H, g, coff, &v3ok))) return bail(rc);
     *out = H;
     return RS_OK;
 }
@@ -605,6 +923,26 @@ static int launch_stencil(rs_ham *H, const HamDev<T> &d, const T *psi, int64_t l
                                                             wl->buf.as<int4>());
     RS_LAUNCH_CHECK();
     return RS_OK;
+}
+
+template <typename T>
+static int launch_v3(rs_ham *H, const HamDev<T> &d, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, int nb,
+                     cudaStream_t st) {
+    if constexpr (sizeof(T) != 4) {
+        return fail(RS_EINVAL, "launch_v3: FP32 only");
+    } else {
+        static bool attr_done = false;
+        if (!attr_done) {
+            RS_CUDA(cudaFuncSetAttribute(k_stencil_v3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V3Cfg::SMEM));
+            attr_done = true;
+        }
+        const WorkList *wl = H->work_v3;
+        if (wl->count == 0) return RS_OK;
+        dim3 grid((unsigned)wl->count, (unsigned)(nb / V3_SG));
+        k_stencil_v3<<<grid, V3Cfg::NT, V3Cfg::SMEM, st>>>(d, psi, ldp, hpsi, ldh, H->cproj.as<T>(), nb, wl->buf.as<int4>());
+        RS_LAUNCH_CHECK();
+        return RS_OK;
+    }
 }
 
 template <typename T>
@@ -638,6 +976,10 @@ static int apply_t(rs_ham *H, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, i
         case 16: rc = launch_stencil<T, 16, 16, 8>(H, d, psi, ldp, hpsi, ldh, nb, st); break;
         default:
             if constexpr (SGMAX >= 32) {
+                if (H->work_v3) {
+                    rc = launch_v3(H, d, psi, ldp, hpsi, ldh, nb, st);
+                    break;
+                }
                 rc = launch_stencil<T, 32, 8, 8>(H, d, psi, ldp, hpsi, ldh, nb, st);
                 break;
             }
