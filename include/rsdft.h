@@ -178,6 +178,27 @@ int rs_ham_launch_bytes(const rs_ham *h, int nb, int dtype, int64_t *project_byt
 int rs_overlap_block(const rs_grid *g, const void *X_dev, int64_t ldx, int nx, const void *Y_dev, int64_t ldy,
                      int ny, double *S_dev, int64_t lds, int dtype, void *stream);
 
+/* Tensor-core contractions of FP32 orbitals (5th-generation tensor cores,
+ * tcgen05): every FP32 operand is split exactly into three BF16 pieces and
+ * the six piece products of weight >= 2^-16 are accumulated in FP32, so the
+ * results carry FP32-level accumulation error (not the exactly rounded FP64
+ * of rs_overlap_block).  Workspace (device, caller-owned):
+ * rs_tc_workspace_bytes(rows_a, rows_b, K) bytes, where the overlap has
+ * rows_a = nx, rows_b = ny, K = npts and the rotation rows_a = npts,
+ * rows_b = m, K = n.  Blocking (they read a status word). */
+int64_t rs_tc_workspace_bytes(int64_t rows_a, int64_t rows_b, int64_t K);
+
+/* S = dV X^T Y (Eq. 5) for FP32 X [npts][ldx] (nx columns) and Y (ny
+ * columns); S device double [nx][lds]. */
+int rs_overlap_block_tc(const rs_grid *g, const float *X_dev, int64_t ldx, int nx, const float *Y_dev, int64_t ldy,
+                        int ny, double *S_dev, int64_t lds, void *work_dev, void *stream);
+
+/* Subspace rotation Y = X C (Eqs. 6 and 8 applied by blocks of points): X
+ * FP32 [npts][ldx] (n columns), C device double [n][ldc] (m columns), Y FP32
+ * [npts][ldy]; Y may be X (the operands are split before the product). */
+int rs_rotate_block(const float *X_dev, int64_t ldx, int n, const double *C_dev, int64_t ldc, int m, float *Y_dev,
+                    int64_t ldy, int64_t npts, void *work_dev, void *stream);
+
 /* Device workspace (bytes) that rs_orthonormalize / rs_subspace_diag need
  * for nst states. */
 int64_t rs_linalg_workspace_bytes(int nst);
@@ -212,6 +233,18 @@ int rs_orthonormalize(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int 
  *    caller.  The call writes every scratch word it reads before reading it.
  * Blocking.  Errors: RS_EINVAL, RS_ENOTSPD (Psi left unchanged), RS_ECUDA. */
 int rs_orthonormalize_noalloc(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int dtype, void *stream);
+
+/* Dense symmetric eigensolver of the Rayleigh-Ritz step (Sec. VI: "the
+ * subspace Hamiltonian is diagonalised", there on the CPU with LAPACK):
+ * A_dev = V diag(w) V^T, eigenvalues ascending, A_dev device double [n][n]
+ * (read only), w_dev [n], V_dev [n][n] (columns are eigenvectors).
+ *   refine > 0: FP32 cyclic Jacobi, `refine` FP64 refinement steps
+ *               (Ogita-Aishima) and an FP64 Jacobi polish (the default);
+ *   refine = 0: FP64 cyclic Jacobi;  refine < 0: FP32 Jacobi only.
+ * work_dev: rs_eigh_workspace_bytes(n) bytes.  Blocking.  Errors:
+ * RS_ENOCONV when the FP64 Jacobi of refine = 0 hits its sweep cap. */
+int64_t rs_eigh_workspace_bytes(int n);
+int rs_eigh(const double *A_dev, int n, double *w_dev, double *V_dev, int refine, void *work_dev, void *stream);
 
 /* Subspace diagonalisation (Sec. VI, Eqs. 7-8): HPsi = H Psi, h = <Psi|H|Psi>
  * (symmetrised, FP64), h xi = xi diag(eps) with eps ascending (FP64 on the

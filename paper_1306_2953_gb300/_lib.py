@@ -69,6 +69,11 @@ SIGNATURES = {
     "rs_ham_launch_bytes": (None, [P, I32, I32, P, P]),
     "rs_overlap_block": (None, [P, P, I64, I32, P, I64, I32, P, I64, I32, P]),
     "rs_linalg_workspace_bytes": (I64, [I32]),
+    "rs_tc_workspace_bytes": (I64, [I64, I64, I64]),
+    "rs_eigh_workspace_bytes": (I64, [I32]),
+    "rs_eigh": (None, [P, I32, P, P, I32, P, P]),
+    "rs_overlap_block_tc": (None, [P, P, I64, I32, P, I64, I32, P, I64, P, P]),
+    "rs_rotate_block": (None, [P, I64, I32, P, I64, I32, P, I64, I64, P, P]),
     "rs_orthonormalize": (None, [P, P, I64, I32, I32, P, P, P]),
     "rs_orthonormalize_noalloc": (None, [P, P, I64, I32, I32, P]),
     "rs_subspace_diag": (None, [P, P, P, I64, I32, I32, I32, P, P, P, P]),

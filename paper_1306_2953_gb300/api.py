@@ -333,3 +333,44 @@ def precond_train(ham: Hamiltonian, R, X, w, n_tiles: int, epochs: int, batch: i
     call("rs_precond_train", ham._h, ham.grid._h, _c(R.data_ptr()), _c(X.data_ptr()), R.stride(0), R.shape[1],
          ctypes.byref(cfg), _c(w.data_ptr()), losses, _stream(stream))
     return list(losses)[:epochs]
+
+
+def tc_workspace(rows_a: int, rows_b: int, K: int, device=None):
+    import torch
+    nbytes = int(_lib.lib().rs_tc_workspace_bytes(rows_a, rows_b, K))
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def overlap_tc(grid: Grid, X, Y, work=None, stream=None):
+    """Tensor-core S = dV X^T Y for FP32 device tensors (FP32-level accuracy)."""
+    import torch
+    nx, ny = X.shape[1], Y.shape[1]
+    work = tc_workspace(nx, ny, X.shape[0], X.device) if work is None else work
+    S = torch.empty((nx, ny), dtype=torch.float64, device=X.device)
+    call("rs_overlap_block_tc", grid._h, _c(X.data_ptr()), X.stride(0), nx, _c(Y.data_ptr()), Y.stride(0), ny,
+         _c(S.data_ptr()), S.stride(0), _c(work.data_ptr()), _stream(stream))
+    return S
+
+
+def rotate(X, C, Y=None, work=None, stream=None):
+    """Tensor-core Y = X C for FP32 X [npts, n] and FP64 C [n, m]."""
+    import torch
+    npts, n = X.shape
+    m = C.shape[1]
+    Y = torch.empty((npts, m), dtype=torch.float32, device=X.device) if Y is None else Y
+    work = tc_workspace(npts, m, n, X.device) if work is None else work
+    call("rs_rotate_block", _c(X.data_ptr()), X.stride(0), n, _c(C.data_ptr()), C.stride(0), m, _c(Y.data_ptr()),
+         Y.stride(0), npts, _c(work.data_ptr()), _stream(stream))
+    return Y
+
+
+def eigh(A, refine: int = 2, stream=None):
+    """Dense symmetric eigensolver on the device: A [n, n] FP64 -> (w, V)."""
+    import torch
+    n = A.shape[0]
+    work = torch.empty(int(_lib.lib().rs_eigh_workspace_bytes(n)), dtype=torch.uint8, device=A.device)
+    w = torch.empty(n, dtype=torch.float64, device=A.device)
+    V = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    A = A.contiguous()
+    call("rs_eigh", _c(A.data_ptr()), n, _c(w.data_ptr()), _c(V.data_ptr()), refine, _c(work.data_ptr()), _stream(stream))
+    return w, V

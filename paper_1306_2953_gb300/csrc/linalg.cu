@@ -45,6 +45,13 @@ template <> struct GramAcc<double> {
     __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
     __device__ __forceinline__ double value() const { return v; }
 };
+// FP32 data, plain FP32 accumulation within a chunk of points (the inner
+// iterations of the FP32 mode); chunks are combined in FP64.
+struct GramAccFast {
+    float v = 0;
+    __device__ __forceinline__ void add(float a, float b) { v = fmaf(a, b, v); }
+    __device__ __forceinline__ double value() const { return (double)v; }
+};
 template <> struct GramAcc<float> {
     float hi = 0, lo = 0;
     __device__ __forceinline__ void add(float a, float b) {
@@ -59,7 +66,7 @@ template <> struct GramAcc<float> {
 };
 
 // S[i][j] += dV * sum_{p in chunk} X[p][i] Y[p][j]; grid (ceil(nx/64), ceil(ny/64), splits)
-template <typename T>
+template <typename T, typename ACC = GramAcc<T>>
 __global__ void __launch_bounds__(G_NT) k_gram(const T *__restrict__ X, int64_t ldx, int nx, const T *__restrict__ Y,
                                                int64_t ldy, int ny, int64_t npts, int64_t chunk, double dV,
                                                double *__restrict__ S, int64_t lds) {
@@ -69,7 +76,7 @@ __global__ void __launch_bounds__(G_NT) k_gram(const T *__restrict__ X, int64_t 
     const int64_t p0 = (int64_t)blockIdx.z * chunk;
     const int64_t p1 = min(npts, p0 + chunk);
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 4x4 micro tile at (4ty.., 4tx..)
-    GramAcc<T> acc[4][4];
+    ACC acc[4][4];
     for (int64_t pk = p0; pk < p1; pk += G_TK) {
         for (int e = threadIdx.x; e < G_TK * G_TM; e += G_NT) {
             const int k = e / G_TM, c = e % G_TM;
@@ -109,7 +116,7 @@ __global__ void k_zero2d(double *S, int64_t lds, int n, int m) {
 
 template <typename T>
 int gram(const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy, int ny, int64_t npts, double dV, double *S,
-         int64_t lds, cudaStream_t st) {
+         int64_t lds, cudaStream_t st, bool fast) {
     k_zero2d<<<64, 256, 0, st>>>(S, lds, nx, ny);
     RS_LAUNCH_CHECK();
     const int gx = (nx + G_TM - 1) / G_TM, gy = (ny + G_TN - 1) / G_TN;
@@ -119,14 +126,21 @@ int gram(const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy, int ny, int64
     chunk = (chunk + G_TK - 1) / G_TK * G_TK;
     splits = (int)((npts + chunk - 1) / chunk);
     dim3 grid(gx, gy, splits);
+    if constexpr (sizeof(T) == 4) {
+        if (fast) {
+            k_gram<float, GramAccFast><<<grid, G_NT, 0, st>>>(X, ldx, nx, Y, ldy, ny, npts, chunk, dV, S, lds);
+            RS_LAUNCH_CHECK();
+            return RS_OK;
+        }
+    }
     k_gram<T><<<grid, G_NT, 0, st>>>(X, ldx, nx, Y, ldy, ny, npts, chunk, dV, S, lds);
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
 template int gram<double>(const double *, int64_t, int, const double *, int64_t, int, int64_t, double, double *,
-                          int64_t, cudaStream_t);
+                          int64_t, cudaStream_t, bool);
 template int gram<float>(const float *, int64_t, int, const float *, int64_t, int, int64_t, double, double *, int64_t,
-                         cudaStream_t);
+                         cudaStream_t, bool);
 
 // ----------------------------------------------------------- k_rowmul ---
 // Y[p][0:m] = alpha * sum_k X[p][k] C[k][0:m] + beta * Y[p][0:m] for a tile of
@@ -314,11 +328,14 @@ int symmetrize(double *A, int lda, int n, cudaStream_t st) {
 // A (overwritten) and V live in global workspace (L1/L2 resident).  On exit
 // w[0..n) holds the eigenvalues ascending and Vout[:, k] the eigenvectors
 // (FP64); info[0] = sweeps used, or -1 if max_sweeps ran out.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_jacobi(T *A, T *V, int n, int max_sweeps, double tol, double *w,
+template <typename T, bool IN_SMEM>
+__global__ void __launch_bounds__(1024) k_jacobi(T *Ag, T *Vg, int n, int max_sweeps, double tol, double *w,
                                                  double *Vout, int ldv, int *info) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *cs = reinterpret_cast<T *>(smraw);       // [n/2]
+    // small matrices live in shared memory for the whole iteration
+    T *A = IN_SMEM ? reinterpret_cast<T *>(smraw) : Ag;
+    T *V = IN_SMEM ? A + (size_t)n * n : Vg;
+    T *cs = IN_SMEM ? V + (size_t)n * n : reinterpret_cast<T *>(smraw);  // [n/2]
     T *sn = cs + n / 2;                          // [n/2]
     int *pp = reinterpret_cast<int *>(sn + n / 2);
     int *qq = pp + n / 2;
@@ -327,7 +344,10 @@ __global__ void __launch_bounds__(1024) k_jacobi(T *A, T *V, int n, int max_swee
     __shared__ double fro2, off2;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int h = n / 2, m = n - 1;
+    if (IN_SMEM)
+        for (int64_t e = tid; e < (int64_t)n * n; e += nt) A[e] = Ag[e];
     for (int64_t e = tid; e < (int64_t)n * n; e += nt) V[e] = (e / n == e % n) ? T(1) : T(0);
+    __syncthreads();
     auto block_sum = [&](double v) -> double {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         __syncthreads();
@@ -425,6 +445,147 @@ __global__ void __launch_bounds__(1024) k_jacobi(T *A, T *V, int n, int max_swee
     if (tid == 0) info[0] = done ? sweep : -1;
 }
 
+// Multi-CTA variant for matrices too large for one CTA's shared memory: the
+// same rounds, with every CTA computing all rotations of a round redundantly,
+// rows split by rotation pair and columns split by row, and a software grid
+// barrier (bounded spin; on timeout err[0] is set and every CTA returns).
+// All CTAs must be resident (launched cooperatively).
+constexpr long long GRID_SPIN_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks, int *err) {
+    __threadfence();   // every thread publishes its writes before the block arrives
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned my = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd((unsigned *)gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == my) {
+                if (++spins > GRID_SPIN_LIMIT || *(volatile int *)err) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)err == 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_jacobi_grid(T *A, T *V, int n, int max_sweeps, double tol, double *w,
+                                                     double *Vout, int ldv, int *info, unsigned *bar, double *red_g,
+                                                     int *err) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *cs = reinterpret_cast<T *>(smraw);
+    T *sn = cs + n / 2;
+    int *pp = reinterpret_cast<int *>(sn + n / 2);
+    int *qq = pp + n / 2;
+    __shared__ double red[8];
+    const int tid = threadIdx.x, nt = blockDim.x, G = gridDim.x, bid = blockIdx.x;
+    const int h = n / 2, m = n - 1;
+    unsigned *count = bar;
+    volatile unsigned *gen = bar + 1;
+    for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)n * n; e += (int64_t)G * nt) V[e] = (e / n == e % n) ? T(1) : T(0);
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        double t = 0;
+        if (tid == 0)
+            for (int i = 0; i < nt / 32; ++i) t += red[i];
+        __syncthreads();
+        return t;
+    };
+    // Frobenius norm (red_g[0]) and off-diagonal sums per sweep (red_g[1 + sweep])
+    double loc = 0;
+    for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)n * n; e += (int64_t)G * nt) loc += (double)__ldcg(A + e) * (double)__ldcg(A + e);
+    const double f = block_sum(loc);
+    if (tid == 0) atomicAdd(red_g, f);
+    if (!grid_barrier(count, gen, G, err)) return;
+    const double fro2 = *(volatile double *)red_g;
+    int sweep = 0, done = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        loc = 0;
+        for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)n * n; e += (int64_t)G * nt)
+            if (e / n != e % n) loc += (double)__ldcg(A + e) * (double)__ldcg(A + e);
+        const double o = block_sum(loc);
+        if (tid == 0) atomicAdd(red_g + 1 + sweep, o);
+        if (!grid_barrier(count, gen, G, err)) return;
+        if (*(volatile double *)(red_g + 1 + sweep) <= tol * tol * fro2) {
+            done = 1;
+            break;
+        }
+        for (int r = 0; r < m; ++r) {
+            for (int k = tid; k < h; k += nt) {
+                int p, q;
+                if (k == 0) {
+                    p = 0;
+                    q = 1 + r % m;
+                } else {
+                    p = 1 + (r + k) % m;
+                    q = 1 + (r - k + m) % m;
+                }
+                const T apq = __ldcg(A + (int64_t)p * n + q);
+                T c = 1, s_ = 0;
+                if (apq != T(0)) {
+                    const T theta = (__ldcg(A + (int64_t)q * n + q) - __ldcg(A + (int64_t)p * n + p)) / (T(2) * apq);
+                    const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+                    c = T(1) / sqrt(t * t + T(1));
+                    s_ = t * c;
+                }
+                cs[k] = c;
+                sn[k] = s_;
+                pp[k] = p;
+                qq[k] = q;
+            }
+            __syncthreads();
+            if (!grid_barrier(count, gen, G, err)) return;   // every CTA has read the round's pivots
+            // rows: pairs split over CTAs
+            for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)h * n; e += (int64_t)G * nt) {
+                const int k = (int)(e / n), j = (int)(e % n);
+                const int p = pp[k], q = qq[k];
+                const T c = cs[k], s_ = sn[k];
+                const T a = __ldcg(A + (int64_t)p * n + j), b = __ldcg(A + (int64_t)q * n + j);
+                A[(int64_t)p * n + j] = c * a - s_ * b;
+                A[(int64_t)q * n + j] = s_ * a + c * b;
+            }
+            if (!grid_barrier(count, gen, G, err)) return;
+            // columns of A and V: rows split over CTAs
+            for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)h * n; e += (int64_t)G * nt) {
+                const int i = (int)(e / h), k = (int)(e % h);
+                const int p = pp[k], q = qq[k];
+                const T c = cs[k], s_ = sn[k];
+                const T a = __ldcg(A + (int64_t)i * n + p), b = __ldcg(A + (int64_t)i * n + q);
+                A[(int64_t)i * n + p] = c * a - s_ * b;
+                A[(int64_t)i * n + q] = s_ * a + c * b;
+                const T va = __ldcg(V + (int64_t)i * n + p), vb = __ldcg(V + (int64_t)i * n + q);
+                V[(int64_t)i * n + p] = c * va - s_ * vb;
+                V[(int64_t)i * n + q] = s_ * va + c * vb;
+            }
+            if (!grid_barrier(count, gen, G, err)) return;
+        }
+    }
+    // ascending order (ties by index), outputs split over CTAs
+    for (int i = bid * nt + tid; i < n; i += G * nt) {
+        const T di = __ldcg(A + (int64_t)i * n + i);
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const T dj = __ldcg(A + (int64_t)j * n + j);
+            rk += (dj < di) || (dj == di && j < i);
+        }
+        w[rk] = (double)di;
+        for (int k = 0; k < n; ++k) Vout[(int64_t)k * ldv + rk] = (double)__ldcg(V + (int64_t)k * n + i);
+    }
+    if (bid == 0 && tid == 0) info[0] = done ? sweep : -1;
+}
+
 // FP64 -> T copy of an n x n matrix into a dense buffer
 template <typename T> __global__ void k_copy_cast(const double *A, int lda, int n, T *B) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
@@ -440,8 +601,26 @@ int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *
     T *v = a + (size_t)n * n;
     k_copy_cast<T><<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(A, lda, n, a);
     RS_LAUNCH_CHECK();
-    const size_t smem = (size_t)n * sizeof(T) + (size_t)n * 2 * sizeof(int) + (size_t)n * sizeof(int);
-    k_jacobi<T><<<1, 1024, smem, st>>>(a, v, n, max_sweeps, tol, w, V, ldv, info);
+    const size_t small = (size_t)n * sizeof(T) + (size_t)n * 3 * sizeof(int) + 64;
+    const size_t full = small + 2 * (size_t)n * n * sizeof(T);
+    if (full <= 200 * 1024) {
+        RS_CUDA(cudaFuncSetAttribute(k_jacobi<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full));
+        k_jacobi<T, true><<<1, 1024, full, st>>>(a, v, n, max_sweeps, tol, w, V, ldv, info);
+        RS_LAUNCH_CHECK();
+        return RS_OK;
+    }
+    // grid variant: barrier words, reduction slots and the error flag follow V in the scratch
+    unsigned *bar = reinterpret_cast<unsigned *>(v + (size_t)n * n);
+    double *red_g = reinterpret_cast<double *>(bar + 4);
+    int *err = reinterpret_cast<int *>(red_g + max_sweeps + 2);
+    RS_CUDA(cudaMemsetAsync(bar, 0, 16 + sizeof(double) * (max_sweeps + 2) + 16, st));
+    int nsm = 0, dev = 0, per_sm = 0;
+    RS_CUDA(cudaGetDevice(&dev));
+    RS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_grid<T>, 256, small));
+    const int G = std::max(1, std::min({n / 2, nsm * std::max(per_sm, 1), 128}));
+    void *args[] = {&a, &v, &n, &max_sweeps, &tol, &w, &V, &ldv, &info, &bar, &red_g, &err};
+    RS_CUDA(cudaLaunchCooperativeKernel((const void *)k_jacobi_grid<T>, dim3(G), dim3(256), args, small, st));
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
@@ -574,7 +753,7 @@ __global__ void k_copy_block(const double *A, int lda, int m, int n, double *B, 
 size_t eigh_work_bytes(int n) {
     const size_t ne = (size_t)n + (n & 1);
     // padded A, Jacobi scratch (2 ne^2), Jacobi vectors, eigenvalues, refinement (4 n^2 + 1), scalars
-    return sizeof(double) * (ne * ne * 4 + ne + 4 * (size_t)n * n + 64);
+    return sizeof(double) * (ne * ne * 4 + ne + 4 * (size_t)n * n + 192);
 }
 
 int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int refine, int *info_dev, void *work,
@@ -582,7 +761,7 @@ int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int ref
     const int ne = n + (n & 1);
     double *Ap = reinterpret_cast<double *>(work);
     double *jscr = Ap + (size_t)ne * ne;
-    double *Vp = jscr + 2 * (size_t)ne * ne;
+    double *Vp = jscr + 2 * (size_t)ne * ne + 64;
     double *wp = Vp + (size_t)ne * ne;
     double *rwork = wp + ne;
     double *big = rwork + 4 * (size_t)n * n + 1;
@@ -598,16 +777,41 @@ int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int ref
         k_copy_block<<<1, 32, 0, st>>>(big, 1, 1, 1, Ap + (size_t)(ne - 1) * ne + (ne - 1), 1);
         RS_LAUNCH_CHECK();
     }
-    if (refine > 0) {
-        RS_TRY(jacobi<float>(Ap, ne, ne, 30, 2e-6, wp, Vp, ne, info_dev, jscr, st));
+    // FP32 stops at its rounding floor (~u sqrt(n) of the Frobenius norm); FP64
+    // at 1e-13 of it
+    const double tol32 = std::max(2e-6, 2.4e-7 * std::sqrt((double)ne));
+    if (refine != 0) {
+        RS_TRY(jacobi<float>(Ap, ne, ne, 30, tol32, wp, Vp, ne, info_dev, jscr, st));
     } else {
-        RS_TRY(jacobi<double>(Ap, ne, ne, 60, 1e-15, wp, Vp, ne, info_dev, jscr, st));
+        RS_TRY(jacobi<double>(Ap, ne, ne, 60, 1e-13, wp, Vp, ne, info_dev, jscr, st));
     }
     // leading n x n block: eigenvectors of A (the pad entry is decoupled and sorts last)
     k_copy_block<<<eb, 256, 0, st>>>(Vp, ne, n, n, V, ldv);
     k_copy_block<<<1, 256, 0, st>>>(wp, ne, 1, n, w, n);
     RS_LAUNCH_CHECK();
-    if (refine > 0) RS_TRY(refsyev(A, lda, V, ldv, n, w, rwork, refine, st));
+    if (refine <= 0) return RS_OK;
+    RS_TRY(refsyev(A, lda, V, ldv, n, w, rwork, refine, st));
+    if (n & 1) return RS_OK;
+    const size_t nn = (size_t)n * n;
+    double *AX = rwork, *B = rwork + nn, *Q = rwork + 2 * nn, *T = rwork + 3 * nn;
+    // make V orthonormal to FP64 accuracy (V^T V = U^T U, V <- V U^-1), so that
+    // B = V^T A V has exactly the eigenvalues of A ...
+    RS_TRY(gemm_small(n, n, n, 1.0, V, ldv, true, V, ldv, false, 0.0, B, n, st));
+    RS_TRY(symmetrize(B, n, n, st));
+    RS_TRY(cholesky(B, n, n, 0.0, info_dev, st));
+    RS_TRY(tri_inv(B, n, n, Q, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, V, ldv, false, Q, n, false, 0.0, T, n, st));
+    k_copy_block<<<eb, 256, 0, st>>>(T, n, n, n, V, ldv);
+    RS_LAUNCH_CHECK();
+    // ... and diagonalise B, which is diagonal up to the couplings the FP32
+    // start and the refinement left, with FP64 Jacobi: V <- V Q, B = Q diag(w) Q^T
+    RS_TRY(gemm_small(n, n, n, 1.0, A, lda, false, V, ldv, false, 0.0, AX, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, V, ldv, true, AX, n, false, 0.0, B, n, st));
+    RS_TRY(symmetrize(B, n, n, st));
+    RS_TRY(jacobi<double>(B, n, n, 10, 1e-13, w, Q, n, info_dev, jscr, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, V, ldv, false, Q, n, false, 0.0, T, n, st));
+    k_copy_block<<<eb, 256, 0, st>>>(T, n, n, n, V, ldv);
+    RS_LAUNCH_CHECK();
     return RS_OK;
 }
 

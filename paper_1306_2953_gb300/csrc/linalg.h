@@ -10,9 +10,11 @@
 namespace rs {
 
 // S = dV X^T Y (nx x ny, FP64, row stride lds); X, Y are [npts][ld] of T.
+// FP32 data: exact products with compensated accumulation, or (fast) plain
+// FP32 accumulation within chunks of points combined in FP64.
 template <typename T>
 int gram(const T *X, int64_t ldx, int nx, const T *Y, int64_t ldy, int ny, int64_t npts, double dV, double *S,
-         int64_t lds, cudaStream_t st);
+         int64_t lds, cudaStream_t st, bool fast = false);
 
 // Y = alpha X C + beta Y row by row; X [npts][ldx] (n columns), C FP64 [n][ldc]
 // (m columns), Y [npts][ldy]; Y may alias X when beta == 0.
@@ -40,9 +42,10 @@ int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *
 int refsyev(const double *A, int lda, double *X, int ldx, int n, double *lam, double *work, int iters,
             cudaStream_t st);
 
-// Symmetric eigendecomposition A = V diag(w) V^T (ascending), FP64 result:
-// FP32 Jacobi followed by `refine` FP64 refinement steps (refine = 0:
-// FP64 Jacobi).  work: eigh_work_bytes(n).
+// Symmetric eigendecomposition A = V diag(w) V^T (ascending), FP64 result.
+// refine > 0: FP32 Jacobi, `refine` Ogita-Aishima FP64 refinement steps and an
+// FP64 Jacobi polish of V^T A V; refine = 0: FP64 Jacobi; refine < 0: FP32
+// Jacobi only.  work: eigh_work_bytes(n).
 size_t eigh_work_bytes(int n);
 int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int refine, int *info_dev, void *work,
          cudaStream_t st);
@@ -65,12 +68,23 @@ struct LaWork {
     static size_t bytes(int n) { return sizeof(double) * ((size_t)4 * n * n + n + 8) + eigh_work_bytes(n) + 256; }
 };
 
-// Psi (n columns) <- Psi C in place (C FP64 n x n).
-int rotate_inplace(void *Psi, int64_t ld, int n, const double *C, int64_t npts, int dtype, cudaStream_t st);
+// Tensor-core workspace for FP32 contractions (optional): base pointer,
+// its size, and a device status word set when a tensor-core wait times out.
+struct TcWork {
+    void *p = nullptr;
+    int64_t bytes = 0;
+    int *err = nullptr;
+};
+
+// Psi (n columns) <- Psi C in place (C FP64 n x n); FP32 data on the tensor
+// cores when tc.p is set and large enough.
+int rotate_inplace(void *Psi, int64_t ld, int n, const double *C, int64_t npts, int dtype, cudaStream_t st,
+                   const TcWork &tc = TcWork());
 // Psi <- Psi U^-1 with <Psi|Psi> = U^T U; w.Ui keeps U^-1.  Blocking; RS_ENOTSPD on failure.
-int orthonormalize_impl(int64_t npts, double dV, void *Psi, int64_t ld, int n, int dtype, void *work, cudaStream_t st);
+int orthonormalize_impl(int64_t npts, double dV, void *Psi, int64_t ld, int n, int dtype, void *work, cudaStream_t st,
+                        const TcWork &tc = TcWork());
 // HPsi = H Psi, h = <Psi|H|Psi>, h xi = xi diag(eps), Psi <- Psi xi, HPsi <- HPsi xi; w.xi keeps xi.
 int subspace_diag_impl(rs_ham *h, void *Psi, void *HPsi, int64_t ld, int n, int dtype, int nb, void *work,
-                       double *eps_dev, cudaStream_t st);
+                       double *eps_dev, cudaStream_t st, const TcWork &tc = TcWork());
 
 }  // namespace rs

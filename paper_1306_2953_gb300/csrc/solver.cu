@@ -26,6 +26,7 @@
 #include "ham.h"
 #include "linalg.h"
 #include "precond.h"
+#include "umma.h"
 
 using namespace rs;
 
@@ -122,7 +123,8 @@ struct rs_solver {
     double dV = 0;
     int es = 8;
     int nblk = 0;
-    DevBuf psi, hpsi, P, Z, HZ, R, small, la, eig, res;
+    DevBuf psi, hpsi, P, Z, HZ, R, small, la, eig, res, tcbuf;
+    TcWork tc;
     std::vector<char> has_p;
     Precond *pc = nullptr;
     // small FP64 buffers (inside `small`)
@@ -146,17 +148,23 @@ int copy_cols(int dtype, const void *S, int64_t lds, void *D, int64_t ldd, int n
     return RS_OK;
 }
 
+// inner-iteration contractions: FP32 mode on the tensor cores (FP32-level
+// accuracy), FP64 mode on the FP64 pipes
 int gram_any(int dtype, const void *X, int64_t ldx, int nx, const void *Y, int64_t ldy, int ny, int64_t npts, double dV,
-             double *S, int64_t lds, cudaStream_t st) {
+             double *S, int64_t lds, cudaStream_t st, const TcWork &tc) {
     if (dtype == RS_F64)
         return gram<double>((const double *)X, ldx, nx, (const double *)Y, ldy, ny, npts, dV, S, lds, st);
-    return gram<float>((const float *)X, ldx, nx, (const float *)Y, ldy, ny, npts, dV, S, lds, st);
+    if (tc.p && tc.bytes >= umma_work_bytes(nx, ny, npts))
+        return umma_gram((const float *)X, ldx, nx, (const float *)Y, ldy, ny, npts, dV, S, lds, tc.p, tc.err, st);
+    return gram<float>((const float *)X, ldx, nx, (const float *)Y, ldy, ny, npts, dV, S, lds, st, true);
 }
 
 int rowmul_any(int dtype, const void *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, void *Y, int64_t ldy,
-               int64_t npts, double alpha, double beta, cudaStream_t st) {
+               int64_t npts, double alpha, double beta, cudaStream_t st, const TcWork &tc) {
     if (dtype == RS_F64)
         return rowmul<double>((const double *)X, ldx, n, C, ldc, m, (double *)Y, ldy, npts, alpha, beta, st);
+    if (tc.p && tc.bytes >= umma_work_bytes(npts, m, n))
+        return umma_rowmul((const float *)X, ldx, n, C, ldc, m, (float *)Y, ldy, npts, alpha, beta, tc.p, tc.err, st);
     return rowmul<float>((const float *)X, ldx, n, C, ldc, m, (float *)Y, ldy, npts, alpha, beta, st);
 }
 
@@ -209,8 +217,8 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
     // 3. classical Gram-Schmidt, twice, against Psi[:, :(b+1) nb]
     const int nq = (b + 1) * nb;
     for (int pass = 0; pass < 2; ++pass) {
-        RS_TRY(gram_any(dt, S->psi.p, nst, nq, Y, ldz, ny, np, S->dV, S->M, ny, st));
-        RS_TRY(rowmul_any(dt, S->psi.p, nst, nq, S->M, ny, ny, Y, ldz, np, -1.0, 1.0, st));
+        RS_TRY(gram_any(dt, S->psi.p, nst, nq, Y, ldz, ny, np, S->dV, S->M, ny, st, S->tc));
+        RS_TRY(rowmul_any(dt, S->psi.p, nst, nq, S->M, ny, ny, Y, ldz, np, -1.0, 1.0, st, S->tc));
     }
     RS_TRY(coldots(dt, Y, ldz, Y, ldz, ny, np, nrm, st));
     if (dt == RS_F64)
@@ -225,8 +233,8 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
 
     // 5. Rayleigh-Ritz on Z = [X, Y]
     int n = nb + ny;
-    RS_TRY(gram_any(dt, S->Z.p, ldz, n, S->Z.p, ldz, n, np, S->dV, S->G, n, st));
-    RS_TRY(gram_any(dt, S->Z.p, ldz, n, S->HZ.p, ldz, n, np, S->dV, S->A, n, st));
+    RS_TRY(gram_any(dt, S->Z.p, ldz, n, S->Z.p, ldz, n, np, S->dV, S->G, n, st, S->tc));
+    RS_TRY(gram_any(dt, S->Z.p, ldz, n, S->HZ.p, ldz, n, np, S->dV, S->A, n, st, S->tc));
     RS_TRY(symmetrize(S->G, n, n, st));
     RS_TRY(symmetrize(S->A, n, n, st));
     int bad = 1;
@@ -237,7 +245,9 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
         }
         k_copy_leading<<<64, 256, 0, st>>>(S->G, nb + ny, n, S->U, n);
         RS_LAUNCH_CHECK();
-        RS_TRY(cholesky(S->U, n, n, 1e-12, S->status, st));
+        // a pivot below what the Gram matrix's own accuracy resolves means the
+        // search space is numerically dependent (FP32 mode: FP32-accumulated G)
+        RS_TRY(cholesky(S->U, n, n, dt == RS_F32 ? 1e-5 : 1e-12, S->status, st));
         RS_CUDA(cudaMemcpyAsync(&bad, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
         RS_CUDA(cudaStreamSynchronize(st));
     }
@@ -247,13 +257,14 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
     RS_TRY(gemm_small(n, n, n, 1.0, S->Ui, n, true, S->A, lda, false, 0.0, S->T1, n, st));
     RS_TRY(gemm_small(n, n, n, 1.0, S->T1, n, false, S->Ui, n, false, 0.0, S->At, n, st));
     RS_TRY(symmetrize(S->At, n, n, st));
-    RS_TRY(eigh(S->At, n, n, S->mu, S->Yv, n, 3, S->status, S->eighw, st));
+    // inner Rayleigh-Ritz: FP32 Jacobi is enough in FP32 mode; FP64 mode refines
+    RS_TRY(eigh(S->At, n, n, S->mu, S->Yv, n, dt == RS_F32 ? -1 : 2, S->status, S->eighw, st));
     RS_TRY(gemm_small(n, nb, n, 1.0, S->Ui, n, false, S->Yv, n, false, 0.0, S->C, nb, st));
 
     // 6. X <- Z C, P <- Z[:, nb:n] C[nb:n, :]
-    RS_TRY(rowmul_any(dt, S->Z.p, ldz, n, S->C, nb, nb, offw(S->psi, (int64_t)b * nb, es), nst, np, 1.0, 0.0, st));
+    RS_TRY(rowmul_any(dt, S->Z.p, ldz, n, S->C, nb, nb, offw(S->psi, (int64_t)b * nb, es), nst, np, 1.0, 0.0, st, S->tc));
     RS_TRY(rowmul_any(dt, offw(S->Z, nb, es), ldz, n - nb, S->C + (size_t)nb * nb, nb, nb,
-                      offw(S->P, (int64_t)b * nb, es), nst, np, 1.0, 0.0, st));
+                      offw(S->P, (int64_t)b * nb, es), nst, np, 1.0, 0.0, st, S->tc));
     S->has_p[b] = 1;
     return RS_OK;
 }
@@ -290,6 +301,15 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
         (rc = S->la.alloc(LaWork::bytes(c.nst))) || (rc = S->eig.alloc(sizeof(double) * c.nst)) ||
         (rc = S->res.alloc(sizeof(double) * c.nst)))
         return bail(rc);
+    if (c.dtype == RS_F32) {
+        const int64_t need = std::max({umma_work_bytes(c.nst, 2 * c.nb, S->npts), umma_work_bytes(S->npts, c.nst, c.nst),
+                                       umma_work_bytes(3 * c.nb, 3 * c.nb, S->npts)});
+        if ((rc = S->tcbuf.alloc((size_t)need + 256))) return bail(rc);
+        S->tc.p = S->tcbuf.p;
+        S->tc.bytes = need;
+        S->tc.err = reinterpret_cast<int *>((char *)S->tcbuf.p + need);
+        if (cudaMemset(S->tc.err, 0, sizeof(int)) != cudaSuccess) return bail(fail(RS_ECUDA, "cudaMemset failed"));
+    }
     const int n3 = 3 * c.nb;
     const size_t smallbytes = sizeof(double) * (512 + (size_t)c.nst * 2 * c.nb + 7 * (size_t)n3 * n3 + n3 + (size_t)n3 * c.nb) +
                               64 + eigh_work_bytes(n3);
@@ -314,8 +334,9 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
     if (cudaMemcpyAsync(S->psi.p, Psi0_dev, big, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(S->P.p, 0, big, st) != cudaSuccess || cudaMemsetAsync(S->res.p, 0, sizeof(double) * c.nst, st) != cudaSuccess)
         return bail(fail(RS_ECUDA, "rs_solver_create: copy failed"));
-    if ((rc = orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st))) return bail(rc);
-    if ((rc = subspace_diag_impl(h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st)))
+    if ((rc = orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st, S->tc))) return bail(rc);
+    if ((rc = subspace_diag_impl(h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st,
+                                 S->tc)))
         return bail(rc);
     if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(RS_ECUDA, "rs_solver_create: sync failed"));
     *out = S;
@@ -327,16 +348,20 @@ extern "C" int rs_eigensolver_step(rs_solver *S, double *eps_dev, double *resnor
     cudaStream_t st = (cudaStream_t)stream;
     const rs_solver_cfg &c = S->cfg;
     for (int b = 0; b < S->nblk; ++b) RS_TRY(block_step(S, b, st));
-    RS_TRY(orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st));
+    RS_TRY(orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st, S->tc));
     LaWork w(S->la.p, c.nst);
-    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.Ui, S->npts, c.dtype, st));
-    RS_TRY(subspace_diag_impl(S->h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st));
-    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.xi, S->npts, c.dtype, st));
+    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.Ui, S->npts, c.dtype, st, S->tc));
+    RS_TRY(subspace_diag_impl(S->h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st,
+                              S->tc));
+    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.xi, S->npts, c.dtype, st, S->tc));
     if (eps_dev) RS_CUDA(cudaMemcpyAsync(eps_dev, S->eig.p, sizeof(double) * c.nst, cudaMemcpyDeviceToDevice, st));
     if (resnorm_dev) RS_CUDA(cudaMemcpyAsync(resnorm_dev, S->res.p, sizeof(double) * c.nst, cudaMemcpyDeviceToDevice, st));
     std::vector<double> res(c.nst);
     RS_CUDA(cudaMemcpyAsync(res.data(), S->res.p, sizeof(double) * c.nst, cudaMemcpyDeviceToHost, st));
+    int tcerr = 0;
+    if (S->tc.err) RS_CUDA(cudaMemcpyAsync(&tcerr, S->tc.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     RS_CUDA(cudaStreamSynchronize(st));
+    if (tcerr) return fail(RS_ECUDA, "eigensolver: a tensor-core pipeline wait timed out");
     if (n_converged) {
         int k = 0;
         for (double r : res) k += r <= c.tol;

@@ -8,6 +8,7 @@
 #include "device.h"
 #include "ham.h"
 #include "linalg.h"
+#include "umma.h"
 
 using namespace rs;
 
@@ -46,13 +47,17 @@ extern "C" int64_t rs_linalg_workspace_bytes(int nst) {
 
 namespace rs {
 
-int rotate_inplace(void *Psi, int64_t ld, int n, const double *C, int64_t npts, int dtype, cudaStream_t st) {
+int rotate_inplace(void *Psi, int64_t ld, int n, const double *C, int64_t npts, int dtype, cudaStream_t st,
+                   const TcWork &tc) {
     if (dtype == RS_F64) return rowmul<double>((const double *)Psi, ld, n, C, n, n, (double *)Psi, ld, npts, 1.0, 0.0, st);
+    if (tc.p && tc.bytes >= umma_work_bytes(npts, n, n))
+        return umma_rowmul((const float *)Psi, ld, n, C, n, n, (float *)Psi, ld, npts, 1.0, 0.0, tc.p, tc.err, st);
     return rowmul<float>((const float *)Psi, ld, n, C, n, n, (float *)Psi, ld, npts, 1.0, 0.0, st);
 }
 
 // Orthonormalise Psi in place; Ui (n x n) receives U^-1.  Blocking.
-int orthonormalize_impl(int64_t npts, double dV, void *Psi, int64_t ld, int n, int dtype, void *work, cudaStream_t st) {
+int orthonormalize_impl(int64_t npts, double dV, void *Psi, int64_t ld, int n, int dtype, void *work, cudaStream_t st,
+                        const TcWork &tc) {
     LaWork w(work, n);
     if (dtype == RS_F64)
         RS_TRY(gram<double>((const double *)Psi, ld, n, (const double *)Psi, ld, n, npts, dV, w.U, n, st));
@@ -65,12 +70,12 @@ int orthonormalize_impl(int64_t npts, double dV, void *Psi, int64_t ld, int n, i
     RS_CUDA(cudaStreamSynchronize(st));
     if (bad) return fail(RS_ENOTSPD, "orthonormalize: overlap matrix not positive definite (pivot %d)", bad - 1);
     RS_TRY(tri_inv(w.U, n, n, w.Ui, n, st));
-    return rotate_inplace(Psi, ld, n, w.Ui, npts, dtype, st);
+    return rotate_inplace(Psi, ld, n, w.Ui, npts, dtype, st, tc);
 }
 
 // Subspace diagonalisation; eps (device, n) and w.xi receive the results.  Blocking.
 int subspace_diag_impl(rs_ham *h, void *Psi, void *HPsi, int64_t ld, int n, int dtype, int nb, void *work,
-                       double *eps_dev, cudaStream_t st) {
+                       double *eps_dev, cudaStream_t st, const TcWork &tc) {
     LaWork w(work, n);
     const int64_t npts = ham_npts(h);
     const double dV = ham_dV(h);
@@ -83,9 +88,9 @@ int subspace_diag_impl(rs_ham *h, void *Psi, void *HPsi, int64_t ld, int n, int 
     else
         RS_TRY(gram<float>((const float *)Psi, ld, n, (const float *)HPsi, ld, n, npts, dV, w.S, n, st));
     RS_TRY(symmetrize(w.S, n, n, st));
-    RS_TRY(eigh(w.S, n, n, eps_dev, w.xi, n, 3, w.status, w.eigw, st));
-    RS_TRY(rotate_inplace(Psi, ld, n, w.xi, npts, dtype, st));
-    return rotate_inplace(HPsi, ld, n, w.xi, npts, dtype, st);
+    RS_TRY(eigh(w.S, n, n, eps_dev, w.xi, n, 2, w.status, w.eigw, st));
+    RS_TRY(rotate_inplace(Psi, ld, n, w.xi, npts, dtype, st, tc));
+    return rotate_inplace(HPsi, ld, n, w.xi, npts, dtype, st, tc);
 }
 
 }  // namespace rs
@@ -118,5 +123,23 @@ extern "C" int rs_subspace_diag(rs_ham *h, void *Psi_dev, void *HPsi_dev, int64_
     RS_CUDA(cudaMemcpyAsync(&info, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     RS_CUDA(cudaStreamSynchronize(st));
     (void)info;  // FP32 Jacobi may stop at its sweep cap; the FP64 refinement that follows decides the accuracy
+    return RS_OK;
+}
+
+extern "C" int64_t rs_eigh_workspace_bytes(int n) {
+    if (n < 1) return -1;
+    return (int64_t)eigh_work_bytes(n) + 64;
+}
+
+extern "C" int rs_eigh(const double *A_dev, int n, double *w_dev, double *V_dev, int refine, void *work_dev,
+                       void *stream) {
+    if (!A_dev || !w_dev || !V_dev || !work_dev || n < 2) return fail(RS_EINVAL, "rs_eigh: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    int *info = reinterpret_cast<int *>((char *)work_dev + eigh_work_bytes(n));
+    RS_TRY(eigh(A_dev, n, n, w_dev, V_dev, n, refine, info, work_dev, st));
+    int sweeps = 0;
+    RS_CUDA(cudaMemcpyAsync(&sweeps, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    if (refine == 0 && sweeps < 0) return fail(RS_ENOCONV, "rs_eigh: Jacobi sweep cap reached");
     return RS_OK;
 }

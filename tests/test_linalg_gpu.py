@@ -88,13 +88,12 @@ def _align_signs(V, R):
     return V * s
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_subspace_diag_parity(dtype):
+@pytest.mark.parametrize("dtype,nst", [("f64", 24), ("f32", 24), ("f64", 256)])
+def test_subspace_diag_parity(dtype, nst):
     from paper_1306_2953_gb300 import api
     from oracle import linalg as ol
     lg, H, g_ora, H_ora, idx = _lib_system(*SYS)
-    nst = 24
-    psi = wl.gaussian_sum_block(g_ora.coords, nst, 12)
+    psi = wl.gaussian_sum_block(g_ora.coords, nst, 12) if nst <= 32 else wl.random_block(g_ora.npts, nst, 12)
     psi, _ = ol.orthonormalize(psi, g_ora.dV)
     t = torch.float64 if dtype == "f64" else torch.float32
     if dtype == "f32":

@@ -99,3 +99,21 @@ def test_solver_bad_config():
     psi0 = torch.zeros((g_ora.npts, 12), dtype=torch.float64, device="cuda")
     with pytest.raises(RsError):
         api.Solver(H, psi0, 8, 1e-6)          # nst not a multiple of nb
+
+
+def test_mol20_mixed_precision_within_1e6_of_oracle():
+    """FP32 orbitals, H psi and inner iterations (tensor-core contractions),
+    FP64 Gram matrices, Cholesky, Rayleigh-Ritz and eigenvalues: every state
+    within 1e-6 Ha of the oracle's FP64 eigenvalues."""
+    from paper_1306_2953_gb300 import api
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0[idx])).float().cuda(), w.block, 1e-4)
+    ref = np.array(golden(w.name)["eigenvalues"])
+    for it in range(600):
+        eps, res, _ = S.step()
+        e = eps.cpu().numpy()
+        if np.abs(e[:w.judged] - ref).max() <= 1e-6 and np.all(res.cpu().numpy()[:w.judged] <= 1e-4):
+            break
+    assert np.abs(e[:w.judged] - ref).max() <= 1e-6
