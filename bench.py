@@ -168,6 +168,88 @@ def run_reference(args, workload):
     return 0
 
 
+def load_golden(name):
+    p = os.path.join(ROOT, "tests", "golden", f"eigs_{name}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)
+
+
+def build_any(workload):
+    """Library grid + Hamiltonian of a workload (molecule or oscillator box)."""
+    from paper_1306_2953_gb300 import api
+    s = workload.system
+    if isinstance(s, wl.BoxSpec):
+        g = api.Grid.box(s.n, s.n, s.n, s.h)
+        return g, api.Hamiltonian(g, wl.harmonic_potential(g.coords(), s.omega))
+    return build_system(workload)
+
+
+def train_learned(H, g, solver, n_res=40, n_tiles=10000, epochs=3, seed=11):
+    """Learned-preconditioner weights from the method's own residuals: Ritz
+    residuals of the current orbitals, their 200-iteration shifted-Poisson CG
+    solutions, and Adam on tiles cut from the pairs."""
+    import torch
+    from paper_1306_2953_gb300 import api
+    Hs = api.Hamiltonian(g, np.full(g.npts, 1.0))
+    ncols = 1 << (max(n_res, 1) - 1).bit_length()     # power of two for the block CG
+    R = solver.residual(0, min(ncols, solver.nst)).float().contiguous()
+    X = torch.empty_like(R)
+    for b in range(0, R.shape[1], 32):
+        X[:, b:b + 32] = api.shifted_poisson_cg(Hs, R[:, b:b + 32].contiguous(), 200)
+    w = torch.from_numpy(np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel()
+                                         for a in wl.conv_init(seed)]).astype(np.float32)).cuda()
+    losses = api.precond_train(Hs, R[:, :n_res].contiguous(), X[:, :n_res].contiguous(), w, n_tiles=n_tiles,
+                               epochs=epochs, batch=64, seed=seed)
+    return w, losses
+
+
+def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
+    """Seconds until every judged eigenvalue is within tol Ha of the oracle's
+    reference (tests/golden), for each precision / preconditioner mode."""
+    import torch
+    from paper_1306_2953_gb300 import api, _lib
+    gold = load_golden(workload.name)
+    if gold is None:
+        return {"workload": workload.name, "unavailable": "no oracle reference eigenvalues for this workload"}
+    ref = np.array(gold["eigenvalues"])
+    judged = len(ref)
+    g, H = build_any(workload)
+    out = {"workload": workload.name, "npts": g.npts, "states": workload.n_states, "judged": judged,
+           "tolerance_ha": tol, "reference": "oracle block CG (tests/golden)", "modes": {}}
+    psi0 = wl.random_block(g.npts, workload.n_states, workload.seed)
+    for mode in modes:
+        dt = torch.float64 if mode.startswith("f64") else torch.float32
+        pc = _lib.RS_PRECOND_LEARNED if mode.endswith("learned") else _lib.RS_PRECOND_FILTER
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = api.Solver(H, torch.from_numpy(psi0).to(dt).cuda(), workload.block, 1e-4, precond=pc)
+        train_s, losses = 0.0, None
+        if pc == _lib.RS_PRECOND_LEARNED:
+            t1 = time.perf_counter()
+            w, losses = train_learned(H, g, S)
+            S.set_precond_weights(w)
+            torch.cuda.synchronize()
+            train_s = time.perf_counter() - t1
+        sweeps, err = 0, float("inf")
+        while True:
+            eps, res, _ = S.step()
+            sweeps += 1
+            r = res.cpu().numpy()[:judged]
+            if dt == torch.float32 and np.all(r <= 1e-4):
+                # FP32 mode: close with an FP64 Rayleigh-Ritz of the subspace
+                eps = S.rayleigh_ritz_f64()
+            err = float(np.abs(eps.cpu().numpy()[:judged] - ref).max())
+            el = time.perf_counter() - t0
+            if err <= tol or el > max_seconds:
+                break
+        out["modes"][mode] = {"seconds": el, "train_seconds": train_s, "sweeps": sweeps, "max_error_ha": err,
+                              "converged": err <= tol, "train_losses": losses}
+        del S
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,6 +258,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=wl.MOL100.name, choices=[wl.MOL100.name, wl.MOL300.name])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eigensolve", default="mol20_h0.35",
+                    help="workload(s) for the time-to-1e-6 Ha eigensolve, comma separated, or 'none'")
     args = ap.parse_args()
     workload = wl.WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -276,6 +360,9 @@ def main():
         line["cpu_baseline"] = {"value": by / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
                                 "sample": f"FP64 oracle H psi on one block of {NB} states of {workload.name} "
                                           f"({dt:.2f} s per block)"}
+    if rank == 0 and world == 1 and args.eigensolve != "none":
+        line["eigensolve"] = [eigensolve_bench(wl.WORKLOADS[n], ["mixed_learned", "mixed_filter", "f64_filter"])
+                              for n in args.eigensolve.split(",")]
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -338,6 +338,23 @@ typedef struct {
 int rs_precond_train(rs_ham *h, const rs_grid *g, const float *R_dev, const float *X_dev, int64_t ld, int ncols,
                      const rs_train_cfg *cfg, float *w_dev, float *loss_host, void *stream);
 
+/* FP64 Rayleigh-Ritz of the solver's current subspace (Sec. VI, Eq. 7): the
+ * FP32 orbitals of an RS_F32 solver are widened to FP64, H is applied in
+ * FP64, and h x = eps S x is solved with h and S accumulated in FP64, giving
+ * eigenvalues free of the FP32 rounding of H (its potential and stencil
+ * weights) -- the closing step of the mixed-precision eigensolve.  The
+ * iteration state is not modified.  For RS_F64 solvers it returns the
+ * current eigenvalues.  eps_dev: device double [nst].  Blocking; the first
+ * call allocates two FP64 copies of the orbitals. */
+int rs_solver_rayleigh_ritz_f64(rs_solver *s, double *eps_dev, void *stream);
+
+/* Ritz residuals R = H psi_k - eps_k psi_k of states first..first+ncols-1
+ * of the current orbitals (after the last sweep's subspace diagonalisation),
+ * into R_dev [npts][ldr] (the solver's dtype): the residuals the method
+ * generates, used as training inputs of the learned preconditioner.
+ * Asynchronous. */
+int rs_solver_residual(rs_solver *s, int first, int ncols, void *R_dev, int64_t ldr, void *stream);
+
 /* The solver's current orbitals: device [npts][nst] (dtype), owned by the
  * solver; valid until rs_solver_destroy. */
 int rs_solver_psi(rs_solver *s, void **psi_dev);

@@ -256,8 +256,23 @@ class Solver:
         call("rs_solver_psi", self._h, ctypes.byref(p))
         return _device_view(p.value, (self.ham.npts, self.nst), self.dtype, self.device)
 
-    def set_precond_weights(self, w1, w2, w3):
-        call("rs_solver_set_precond_weights", self._h, _c(w1.data_ptr()), _c(w2.data_ptr()), _c(w3.data_ptr()))
+    def set_precond_weights(self, w):
+        """Learned-preconditioner weights: FP32 device tensor of 2160 values."""
+        call("rs_solver_set_precond_weights", self._h, _c(w.data_ptr()))
+
+    def rayleigh_ritz_f64(self, stream=None):
+        """FP64 eigenvalues of the current subspace (closing step of FP32 mode)."""
+        import torch
+        eps = torch.empty(self.nst, dtype=torch.float64, device=self.device)
+        call("rs_solver_rayleigh_ritz_f64", self._h, _c(eps.data_ptr()), _stream(stream))
+        return eps
+
+    def residual(self, first: int, ncols: int, stream=None):
+        """Ritz residuals of states first..first+ncols-1 as a device tensor."""
+        import torch
+        R = torch.empty((self.ham.npts, ncols), dtype=self.dtype, device=self.device)
+        call("rs_solver_residual", self._h, first, ncols, _c(R.data_ptr()), R.stride(0), _stream(stream))
+        return R
 
     def close(self):
         if self._h:

@@ -123,7 +123,7 @@ struct rs_solver {
     double dV = 0;
     int es = 8;
     int nblk = 0;
-    DevBuf psi, hpsi, P, Z, HZ, R, small, la, eig, res, tcbuf;
+    DevBuf psi, hpsi, P, Z, HZ, R, small, la, eig, res, tcbuf, psi64, hpsi64, rr64;
     TcWork tc;
     std::vector<char> has_p;
     Precond *pc = nullptr;
@@ -367,6 +367,77 @@ extern "C" int rs_eigensolver_step(rs_solver *S, double *eps_dev, double *resnor
         for (double r : res) k += r <= c.tol;
         *n_converged = k;
     }
+    return RS_OK;
+}
+
+template <typename T>
+__global__ void k_ritz_residual(const T *__restrict__ X, const T *__restrict__ HX, int64_t ld, const double *__restrict__ eps,
+                                int first, int ncols, int64_t npts, T *__restrict__ R, int64_t ldr) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = t / ncols;
+    const int k = (int)(t % ncols);
+    if (p >= npts) return;
+    R[p * ldr + k] = HX[p * ld + first + k] - (T)eps[first + k] * X[p * ld + first + k];
+}
+
+extern "C" int rs_solver_residual(rs_solver *S, int first, int ncols, void *R_dev, int64_t ldr, void *stream) {
+    if (!S || !R_dev) return fail(RS_EINVAL, "rs_solver_residual: null argument");
+    if (first < 0 || ncols < 1 || first + ncols > S->cfg.nst || ldr < ncols)
+        return fail(RS_EINVAL, "rs_solver_residual: bad state range");
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((S->npts * ncols + 255) / 256);
+    if (S->cfg.dtype == RS_F64)
+        k_ritz_residual<double><<<blocks, 256, 0, st>>>(S->psi.as<double>(), S->hpsi.as<double>(), S->cfg.nst,
+                                                        S->eig.as<double>(), first, ncols, S->npts, (double *)R_dev, ldr);
+    else
+        k_ritz_residual<float><<<blocks, 256, 0, st>>>(S->psi.as<float>(), S->hpsi.as<float>(), S->cfg.nst,
+                                                       S->eig.as<double>(), first, ncols, S->npts, (float *)R_dev, ldr);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
+__global__ void k_widen(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = (double)a[e];
+}
+
+extern "C" int rs_solver_rayleigh_ritz_f64(rs_solver *S, double *eps_dev, void *stream) {
+    if (!S || !eps_dev) return fail(RS_EINVAL, "rs_solver_rayleigh_ritz_f64: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const rs_solver_cfg &c = S->cfg;
+    const int n = c.nst;
+    if (c.dtype == RS_F64) {
+        RS_CUDA(cudaMemcpyAsync(eps_dev, S->eig.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+        return RS_OK;
+    }
+    const size_t nn = (size_t)n * n;
+    if (!S->psi64.p) {
+        RS_TRY(S->psi64.alloc(sizeof(double) * (size_t)S->npts * n));
+        RS_TRY(S->hpsi64.alloc(sizeof(double) * (size_t)S->npts * n));
+        RS_TRY(S->rr64.alloc(sizeof(double) * (4 * nn + 16) + eigh_work_bytes(n)));
+    }
+    double *Sm = S->rr64.as<double>(), *h = Sm + nn, *Ui = h + nn, *T = Ui + nn;
+    int *status = reinterpret_cast<int *>(T + nn);
+    void *ew = reinterpret_cast<void *>(T + nn + 16);
+    // FP64 copy of the FP32 orbitals, H applied in FP64
+    k_widen<<<1024, 256, 0, st>>>(S->psi.as<float>(), S->psi64.as<double>(), S->npts * n);
+    RS_LAUNCH_CHECK();
+    for (int b = 0; b < n; b += c.nb)
+        RS_TRY(rs_ham_apply_block(S->h, S->psi64.as<double>() + b, n, S->hpsi64.as<double>() + b, n, c.nb, RS_F64, st));
+    // generalized Rayleigh-Ritz h x = eps S x with S, h accumulated in FP64
+    // (the overlap of the FP32 orbitals is exact: products of FP32 values)
+    RS_TRY(gram<float>(S->psi.as<float>(), n, n, S->psi.as<float>(), n, n, S->npts, S->dV, Sm, n, st));
+    RS_TRY(gram<double>(S->psi64.as<double>(), n, n, S->hpsi64.as<double>(), n, n, S->npts, S->dV, h, n, st));
+    RS_TRY(symmetrize(Sm, n, n, st));
+    RS_TRY(symmetrize(h, n, n, st));
+    RS_TRY(cholesky(Sm, n, n, 1e-14, status, st));
+    RS_TRY(tri_inv(Sm, n, n, Ui, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, Ui, n, true, h, n, false, 0.0, T, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, T, n, false, Ui, n, false, 0.0, h, n, st));
+    RS_TRY(symmetrize(h, n, n, st));
+    RS_TRY(eigh(h, n, n, eps_dev, T, n, 2, status, ew, st));
+    RS_CUDA(cudaStreamSynchronize(st));
     return RS_OK;
 }
 

@@ -87,3 +87,23 @@ def test_argument_errors():
         api.Grid.box(0, 4, 4, 0.3)
     with pytest.raises(RsError):
         api.Grid.spheres(np.array([[np.nan, 0.0, 0.0]]), 1.0, 0.3)
+
+
+def test_library_exports_every_declared_symbol():
+    """Every function include/rsdft.h declares is exported by librsdft.so
+    (looked up only, never called) and bound by the Python layer."""
+    import ctypes
+    import os
+    import re
+    from paper_1306_2953_gb300 import _lib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "include", "rsdft.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    names = sorted(set(re.findall(r"\b(rs_[a-z0-9_]+)\s*\(", text)))
+    assert len(names) >= 40
+    lib = ctypes.CDLL(_lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    unbound = [n for n in names if n not in _lib.exported_names()]
+    assert not unbound, unbound

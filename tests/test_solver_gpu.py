@@ -103,8 +103,10 @@ def test_solver_bad_config():
 
 def test_mol20_mixed_precision_within_1e6_of_oracle():
     """FP32 orbitals, H psi and inner iterations (tensor-core contractions),
-    FP64 Gram matrices, Cholesky, Rayleigh-Ritz and eigenvalues: every state
-    within 1e-6 Ha of the oracle's FP64 eigenvalues."""
+    FP64 Gram matrices, Cholesky, Rayleigh-Ritz and eigenvalues, closed by one
+    FP64 Rayleigh-Ritz of the converged subspace: every state within 1e-6 Ha
+    of the oracle's FP64 eigenvalues.  Without the closing step the FP32
+    rounding of H itself (potential ~40 Ha stored to 6e-8) leaves ~2e-6 Ha."""
     from paper_1306_2953_gb300 import api
     w = wl.MOL20
     lg, H, g_ora, H_ora, idx = _system(w)
@@ -113,7 +115,7 @@ def test_mol20_mixed_precision_within_1e6_of_oracle():
     ref = np.array(golden(w.name)["eigenvalues"])
     for it in range(600):
         eps, res, _ = S.step()
-        e = eps.cpu().numpy()
-        if np.abs(e[:w.judged] - ref).max() <= 1e-6 and np.all(res.cpu().numpy()[:w.judged] <= 1e-4):
+        if np.all(res.cpu().numpy()[:w.judged] <= 1e-4):
             break
+    e = S.rayleigh_ritz_f64().cpu().numpy()
     assert np.abs(e[:w.judged] - ref).max() <= 1e-6
