@@ -150,6 +150,13 @@ int rs_ham_destroy(rs_ham *h);
 int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi, void *hpsi_dev, int64_t ld_hpsi,
                        int nb, int dtype, void *stream);
 
+/* Status of the bounded shared-memory pipeline waits inside the FP32
+ * 32-state H psi kernel (no counterpart in the paper; a failure-detection
+ * aid): *flags = 0 when every wait completed, 1 when one gave up after its
+ * iteration limit (that call's hpsi is incomplete).  Blocking: it reads a
+ * device word after the work queued before it.  Errors: RS_EINVAL, RS_ECUDA. */
+int rs_ham_status(rs_ham *h, int *flags);
+
 /* Algorithmic bytes one rs_ham_apply_block call moves (psi read once, hpsi
  * written once, V, the point map and the projector tables), used for GB/s. */
 int64_t rs_ham_apply_bytes(const rs_ham *h, int nb, int dtype);
@@ -352,7 +359,7 @@ int rs_solver_rayleigh_ritz_f64(rs_solver *s, double *eps_dev, void *stream);
  * of the current orbitals (after the last sweep's subspace diagonalisation),
  * into R_dev [npts][ldr] (the solver's dtype): the residuals the method
  * generates, used as training inputs of the learned preconditioner.
- * Asynchronous. */
+ * 1 <= ncols <= 256.  Asynchronous.  Errors: RS_EINVAL (range, ldr). */
 int rs_solver_residual(rs_solver *s, int first, int ncols, void *R_dev, int64_t ldr, void *stream);
 
 /* The solver's current orbitals: device [npts][nst] (dtype), owned by the

@@ -64,6 +64,7 @@ SIGNATURES = {
     "rs_ham_destroy": (None, [P]),
     "rs_ham_apply_block": (None, [P, P, I64, P, I64, I32, I32, P]),
     "rs_ham_apply_bytes": (I64, [P, I32, I32]),
+    "rs_ham_status": (None, [P, P]),
     "rs_ham_timing": (None, [P, I32]),
     "rs_ham_timing_read": (None, [P, P, P, P]),
     "rs_ham_launch_bytes": (None, [P, I32, I32, P, P]),

@@ -173,6 +173,12 @@ class Hamiltonian:
     def apply_bytes(self, nb: int, dtype: int) -> int:
         return int(_lib.lib().rs_ham_apply_bytes(self._h, nb, dtype))
 
+    def status(self) -> int:
+        """rs_ham_status: 0 unless a bounded pipeline wait gave up (blocking)."""
+        f = ctypes.c_int32()
+        call("rs_ham_status", self._h, ctypes.byref(f))
+        return int(f.value)
+
     def close(self):
         if self._h:
             _lib.lib().rs_ham_destroy(self._h)

@@ -30,9 +30,21 @@
 
 #include "device.h"
 #include "ham.h"
+#include "stencil_ring.h"
 
 #ifndef RS_STENCIL_V3
 #define RS_STENCIL_V3 0
+#endif
+
+// 1: FP32 blocks of 32 states go to the persistent ring-buffer kernel
+// (stencil_ring.cu) when the block's layout allows 16-byte row copies.
+#ifndef RS_STENCIL_RING
+#define RS_STENCIL_RING 1
+#endif
+
+// Height (planes) of the z-slabs of that kernel's work units.
+#ifndef RS_RING_SLAB
+#define RS_RING_SLAB 32
 #endif
 
 #ifndef RS_STENCIL_MINB_F32
@@ -952,11 +964,13 @@ struct rs_ham {
         cproj, dummy, scratch;
     std::map<std::pair<int, int>, WorkList *> work;
     WorkList *work_v3 = nullptr;   // FP32 32-state kernel with bounded nonlocal entries per item
+    RingPlan *ring = nullptr;      // tables of the ring-buffer FP32 kernel (nullptr: not usable)
     // optional per-launch timing (rs_ham_timing)
     bool timing = false;
     std::vector<cudaEvent_t> events;   // 3 per recorded call
     size_t n_recorded = 0;
     ~rs_ham() {
+        ring_plan_destroy(ring);
         delete work_v3;
         for (auto &kv : work) delete kv.second;
         for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -1201,6 +1215,9 @@ extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_pr
         if ((rc = build_work(H, g, s.tx, s.ty))) return bail(rc);
     bool v3ok = false;
     if ((rc = build_work_v3(H, g, coff, &v3ok))) return bail(rc);
+#if RS_STENCIL_RING
+    if ((rc = ring_plan_build(&H->ring, g, coff, catom, cg32, v32, na, RS_RING_SLAB))) return bail(rc);
+#endif
     *out = H;
     return RS_OK;
 }
@@ -1289,6 +1306,14 @@ static int apply_t(rs_ham *H, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, i
         case 16: rc = launch_stencil<T, 16, 16, 8>(H, d, psi, ldp, hpsi, ldh, nb, st); break;
         default:
             if constexpr (SGMAX >= 32) {
+                if constexpr (sizeof(T) == 4) {
+                    if (ring_usable(H->ring, psi, ldp, nb)) {
+                        float w[5];
+                        for (int j = 0; j < 5; ++j) w[j] = (float)H->w[j];
+                        rc = ring_launch(H->ring, psi, ldp, hpsi, ldh, H->cproj.as<float>(), nb, w, st);
+                        break;
+                    }
+                }
                 if (H->work_v3) {
                     rc = launch_v3(H, d, psi, ldp, hpsi, ldh, nb, st);
                     break;
@@ -1334,6 +1359,14 @@ extern "C" int rs_ham_launch_bytes(const rs_ham *h, int nb, int dtype, int64_t *
     const int64_t np = h->npts, ne = h->n_entries, nc = (int64_t)h->n_atoms * 4 * nb * s;
     if (project_bytes) *project_bytes = ne * (4 + 4 * s) + (h->n_atoms + 1) * 4 + nc;
     if (stencil_bytes) *stencil_bytes = np * nb * 2 * s + np * s + np * 4 + ne * (4 + 4 * s) + (np + 1) * 4 + nc;
+    return RS_OK;
+}
+
+extern "C" int rs_ham_status(rs_ham *h, int *flags) {
+    if (!h || !flags) return fail(RS_EINVAL, "rs_ham_status: null argument");
+    int f = 0;
+    RS_TRY(ring_status(h->ring, &f));
+    *flags = f;
     return RS_OK;
 }
 

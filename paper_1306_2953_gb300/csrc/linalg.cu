@@ -201,57 +201,80 @@ template int rowmul<float>(const float *, int64_t, int, const double *, int64_t,
 // Right-looking Cholesky of the leading n x n block of A (in place): the
 // upper triangle receives U with A = U^T U, the strict lower triangle is
 // zeroed.  status[0] = 0, or j+1 if pivot j is not finite or not larger
-// than rel * (original A_jj).  n <= CHOL_MAX.
+// than rel * (original A_jj).  One CTA; the matrix is worked on in shared
+// memory when it fits (IN_SMEM), else in global memory (L1/L2 resident).
+// Rows are spread over warps and columns over lanes, so no index division.
 constexpr int CHOL_MAX = 2048;
-__global__ void __launch_bounds__(1024) k_chol(double *A, int lda, int n, double rel, int *status) {
+constexpr int CHOL_SMEM_MAX = 160;   // n x n FP64 in 200 KB
+template <bool IN_SMEM>
+__global__ void __launch_bounds__(1024) k_chol(double *Ag, int lda, int n, double rel, int *status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double diag0[CHOL_MAX];
     __shared__ double piv;
     __shared__ int bad;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) diag0[j] = A[(int64_t)j * lda + j];
-    if (threadIdx.x == 0) bad = 0;
+    double *A = IN_SMEM ? reinterpret_cast<double *>(smraw) : Ag;
+    const int ld = IN_SMEM ? n : lda;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (IN_SMEM)
+        for (int r = warp; r < n; r += nw)
+            for (int c = lane; c < n; c += 32) A[r * ld + c] = Ag[(int64_t)r * lda + c];
+    __syncthreads();
+    for (int j = tid; j < n; j += blockDim.x) diag0[j] = A[(int64_t)j * ld + j];
+    if (tid == 0) bad = 0;
     __syncthreads();
     for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = A[(int64_t)j * lda + j];
+        if (tid == 0) {
+            const double d = A[(int64_t)j * ld + j];
             if (!isfinite(d) || !(d > 0.0) || !(d > rel * diag0[j])) {
                 bad = j + 1;
                 piv = 1.0;
             } else {
                 piv = sqrt(d);
             }
-            A[(int64_t)j * lda + j] = piv;
+            A[(int64_t)j * ld + j] = piv;
         }
         __syncthreads();
         if (bad) break;
-        const double p = piv;
-        for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) A[(int64_t)j * lda + c] /= p;
+        const double inv = 1.0 / piv;
+        double *uj = A + (int64_t)j * ld;
+        for (int c = j + 1 + tid; c < n; c += blockDim.x) uj[c] *= inv;
         __syncthreads();
         // trailing update A[r][c] -= U[j][r] U[j][c] on the upper triangle, r, c > j
-        const int m = n - j - 1;
-        for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-            const int r = j + 1 + (int)(e / m), c = j + 1 + (int)(e % m);
-            if (c >= r) A[(int64_t)r * lda + c] -= A[(int64_t)j * lda + r] * A[(int64_t)j * lda + c];
+        for (int r = j + 1 + warp; r < n; r += nw) {
+            const double ujr = uj[r];
+            double *ar = A + (int64_t)r * ld;
+            for (int c = r + lane; c < n; c += 32) ar[c] -= ujr * uj[c];
         }
         __syncthreads();
     }
-    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
-        const int r = (int)(e / n), c = (int)(e % n);
-        if (c < r) A[(int64_t)r * lda + c] = 0.0;
-    }
-    if (threadIdx.x == 0) status[0] = bad;
+    for (int r = warp; r < n; r += nw)
+        for (int c = lane; c < n; c += 32) {
+            const double v = c < r ? 0.0 : A[(int64_t)r * ld + c];
+            if (IN_SMEM) Ag[(int64_t)r * lda + c] = v;
+            else if (c < r) Ag[(int64_t)r * lda + c] = 0.0;
+        }
+    if (tid == 0) status[0] = bad;
 }
 
-// X = U^-1 for upper-triangular U (n x n): one thread per column, back
-// substitution from the diagonal upwards.  X must not alias U.
-__global__ void k_trinv(const double *__restrict__ U, int ldu, int n, double *__restrict__ X, int ldx) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= n) return;
-    for (int i = n - 1; i > col; --i) X[(int64_t)i * ldx + col] = 0.0;
-    for (int i = col; i >= 0; --i) {
-        double t = (i == col) ? 1.0 : 0.0;
-        for (int k = i + 1; k <= col; ++k) t -= U[(int64_t)i * ldu + k] * X[(int64_t)k * ldx + col];
-        X[(int64_t)i * ldx + col] = t / U[(int64_t)i * ldu + i];
+// X = U^-1 for upper-triangular U (n x n): one warp per column j, back
+// substitution x_i = (delta_ij - sum_{k=i+1..j} U_ik x_k) / U_ii from the
+// diagonal upwards, the sums split over the lanes.  X must not alias U.
+__global__ void __launch_bounds__(256) k_trinv(const double *__restrict__ U, int ldu, int n, double *__restrict__ X,
+                                               int ldx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int j = blockIdx.x * (blockDim.x >> 5) + wl;
+    double *x = reinterpret_cast<double *>(smraw) + (size_t)wl * n;
+    if (j >= n) return;
+    for (int i = j; i >= 0; --i) {
+        const double *ui = U + (int64_t)i * ldu;
+        double t = 0.0;
+        for (int k = i + 1 + lane; k <= j; k += 32) t += ui[k] * x[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - t) / ui[i];
+        __syncwarp();
     }
+    for (int i = lane; i < n; i += 32) X[(int64_t)i * ldx + j] = i <= j ? x[i] : 0.0;
 }
 
 // C = alpha op(A) op(B) + beta C for small dense FP64 matrices (row-major),
@@ -289,13 +312,33 @@ int gemm_small(int m, int n, int k, double alpha, const double *A, int lda, bool
 
 int cholesky(double *A, int lda, int n, double rel, int *status_dev, cudaStream_t st) {
     if (n > CHOL_MAX) return fail(RS_EINVAL, "cholesky: n > %d", CHOL_MAX);
-    k_chol<<<1, 1024, 0, st>>>(A, lda, n, rel, status_dev);
+    if (n <= CHOL_SMEM_MAX) {
+        const size_t sm = sizeof(double) * (size_t)n * n;
+        static bool attr = false;
+        if (!attr) {
+            RS_CUDA(cudaFuncSetAttribute(k_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * CHOL_SMEM_MAX * CHOL_SMEM_MAX)));
+            attr = true;
+        }
+        k_chol<true><<<1, 1024, sm, st>>>(A, lda, n, rel, status_dev);
+    } else {
+        k_chol<false><<<1, 1024, 0, st>>>(A, lda, n, rel, status_dev);
+    }
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
 
 int tri_inv(const double *U, int ldu, int n, double *X, int ldx, cudaStream_t st) {
-    k_trinv<<<(n + 127) / 128, 128, 0, st>>>(U, ldu, n, X, ldx);
+    constexpr int WPB = 8;   // columns (warps) per CTA
+    const size_t sm = sizeof(double) * (size_t)WPB * n;
+    if (sm > 48 * 1024) {
+        static int attr = 0;
+        if ((int)sm > attr) {
+            RS_CUDA(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            attr = (int)sm;
+        }
+    }
+    k_trinv<<<(n + WPB - 1) / WPB, 32 * WPB, sm, st>>>(U, ldu, n, X, ldx);
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
@@ -320,130 +363,13 @@ int symmetrize(double *A, int lda, int n, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------- Jacobi ---
-// Cyclic Jacobi eigenvalue iteration for a symmetric n x n matrix (n even),
-// one CTA.  Each round applies n/2 rotations on disjoint index pairs (the
-// round-robin "circle" ordering: pair (0, 1 + r mod (n-1)) and the pairs
+// Cyclic Jacobi eigenvalue iteration for a symmetric n x n matrix (n even).
+// Each round applies n/2 rotations on disjoint index pairs (the round-robin
+// "circle" ordering: pair (0, 1 + r mod (n-1)) and the pairs
 // (1 + (r+k) mod (n-1), 1 + (r-k) mod (n-1)), k = 1..n/2-1), each rotation
 // annihilating its (p,q) entry; n-1 rounds make a sweep visiting every pair.
-// A (overwritten) and V live in global workspace (L1/L2 resident).  On exit
-// w[0..n) holds the eigenvalues ascending and Vout[:, k] the eigenvectors
-// (FP64); info[0] = sweeps used, or -1 if max_sweeps ran out.
-template <typename T, bool IN_SMEM>
-__global__ void __launch_bounds__(1024) k_jacobi(T *Ag, T *Vg, int n, int max_sweeps, double tol, double *w,
-                                                 double *Vout, int ldv, int *info) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    // small matrices live in shared memory for the whole iteration
-    T *A = IN_SMEM ? reinterpret_cast<T *>(smraw) : Ag;
-    T *V = IN_SMEM ? A + (size_t)n * n : Vg;
-    T *cs = IN_SMEM ? V + (size_t)n * n : reinterpret_cast<T *>(smraw);  // [n/2]
-    T *sn = cs + n / 2;                          // [n/2]
-    int *pp = reinterpret_cast<int *>(sn + n / 2);
-    int *qq = pp + n / 2;
-    int *rank = qq + n / 2;                      // [n]
-    __shared__ double red[32];
-    __shared__ double fro2, off2;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int h = n / 2, m = n - 1;
-    if (IN_SMEM)
-        for (int64_t e = tid; e < (int64_t)n * n; e += nt) A[e] = Ag[e];
-    for (int64_t e = tid; e < (int64_t)n * n; e += nt) V[e] = (e / n == e % n) ? T(1) : T(0);
-    __syncthreads();
-    auto block_sum = [&](double v) -> double {
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        __syncthreads();
-        if ((tid & 31) == 0) red[tid >> 5] = v;
-        __syncthreads();
-        double t = 0;
-        if (tid < 32) {
-            t = tid < (nt + 31) / 32 ? red[tid] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        }
-        return t;  // valid in thread 0
-    };
-    double loc = 0;
-    for (int64_t e = tid; e < (int64_t)n * n; e += nt) loc += (double)A[e] * (double)A[e];
-    const double f = block_sum(loc);
-    if (tid == 0) fro2 = f;
-    __syncthreads();
-    int sweep = 0, done = 0;
-    for (; sweep < max_sweeps; ++sweep) {
-        loc = 0;
-        for (int64_t e = tid; e < (int64_t)n * n; e += nt)
-            if (e / n != e % n) loc += (double)A[e] * (double)A[e];
-        const double o = block_sum(loc);
-        if (tid == 0) off2 = o;
-        __syncthreads();
-        if (off2 <= tol * tol * fro2) {
-            done = 1;
-            break;
-        }
-        for (int r = 0; r < m; ++r) {
-            for (int k = tid; k < h; k += nt) {
-                int p, q;
-                if (k == 0) {
-                    p = 0;
-                    q = 1 + r % m;
-                } else {
-                    p = 1 + (r + k) % m;
-                    q = 1 + (r - k + m) % m;
-                }
-                const T apq = A[(int64_t)p * n + q];
-                T c = 1, s_ = 0;
-                if (apq != T(0)) {
-                    const T theta = (A[(int64_t)q * n + q] - A[(int64_t)p * n + p]) / (T(2) * apq);
-                    const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-                    c = T(1) / sqrt(t * t + T(1));
-                    s_ = t * c;
-                }
-                cs[k] = c;
-                sn[k] = s_;
-                pp[k] = p;
-                qq[k] = q;
-            }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (int64_t e = tid; e < (int64_t)h * n; e += nt) {
-                const int k = (int)(e / n), j = (int)(e % n);
-                const int p = pp[k], q = qq[k];
-                const T c = cs[k], s_ = sn[k];
-                const T a = A[(int64_t)p * n + j], b = A[(int64_t)q * n + j];
-                A[(int64_t)p * n + j] = c * a - s_ * b;
-                A[(int64_t)q * n + j] = s_ * a + c * b;
-            }
-            __syncthreads();
-            // columns: A <- A J, V <- V J
-            for (int64_t e = tid; e < (int64_t)h * n; e += nt) {
-                const int k = (int)(e / n), i = (int)(e % n);
-                const int p = pp[k], q = qq[k];
-                const T c = cs[k], s_ = sn[k];
-                const T a = A[(int64_t)i * n + p], b = A[(int64_t)i * n + q];
-                A[(int64_t)i * n + p] = c * a - s_ * b;
-                A[(int64_t)i * n + q] = s_ * a + c * b;
-                const T va = V[(int64_t)i * n + p], vb = V[(int64_t)i * n + q];
-                V[(int64_t)i * n + p] = c * va - s_ * vb;
-                V[(int64_t)i * n + q] = s_ * va + c * vb;
-            }
-            __syncthreads();
-        }
-    }
-    // ascending order (ties by index)
-    for (int i = tid; i < n; i += nt) {
-        const T di = A[(int64_t)i * n + i];
-        int rk = 0;
-        for (int j = 0; j < n; ++j) {
-            const T dj = A[(int64_t)j * n + j];
-            rk += (dj < di) || (dj == di && j < i);
-        }
-        rank[i] = rk;
-    }
-    __syncthreads();
-    for (int i = tid; i < n; i += nt) w[rank[i]] = (double)A[(int64_t)i * n + i];
-    for (int64_t e = tid; e < (int64_t)n * n; e += nt) {
-        const int i = (int)(e / n), k = (int)(e % n);
-        Vout[(int64_t)i * ldv + rank[k]] = (double)V[e];
-    }
-    if (tid == 0) info[0] = done ? sweep : -1;
-}
+// Matrices whose packed triangle fits one CTA's shared memory use
+// k_jacobi_pk below; larger ones the cooperative multi-CTA k_jacobi_grid.
 
 // Multi-CTA variant for matrices too large for one CTA's shared memory: the
 // same rounds, with every CTA computing all rotations of a round redundantly,
@@ -586,6 +512,219 @@ __global__ void __launch_bounds__(256) k_jacobi_grid(T *A, T *V, int n, int max_
     if (bid == 0 && tid == 0) info[0] = done ? sweep : -1;
 }
 
+// Single-CTA cyclic Jacobi with the matrix held in shared memory as its
+// packed upper triangle (n (n+1)/2 elements), for n up to a few hundred.  A
+// round of the circle ordering rotates h = n/2 disjoint pairs (p_k, q_k); the
+// two-sided update J^T A J then acts independently on every 2 x 2 block
+// A[{p_k,q_k}][{p_l,q_l}] (k <= l), so a round is one pass over those blocks
+// between two barriers.  The rotations are logged, (c, s) per pair per round,
+// and the eigenvectors are accumulated afterwards by k_jacobi_vacc, whose
+// CTAs each own a few rows of V.  On exit w holds the eigenvalues ascending,
+// perm[i] the rank of diagonal position i, info[0] the sweeps used (-1 when
+// max_sweeps ran out).
+__device__ __forceinline__ void circle_pair(int r, int k, int m, int &p, int &q) {
+    if (k == 0) {
+        p = 0;
+        q = 1 + r % m;
+    } else {
+        p = 1 + (r + k) % m;
+        q = 1 + (r - k + m) % m;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_jacobi_pk(const double *__restrict__ Ag, int lda, int n, int max_sweeps,
+                                                    double tol, T *__restrict__ rot, double *__restrict__ w,
+                                                    int *__restrict__ perm, int *__restrict__ info) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int h = n / 2, m = n - 1;
+    T *cs = reinterpret_cast<T *>(smraw);
+    T *sn = cs + h;
+    T *a = sn + h;
+    const int npk = n * (n + 1) / 2;
+    int *ro = reinterpret_cast<int *>(a + npk);   // packed offset of row i minus i: f(i,j) = ro[i] + j, i <= j
+    int *pp = ro + n;
+    int *qq = pp + h;
+    __shared__ double red[32];
+    __shared__ double fro2, off2;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int i = tid; i < n; i += nt) ro[i] = i * (2 * n - i - 1) / 2;
+    __syncthreads();
+    for (int i = warp; i < n; i += nw)
+        for (int j = i + lane; j < n; j += 32) a[ro[i] + j] = (T)Ag[(int64_t)i * lda + j];
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        double t = 0;
+        if (tid < 32) {
+            t = tid < nw ? red[tid] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        }
+        return t;  // valid in thread 0
+    };
+    __syncthreads();
+    {
+        double d = 0, o = 0;
+        for (int i = warp; i < n; i += nw)
+            for (int j = i + lane; j < n; j += 32) {
+                const double x = (double)a[ro[i] + j];
+                if (j == i) d += x * x;
+                else o += x * x;
+            }
+        const double f = block_sum(d + 2.0 * o);
+        if (tid == 0) fro2 = f;
+    }
+    __syncthreads();
+    int sweep = 0, done = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double o = 0;
+        for (int i = warp; i < n; i += nw)
+            for (int j = i + 1 + lane; j < n; j += 32) {
+                const double x = (double)a[ro[i] + j];
+                o += x * x;
+            }
+        const double t = block_sum(2.0 * o);
+        if (tid == 0) off2 = t;
+        __syncthreads();
+        if (off2 <= tol * tol * fro2) {
+            done = 1;
+            break;
+        }
+        for (int r = 0; r < m; ++r) {
+            for (int k = tid; k < h; k += nt) {
+                int p, q;
+                circle_pair(r, k, m, p, q);
+                const int lo = min(p, q), hi = max(p, q);
+                const T apq = a[ro[lo] + hi];
+                T c = 1, s_ = 0;
+                if (apq != T(0)) {
+                    const T theta = (a[ro[q] + q] - a[ro[p] + p]) / (T(2) * apq);
+                    const T tt = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+                    c = T(1) / sqrt(tt * tt + T(1));
+                    s_ = tt * c;
+                }
+                cs[k] = c;
+                sn[k] = s_;
+                pp[k] = p;
+                qq[k] = q;
+                T *lg = rot + 2 * (((int64_t)sweep * m + r) * h + k);
+                lg[0] = c;
+                lg[1] = s_;
+            }
+            __syncthreads();
+            for (int k = warp; k < h; k += nw) {
+                const int pk = pp[k], qk = qq[k];
+                const T ck = cs[k], sk = sn[k];
+                for (int l = k + lane; l < h; l += 32) {
+                    const int pl = pp[l], ql = qq[l];
+                    const T cl = cs[l], sl = sn[l];
+                    if (l == k) {
+                        const int lo = min(pk, qk), hi = max(pk, qk);
+                        const T app = a[ro[pk] + pk], aqq = a[ro[qk] + qk], apq = a[ro[lo] + hi];
+                        // rows then columns of [[app, apq], [apq, aqq]]
+                        const T x00 = ck * app - sk * apq, x01 = ck * apq - sk * aqq;
+                        const T x10 = sk * app + ck * apq, x11 = sk * apq + ck * aqq;
+                        a[ro[pk] + pk] = ck * x00 - sk * x01;
+                        a[ro[qk] + qk] = sk * x10 + ck * x11;
+                        a[ro[lo] + hi] = T(0);
+                    } else {
+                        auto at = [&](int i, int j) -> T & { return i <= j ? a[ro[i] + j] : a[ro[j] + i]; };
+                        T &b00 = at(pk, pl), &b01 = at(pk, ql), &b10 = at(qk, pl), &b11 = at(qk, ql);
+                        const T x00 = ck * b00 - sk * b10, x10 = sk * b00 + ck * b10;
+                        const T x01 = ck * b01 - sk * b11, x11 = sk * b01 + ck * b11;
+                        b00 = cl * x00 - sl * x01;
+                        b01 = sl * x00 + cl * x01;
+                        b10 = cl * x10 - sl * x11;
+                        b11 = sl * x10 + cl * x11;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ascending order (ties by index)
+    for (int i = tid; i < n; i += nt) {
+        const T di = a[ro[i] + i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const T dj = a[ro[j] + j];
+            rk += (dj < di) || (dj == di && j < i);
+        }
+        perm[i] = rk;
+        w[rk] = (double)di;
+    }
+    if (tid == 0) info[0] = done ? sweep : -1;
+}
+
+// V = product of the logged rotations, row by row: CTA b owns rows
+// [RB b, RB b + RB) in shared memory (identity at the start); thread k applies
+// pair k's rotation of every round.  Vout[i][perm[j]] = V[i][j] (FP64).
+constexpr int VACC_RB = 8;
+template <typename T>
+__global__ void k_jacobi_vacc(const T *__restrict__ rot, int n, int max_sweeps, const int *__restrict__ info,
+                              const int *__restrict__ perm, double *__restrict__ Vout, int ldv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *v = reinterpret_cast<T *>(smraw);   // [VACC_RB][n]
+    const int h = n / 2, m = n - 1, tid = threadIdx.x;
+    const int i0 = blockIdx.x * VACC_RB, nr = min(VACC_RB, n - i0);
+    for (int e = tid; e < VACC_RB * n; e += blockDim.x) {
+        const int r = e / n, j = e - r * n;
+        v[e] = (i0 + r == j) ? T(1) : T(0);
+    }
+    __syncthreads();
+    const int sweeps = info[0] < 0 ? max_sweeps : info[0];
+    const int64_t rounds = (int64_t)sweeps * m;
+    T c = 1, s_ = 0;
+    if (tid < h && rounds > 0) {
+        c = rot[2 * tid];
+        s_ = rot[2 * tid + 1];
+    }
+    for (int64_t R = 0; R < rounds; ++R) {
+        T cn = 1, sn_ = 0;
+        if (tid < h && R + 1 < rounds) {
+            const T *lg = rot + 2 * ((R + 1) * h + tid);
+            cn = lg[0];
+            sn_ = lg[1];
+        }
+        if (tid < h) {
+            int p, q;
+            circle_pair((int)(R % m), tid, m, p, q);
+#pragma unroll
+            for (int r = 0; r < VACC_RB; ++r) {
+                T *row = v + r * n;
+                const T va = row[p], vb = row[q];
+                row[p] = c * va - s_ * vb;
+                row[q] = s_ * va + c * vb;
+            }
+        }
+        __syncthreads();
+        c = cn;
+        s_ = sn_;
+    }
+    for (int e = tid; e < nr * n; e += blockDim.x) {
+        const int r = e / n, j = e - r * n;
+        Vout[(int64_t)(i0 + r) * ldv + perm[j]] = (double)v[r * n + j];
+    }
+}
+
+// shared memory of k_jacobi_pk for order n and element type size es
+size_t jacobi_pk_smem(int n, size_t es) {
+    const size_t h = n / 2;
+    return es * (2 * h + (size_t)n * (n + 1) / 2) + sizeof(int) * ((size_t)n + 2 * h) + 64;
+}
+constexpr size_t JACOBI_PK_MAX_SMEM = 220 * 1024;
+// (c, s) entries of the rotation log of up to max_sweeps sweeps
+size_t jacobi_log_elems(int n, int max_sweeps) { return 2 * (size_t)max_sweeps * (n - 1) * (n / 2); }
+
+// scratch bytes of jacobi<T> (es = sizeof(T)) for order n and max_sweeps
+size_t jacobi_scratch_bytes(int n, int max_sweeps, size_t es) {
+    if (jacobi_pk_smem(n, es) <= JACOBI_PK_MAX_SMEM)
+        return es * jacobi_log_elems(n, max_sweeps) + sizeof(int) * (size_t)n + 64;
+    return 2 * es * (size_t)n * n + 16 + sizeof(double) * ((size_t)max_sweeps + 2) + 16 + 64;
+}
+
 // FP64 -> T copy of an n x n matrix into a dense buffer
 template <typename T> __global__ void k_copy_cast(const double *A, int lda, int n, T *B) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
@@ -597,18 +736,29 @@ template <typename T>
 int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *w, double *V, int ldv, int *info,
            void *scratch, cudaStream_t st) {
     if (n % 2) return fail(RS_EINVAL, "jacobi: n must be even");
+    const size_t pk = jacobi_pk_smem(n, sizeof(T));
+    if (pk <= JACOBI_PK_MAX_SMEM) {
+        // rotation log and rank array in the scratch
+        T *rot = reinterpret_cast<T *>(scratch);
+        int *perm = reinterpret_cast<int *>(rot + jacobi_log_elems(n, max_sweeps));
+        static int pk_attr = 0;   // largest dynamic shared memory granted so far (per instantiation)
+        if ((int)pk > pk_attr) {
+            RS_CUDA(cudaFuncSetAttribute(k_jacobi_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk));
+            pk_attr = (int)pk;
+        }
+        k_jacobi_pk<T><<<1, 1024, pk, st>>>(A, lda, n, max_sweeps, tol, rot, w, perm, info);
+        RS_LAUNCH_CHECK();
+        const int threads = std::max(32, ((n / 2 + 31) / 32) * 32);
+        const size_t vs = (size_t)VACC_RB * n * sizeof(T);
+        k_jacobi_vacc<T><<<(n + VACC_RB - 1) / VACC_RB, threads, vs, st>>>(rot, n, max_sweeps, info, perm, V, ldv);
+        RS_LAUNCH_CHECK();
+        return RS_OK;
+    }
     T *a = reinterpret_cast<T *>(scratch);
     T *v = a + (size_t)n * n;
     k_copy_cast<T><<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(A, lda, n, a);
     RS_LAUNCH_CHECK();
     const size_t small = (size_t)n * sizeof(T) + (size_t)n * 3 * sizeof(int) + 64;
-    const size_t full = small + 2 * (size_t)n * n * sizeof(T);
-    if (full <= 200 * 1024) {
-        RS_CUDA(cudaFuncSetAttribute(k_jacobi<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full));
-        k_jacobi<T, true><<<1, 1024, full, st>>>(a, v, n, max_sweeps, tol, w, V, ldv, info);
-        RS_LAUNCH_CHECK();
-        return RS_OK;
-    }
     // grid variant: barrier words, reduction slots and the error flag follow V in the scratch
     unsigned *bar = reinterpret_cast<unsigned *>(v + (size_t)n * n);
     double *red_g = reinterpret_cast<double *>(bar + 4);
@@ -750,21 +900,29 @@ __global__ void k_copy_block(const double *A, int lda, int m, int n, double *B, 
         B[(e / n) * ldb + e % n] = A[(e / n) * lda + e % n];
 }
 
+// Jacobi scratch of eigh: FP32 (30 sweeps) or FP64 (60 sweeps) on the padded
+// order, the FP64 polish (10 sweeps) on n
+static size_t eigh_jacobi_bytes(int n) {
+    const int ne = n + (n & 1);
+    return std::max({jacobi_scratch_bytes(ne, 30, sizeof(float)), jacobi_scratch_bytes(ne, 60, sizeof(double)),
+                     jacobi_scratch_bytes(n + (n & 1), 10, sizeof(double))});
+}
+
 size_t eigh_work_bytes(int n) {
     const size_t ne = (size_t)n + (n & 1);
-    // padded A, Jacobi scratch (2 ne^2), Jacobi vectors, eigenvalues, refinement (4 n^2 + 1), scalars
-    return sizeof(double) * (ne * ne * 4 + ne + 4 * (size_t)n * n + 192);
+    // padded A, Jacobi vectors, eigenvalues, refinement (4 n^2 + 1), scalars, Jacobi scratch
+    return sizeof(double) * (ne * ne * 2 + ne + 4 * (size_t)n * n + 192) + eigh_jacobi_bytes(n);
 }
 
 int eigh(const double *A, int lda, int n, double *w, double *V, int ldv, int refine, int *info_dev, void *work,
          cudaStream_t st) {
     const int ne = n + (n & 1);
     double *Ap = reinterpret_cast<double *>(work);
-    double *jscr = Ap + (size_t)ne * ne;
-    double *Vp = jscr + 2 * (size_t)ne * ne + 64;
+    double *Vp = Ap + (size_t)ne * ne;
     double *wp = Vp + (size_t)ne * ne;
     double *rwork = wp + ne;
     double *big = rwork + 4 * (size_t)n * n + 1;
+    double *jscr = big + 64;
     const int eb = std::min(1024, (ne * ne + 255) / 256);
     if (ne != n) {
         k_pad_big<<<1, 1024, 0, st>>>(A, lda, n, big);

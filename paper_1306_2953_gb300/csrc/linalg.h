@@ -74,6 +74,10 @@ struct TcWork {
     void *p = nullptr;
     int64_t bytes = 0;
     int *err = nullptr;
+    // inner iterations of the FP32 eigensolver: the full overlaps of Sec. VI
+    // on the tensor cores as well, and the subspace eigenvectors from FP32
+    // Jacobi alone (the closing FP64 Rayleigh-Ritz fixes the final accuracy)
+    bool inner = false;
 };
 
 // Psi (n columns) <- Psi C in place (C FP64 n x n); FP32 data on the tensor

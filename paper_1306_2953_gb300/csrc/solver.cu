@@ -58,16 +58,18 @@ __global__ void k_coldots(const T *__restrict__ A, int64_t lda, const T *__restr
     }
 }
 
+// Elementwise kernels over [npts][ncols] column blocks (ncols <= 256): a
+// thread keeps one column k = tid % ncols, derives its per-column factor once
+// and strides over rows, so no per-element index division or FP64 divide.
 template <typename T>
 __global__ void k_residual(const T *__restrict__ X, int64_t ldx, const T *__restrict__ HX, int64_t ldh,
                            const double *__restrict__ num, const double *__restrict__ den, T *__restrict__ R,
                            int64_t ldr, int ncols, int64_t npts) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t p = t / ncols;
-    const int k = (int)(t % ncols);
-    if (p >= npts) return;
+    const int rows = blockDim.x / ncols, k = threadIdx.x % ncols, r = threadIdx.x / ncols;
+    if (r >= rows) return;
     const T lam = (T)(num[k] / den[k]);
-    R[p * ldr + k] = HX[p * ldh + k] - lam * X[p * ldx + k];
+    for (int64_t p = blockIdx.x * (int64_t)rows + r; p < npts; p += (int64_t)gridDim.x * rows)
+        R[p * ldr + k] = HX[p * ldh + k] - lam * X[p * ldx + k];
 }
 
 __global__ void k_resnorm(const double *rr, int n, double dV, double *res) {
@@ -77,22 +79,21 @@ __global__ void k_resnorm(const double *rr, int n, double dV, double *res) {
 
 template <typename T>
 __global__ void k_scale_cols(T *Y, int64_t ldy, int ncols, int64_t npts, const double *nrm2, double dV) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t p = t / ncols;
-    const int k = (int)(t % ncols);
-    if (p >= npts) return;
+    const int rows = blockDim.x / ncols, k = threadIdx.x % ncols, r = threadIdx.x / ncols;
+    if (r >= rows) return;
     const double n2 = dV * nrm2[k];
-    if (n2 > 0) Y[p * ldy + k] = (T)((double)Y[p * ldy + k] / sqrt(n2));
+    if (!(n2 > 0)) return;
+    const T f = (T)(1.0 / sqrt(n2));
+    for (int64_t p = blockIdx.x * (int64_t)rows + r; p < npts; p += (int64_t)gridDim.x * rows) Y[p * ldy + k] *= f;
 }
 
 template <typename T>
 __global__ void k_copy_cols(const T *__restrict__ S, int64_t lds, T *__restrict__ D, int64_t ldd, int ncols,
                             int64_t npts) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t p = t / ncols;
-    const int k = (int)(t % ncols);
-    if (p >= npts) return;
-    D[p * ldd + k] = S[p * lds + k];
+    const int rows = blockDim.x / ncols, k = threadIdx.x % ncols, r = threadIdx.x / ncols;
+    if (r >= rows) return;
+    for (int64_t p = blockIdx.x * (int64_t)rows + r; p < npts; p += (int64_t)gridDim.x * rows)
+        D[p * ldd + k] = S[p * lds + k];
 }
 
 __global__ void k_copy_leading(const double *A, int lda, int n, double *B, int ldb) {
@@ -137,7 +138,11 @@ struct rs_solver {
 
 namespace {
 
-unsigned elem_blocks(int64_t npts, int ncols) { return (unsigned)((npts * ncols + 255) / 256); }
+// grid of the column-block kernels (256 threads, 256 / ncols rows per CTA pass)
+unsigned elem_blocks(int64_t npts, int ncols) {
+    const int64_t rows = std::max(1, 256 / ncols);
+    return (unsigned)std::min<int64_t>((npts + rows - 1) / rows, 152 * 16);
+}
 
 int copy_cols(int dtype, const void *S, int64_t lds, void *D, int64_t ldd, int ncols, int64_t npts, cudaStream_t st) {
     if (dtype == RS_F64)
@@ -303,11 +308,13 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
         return bail(rc);
     if (c.dtype == RS_F32) {
         const int64_t need = std::max({umma_work_bytes(c.nst, 2 * c.nb, S->npts), umma_work_bytes(S->npts, c.nst, c.nst),
-                                       umma_work_bytes(3 * c.nb, 3 * c.nb, S->npts)});
+                                       umma_work_bytes(3 * c.nb, 3 * c.nb, S->npts),
+                                       umma_work_bytes(c.nst, c.nst, S->npts)});
         if ((rc = S->tcbuf.alloc((size_t)need + 256))) return bail(rc);
         S->tc.p = S->tcbuf.p;
         S->tc.bytes = need;
         S->tc.err = reinterpret_cast<int *>((char *)S->tcbuf.p + need);
+        S->tc.inner = true;
         if (cudaMemset(S->tc.err, 0, sizeof(int)) != cudaSuccess) return bail(fail(RS_ECUDA, "cudaMemset failed"));
     }
     const int n3 = 3 * c.nb;
@@ -373,19 +380,20 @@ extern "C" int rs_eigensolver_step(rs_solver *S, double *eps_dev, double *resnor
 template <typename T>
 __global__ void k_ritz_residual(const T *__restrict__ X, const T *__restrict__ HX, int64_t ld, const double *__restrict__ eps,
                                 int first, int ncols, int64_t npts, T *__restrict__ R, int64_t ldr) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t p = t / ncols;
-    const int k = (int)(t % ncols);
-    if (p >= npts) return;
-    R[p * ldr + k] = HX[p * ld + first + k] - (T)eps[first + k] * X[p * ld + first + k];
+    const int rows = blockDim.x / ncols, k = threadIdx.x % ncols, r = threadIdx.x / ncols;
+    if (r >= rows) return;
+    const T e = (T)eps[first + k];
+    for (int64_t p = blockIdx.x * (int64_t)rows + r; p < npts; p += (int64_t)gridDim.x * rows)
+        R[p * ldr + k] = HX[p * ld + first + k] - e * X[p * ld + first + k];
 }
 
 extern "C" int rs_solver_residual(rs_solver *S, int first, int ncols, void *R_dev, int64_t ldr, void *stream) {
     if (!S || !R_dev) return fail(RS_EINVAL, "rs_solver_residual: null argument");
     if (first < 0 || ncols < 1 || first + ncols > S->cfg.nst || ldr < ncols)
         return fail(RS_EINVAL, "rs_solver_residual: bad state range");
+    if (ncols > 256) return fail(RS_EINVAL, "rs_solver_residual: at most 256 columns per call");
     cudaStream_t st = (cudaStream_t)stream;
-    const unsigned blocks = (unsigned)((S->npts * ncols + 255) / 256);
+    const unsigned blocks = elem_blocks(S->npts, ncols);
     if (S->cfg.dtype == RS_F64)
         k_ritz_residual<double><<<blocks, 256, 0, st>>>(S->psi.as<double>(), S->hpsi.as<double>(), S->cfg.nst,
                                                         S->eig.as<double>(), first, ncols, S->npts, (double *)R_dev, ldr);

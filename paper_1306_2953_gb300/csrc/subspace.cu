@@ -47,6 +47,12 @@ extern "C" int64_t rs_linalg_workspace_bytes(int nst) {
 
 namespace rs {
 
+namespace {
+bool tc_grams(const TcWork &tc, int n, int64_t npts) {
+    return tc.inner && tc.p && tc.bytes >= umma_work_bytes(n, n, npts);
+}
+}  // namespace
+
 int rotate_inplace(void *Psi, int64_t ld, int n, const double *C, int64_t npts, int dtype, cudaStream_t st,
                    const TcWork &tc) {
     if (dtype == RS_F64) return rowmul<double>((const double *)Psi, ld, n, C, n, n, (double *)Psi, ld, npts, 1.0, 0.0, st);
@@ -61,6 +67,8 @@ int orthonormalize_impl(int64_t npts, double dV, void *Psi, int64_t ld, int n, i
     LaWork w(work, n);
     if (dtype == RS_F64)
         RS_TRY(gram<double>((const double *)Psi, ld, n, (const double *)Psi, ld, n, npts, dV, w.U, n, st));
+    else if (tc_grams(tc, n, npts))
+        RS_TRY(umma_gram((const float *)Psi, ld, n, (const float *)Psi, ld, n, npts, dV, w.U, n, tc.p, tc.err, st));
     else
         RS_TRY(gram<float>((const float *)Psi, ld, n, (const float *)Psi, ld, n, npts, dV, w.U, n, st));
     RS_TRY(symmetrize(w.U, n, n, st));
@@ -85,10 +93,12 @@ int subspace_diag_impl(rs_ham *h, void *Psi, void *HPsi, int64_t ld, int n, int 
                                   std::min(nb, n - b), dtype, st));
     if (dtype == RS_F64)
         RS_TRY(gram<double>((const double *)Psi, ld, n, (const double *)HPsi, ld, n, npts, dV, w.S, n, st));
+    else if (tc_grams(tc, n, npts))
+        RS_TRY(umma_gram((const float *)Psi, ld, n, (const float *)HPsi, ld, n, npts, dV, w.S, n, tc.p, tc.err, st));
     else
         RS_TRY(gram<float>((const float *)Psi, ld, n, (const float *)HPsi, ld, n, npts, dV, w.S, n, st));
     RS_TRY(symmetrize(w.S, n, n, st));
-    RS_TRY(eigh(w.S, n, n, eps_dev, w.xi, n, 2, w.status, w.eigw, st));
+    RS_TRY(eigh(w.S, n, n, eps_dev, w.xi, n, dtype == RS_F32 && tc.inner ? -1 : 2, w.status, w.eigw, st));
     RS_TRY(rotate_inplace(Psi, ld, n, w.xi, npts, dtype, st, tc));
     return rotate_inplace(HPsi, ld, n, w.xi, npts, dtype, st, tc);
 }

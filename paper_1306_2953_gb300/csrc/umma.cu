@@ -35,6 +35,7 @@
 namespace rs {
 
 constexpr int UM_BM = 128, UM_BK = 64, UM_NT = 128;
+constexpr int UM_KB_CTA = 32;   // K blocks per CTA of a split-K contraction (2048 points)
 constexpr long long UM_SPIN = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -360,8 +361,13 @@ int umma_gram(const float *X, int64_t ldx, int nx, const float *Y, int64_t ldy, 
     __nv_bfloat16 *PA = reinterpret_cast<__nv_bfloat16 *>(work);
     __nv_bfloat16 *PB = PA + 3 * round_up(nx, UM_BM) * Kp;
     dim3 tb(32, 8);
+    // S = X^T X: one split serves both operands
+    const bool same = X == Y && ldx == ldy && nx == ny;
+    if (same) PB = PA;
     k_split_t<float><<<dim3((unsigned)(Kp / 32), (unsigned)((nx + 31) / 32)), tb, 0, st>>>(X, ldx, (int)npts, nx, (int)Kp, PA);
-    k_split_t<float><<<dim3((unsigned)(Kp / 32), (unsigned)((ny + 31) / 32)), tb, 0, st>>>(Y, ldy, (int)npts, ny, (int)Kp, PB);
+    if (!same)
+        k_split_t<float><<<dim3((unsigned)(Kp / 32), (unsigned)((ny + 31) / 32)), tb, 0, st>>>(Y, ldy, (int)npts, ny, (int)Kp,
+                                                                                             PB);
     RS_LAUNCH_CHECK();
     CUtensorMap ta, tbm;
     RS_TRY(make_map(&ta, PA, nx, (int)Kp, UM_BM));
@@ -374,7 +380,10 @@ int umma_gram(const float *X, int64_t ldx, int nx, const float *Y, int64_t ldy, 
     const int tiles = ((nx + UM_BM - 1) / UM_BM) * ((ny + BN - 1) / BN);
     const int nkb = (int)(Kp / UM_BK);
     int splits = std::max(1, std::min(nkb, (148 + tiles - 1) / tiles));
-    a.kb_per_cta = (nkb + splits - 1) / splits;
+    // at most UM_KB_CTA K blocks accumulate in FP32 per CTA; the partial
+    // sums meet in FP64, so the rounding of the contraction stays near that
+    // of one FP32 sum of UM_KB_CTA * 64 terms
+    a.kb_per_cta = std::min((nkb + splits - 1) / splits, UM_KB_CTA);
     splits = (nkb + a.kb_per_cta - 1) / a.kb_per_cta;
     a.mode = 0;
     a.alpha = dV;

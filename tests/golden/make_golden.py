@@ -5,9 +5,11 @@ and the benchmark's time-to-accuracy measurement.
 
 Calls only the FP64 CPU oracle (``oracle/``) on the seeded synthetic
 workloads of ``workloads``: block CG from the workload's random start
-vectors, converged to a residual norm of 1e-9 (eigenvalue error ~1e-18
-times the inverse gap), plus, for the harmonic oscillator, the separable
-closed form.  Output: tests/golden/eigs_<workload>.json.
+vectors, converged until every judged state's residual norm is below 1e-9
+(molecules of 100 or more atoms: 1e-6), so that the eigenvalue error, of
+order residual^2 / gap, is far below the 1e-8 Ha / 1e-6 Ha targets, plus,
+for the harmonic oscillator, the separable closed form.  Output:
+tests/golden/eigs_<workload>.json.
 """
 from __future__ import annotations
 
@@ -67,10 +69,11 @@ def main(names):
                 print(f"  sweep {s.iterations} max residual {log[-1]:.3e} eps0 {s.eps[0]:.10f} "
                       f"{time.time() - t0:.0f}s", flush=True)
 
-        solver = eigensolver.BlockCG(H, psi0, w.block, precond=pc, tol=1e-9)
+        tol = 1e-6 if big else 1e-9
+        solver = eigensolver.BlockCG(H, psi0, w.block, precond=pc, tol=tol)
         eps = solver.solve(max_iter=3000, judged=w.judged, callback=progress)
         out = {"workload": name, "npts": g.npts, "n_states": w.n_states, "judged": w.judged,
-               "eigenvalues": [float(v) for v in eps], "residual_tol": 1e-9, "iterations": solver.iterations,
+               "eigenvalues": [float(v) for v in eps], "residual_tol": tol, "iterations": solver.iterations,
                "max_residual": float(np.max(solver.resnorm[:w.judged])), "cpu_seconds": time.time() - t0,
                "preconditioner": "kinetic CG(10), sigma=1" if big else "filter alpha=0.5",
                "source": "oracle/eigensolver.py BlockCG (FP64), written by tests/golden/make_golden.py"}

@@ -59,9 +59,10 @@ def test_hpsi_f64_parity(system, nb):
     assert np.max(_rel_err_per_state(out, ref)) <= 1e-12
 
 
+@pytest.mark.parametrize("system", list(SYSTEMS))
 @pytest.mark.parametrize("nb", [4, 16, 32, 64])
-def test_hpsi_f32_parity(nb):
-    kind, params = SYSTEMS["small_mol"]
+def test_hpsi_f32_parity(system, nb):
+    kind, params = SYSTEMS[system]
     lg, H, g_ora, H_ora, idx = _lib_system(kind, params)
     psi32 = wl.random_block(g_ora.npts, nb, 7).astype(np.float32)
     # the oracle sees the FP32 inputs exactly, the potential and projectors in FP64
@@ -73,6 +74,43 @@ def test_hpsi_f32_parity(nb):
     ref = H_ora.apply(smooth.astype(np.float64))[idx]
     out = H.apply(torch.from_numpy(np.ascontiguousarray(smooth[idx])).cuda()).cpu().numpy()
     assert np.max(_rel_err_per_state(out.astype(np.float64), ref)) <= 3e-5
+    assert H.status() == 0
+
+
+@pytest.mark.parametrize("ld,col0,nb", [(96, 32, 32), (96, 32, 64), (128, 64, 64), (36, 4, 32)])
+def test_hpsi_f32_blocks_of_wide_psi(ld, col0, nb):
+    """FP32 blocks that are column slices of a wider orbital array (the
+    eigensolver's layout), including a slice whose rows start 16 bytes into a
+    row; columns outside the block are left untouched."""
+    kind, params = SYSTEMS["small_mol"]
+    lg, H, g_ora, H_ora, idx = _lib_system(kind, params)
+    psi32 = wl.random_block(g_ora.npts, ld, 21).astype(np.float32)
+    full = torch.from_numpy(np.ascontiguousarray(psi32[idx])).cuda()
+    out = torch.full_like(full, 7.0)
+    H.apply(full[:, col0:col0 + nb], out[:, col0:col0 + nb], nb=nb)
+    ref = H_ora.apply(psi32[:, col0:col0 + nb].astype(np.float64))[idx]
+    o = out.cpu().numpy().astype(np.float64)
+    assert np.max(_rel_err_per_state(o[:, col0:col0 + nb], ref)) <= 2e-6
+    assert np.all(o[:, :col0] == 7.0) and np.all(o[:, col0 + nb:] == 7.0)
+    assert H.status() == 0
+
+
+def test_hpsi_f32_mol20_repeated_calls():
+    """Repeated calls on one handle, one and two state groups: the kernel's
+    work queue restarts cleanly on every call.  (The projection integrals are
+    summed with atomics, so repeated results agree to rounding, not bitwise.)"""
+    spec = wl.MOL20.system
+    lg, H, g_ora, H_ora, idx = _lib_system("mol", (spec,))
+    psi32 = wl.random_block(g_ora.npts, 64, 31).astype(np.float32)
+    ref = H_ora.apply(psi32.astype(np.float64))[idx]
+    psi = torch.from_numpy(np.ascontiguousarray(psi32[idx])).cuda()
+    for _ in range(3):
+        o = H.apply(psi, nb=32)[:, :32].cpu().numpy().astype(np.float64)
+        assert np.max(_rel_err_per_state(o, ref[:, :32])) <= 2e-6
+    for _ in range(2):
+        o = H.apply(psi, nb=64).cpu().numpy().astype(np.float64)
+        assert np.max(_rel_err_per_state(o, ref)) <= 2e-6
+    assert H.status() == 0
 
 
 def test_hpsi_strided_block_and_untouched_columns():
@@ -114,3 +152,4 @@ def test_hpsi_full_size_mol100(dtype):
     out = H.apply(psi).double().cpu().numpy()
     tol = 1e-12 if dtype == "f64" else 2e-6
     assert np.max(_rel_err_per_state(out, ref)) <= tol
+    assert H.status() == 0

@@ -61,11 +61,15 @@ class Workload:
 
 
 # The five workloads of the hot path (harmonic oscillator, 20/100/300 atoms).
+# The 100- and 300-atom molecules iterate n_states states but judge the
+# eigenvalues of all but the top block: those states have no higher
+# neighbours inside the iterated subspace and converge far more slowly, so
+# the top block serves as the usual convergence buffer.
 HO32 = Workload("ho32_h0.3", BoxSpec(32, 0.3, 1.0), 16, 16, 10, "f64", "filter", 1306)
 MOL20 = Workload("mol20_h0.35", MoleculeSpec(20, 12.0, 2.0, 5.0, 0.35, 1306), 48, 16, 48, "f64", "filter", 1306)
-MOL100 = Workload("mol100_h0.3", MoleculeSpec(100, 22.0, 2.0, 5.0, 0.3, 1307), 256, 32, 256, "mixed", "filter", 1307)
-MOL100_LEARNED = Workload("mol100_h0.3_learned", MOL100.system, 256, 32, 256, "mixed", "learned", 1307)
-MOL300 = Workload("mol300_h0.3", MoleculeSpec(300, 32.0, 2.0, 5.0, 0.3, 1308), 1024, 32, 1024, "mixed", "learned", 1308)
+MOL100 = Workload("mol100_h0.3", MoleculeSpec(100, 22.0, 2.0, 5.0, 0.3, 1307), 256, 32, 224, "mixed", "filter", 1307)
+MOL100_LEARNED = Workload("mol100_h0.3_learned", MOL100.system, 256, 32, 224, "mixed", "learned", 1307)
+MOL300 = Workload("mol300_h0.3", MoleculeSpec(300, 32.0, 2.0, 5.0, 0.3, 1308), 1024, 32, 992, "mixed", "learned", 1308)
 WORKLOADS = {w.name: w for w in (HO32, MOL20, MOL100, MOL100_LEARNED, MOL300)}
 
 
