@@ -168,6 +168,31 @@ def run_reference(args, workload):
     return 0
 
 
+def profiled_traffic():
+    """DRAM bytes (read + write) per launch of the H psi kernel from the
+    committed ncu summary, or None when the kernel source has changed since
+    that capture (the summary records the source's SHA-1)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_hpsi_ring_mol100.md")
+    src = os.path.join(ROOT, "paper_1306_2953_gb300", "csrc", "stencil_ring.cu")
+    if not (os.path.exists(prof) and os.path.exists(src)):
+        return None
+    with open(src, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    fields = {}
+    with open(prof) as f:
+        for line in f:
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+    if fields.get("stencil_ring.cu sha1") != sha:
+        return None
+    try:
+        return int(fields["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_golden(name):
     p = os.path.join(ROOT, "tests", "golden", f"eigs_{name}.json")
     if not os.path.exists(p):
@@ -250,6 +275,21 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
     return out
 
 
+def profile_sweeps(workload, n):
+    import torch
+    from paper_1306_2953_gb300 import api
+    g, H = build_system(workload)
+    psi0 = torch.from_numpy(wl.random_block(g.npts, workload.n_states, workload.seed)).float().cuda()
+    S = api.Solver(H, psi0, workload.block, 1e-4)
+    for _ in range(n):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.step()
+        torch.cuda.synchronize()
+        print(json.dumps({"sweep_seconds": time.perf_counter() - t0}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -260,10 +300,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eigensolve", default="mol20_h0.35",
                     help="workload(s) for the time-to-1e-6 Ha eigensolve, comma separated, or 'none'")
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="profiling aid: run this many mixed-precision eigensolver sweeps on --workload, "
+                         "print their times and exit (no benchmark line)")
     args = ap.parse_args()
     workload = wl.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, workload)
+    if args.profile_sweeps > 0:
+        return profile_sweeps(workload, args.profile_sweeps)
 
     import torch
     import torch.distributed as dist
@@ -346,9 +391,10 @@ def main():
             "config": {"workload": workload.name, "npts": npts, "states": nst, "block": NB,
                        "psi_bytes": psi.numel() * 4, "l2": "inputs (psi, 0.73 GB) larger than L2 (129 MB)",
                        "parallelism": f"replicas{world}"},
-            "roofline": {"bound": "hbm", "kernel": "k_stencil (fused stencil + V + nonlocal gather)",
+            "roofline": {"bound": "hbm", "kernel": "k_hpsi_ring (fused stencil + V + nonlocal gather)",
                          "achieved": stencil_gbs, "peak": peak, "unit": "GB/s", "frac": stencil_gbs / peak,
-                         "peak_source": peak_kind, "traffic": None,
+                         "peak_source": peak_kind, "traffic": profiled_traffic(),
+                         "algorithmic_bytes_per_launch": sb.value,
                          "stencil_ms_per_launch": sms.value / max(ncalls.value, 1),
                          "project_ms_per_launch": pms.value / max(ncalls.value, 1)},
             "e2e": {"value": world * bytes_per_step / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,

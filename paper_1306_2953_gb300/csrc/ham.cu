@@ -20,6 +20,9 @@
 //     nor atomics, and the output is written exactly once.
 // Orbitals are [npts][ld] with the state index fastest (Sec. IV, Fig. 4b);
 // grid points are addressed through the int32 point map (Sec. V.A).
+// FP32 blocks whose state count is a multiple of 32 take the persistent
+// ring-buffer kernel of stencil_ring.cu for step 2 instead; k_stencil serves
+// FP64 blocks, narrower state groups and layouts that kernel cannot copy.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -32,10 +35,6 @@
 #include "ham.h"
 #include "stencil_ring.h"
 
-#ifndef RS_STENCIL_V3
-#define RS_STENCIL_V3 0
-#endif
-
 // 1: FP32 blocks of 32 states go to the persistent ring-buffer kernel
 // (stencil_ring.cu) when the block's layout allows 16-byte row copies.
 #ifndef RS_STENCIL_RING
@@ -44,7 +43,7 @@
 
 // Height (planes) of the z-slabs of that kernel's work units.
 #ifndef RS_RING_SLAB
-#define RS_RING_SLAB 32
+#define RS_RING_SLAB 64
 #endif
 
 #ifndef RS_STENCIL_MINB_F32
@@ -355,557 +354,6 @@ __global__ void __launch_bounds__(StencilCfg<T, SG, TX, TY>::NT, StencilCfg<T, S
     cp_async_wait<0>();
 }
 
-// ------------------------------- FP32 kernel with per-chunk NL staging ---
-// The same march as k_stencil for FP32 blocks of 32 states on 8 x 8 tiles, with
-// everything irregular about a work item staged in shared memory once, at its
-// start: interior and halo point rows, each output point's potential, and the
-// nonlocal entries (projector values and atom) of all its output points (the
-// host bounds the entries of a work item by V3_CAP).  In the march the only
-// global traffic is psi (queue refill, halo copies), the projection
-// coefficients (L1-resident) and the H psi stores.
-
-constexpr int V3_CAP = 3584;   // nonlocal entries per work item
-constexpr int V3_TX = 8, V3_TY = 8, V3_SG = 32;
-
-struct V3Cfg {
-    static constexpr int TX = V3_TX, TY = V3_TY, SG = V3_SG;
-    static constexpr int W2 = TX + 8, W1 = TY + 8;
-    static constexpr int PLANE = W1 * W2 * SG;
-    static constexpr int NT = (TX / 2) * (TY / 2) * SG;   // 512
-    static constexpr int RING = 3;
-    static constexpr int CPR = 8;                          // 16-byte copies per 128-byte row
-    static constexpr int NH = 8 * TY + 8 * TX;
-    static constexpr int HPT = (NH * CPR + NT - 1) / NT;
-    static constexpr int NI = TX * TY;
-    static constexpr size_t OFF_ROWS = (size_t)RING * PLANE * 4;
-    static constexpr size_t OFF_HROWS = OFF_ROWS + (size_t)(ZCHUNK + 9) * NI * 4;
-    static constexpr size_t OFF_PV = OFF_HROWS + (size_t)ZCHUNK * NH * 4;
-    static constexpr size_t OFF_PE = OFF_PV + (size_t)ZCHUNK * NI * 4;
-    static constexpr size_t OFF_EG = OFF_PE + (size_t)ZCHUNK * NI * 4;
-    static constexpr size_t OFF_EA = OFF_EG + (size_t)V3_CAP * 16;
-    static constexpr size_t OFF_SCAN = OFF_EA + (size_t)V3_CAP * 4;
-    static constexpr size_t SMEM = OFF_SCAN + 32 * 4;
-};
-
-__global__ void __launch_bounds__(V3Cfg::NT, 1)
-    k_stencil_v3(HamDev<float> d, const float *__restrict__ psi, int64_t ldp, float *__restrict__ hpsi, int64_t ldh,
-                 const float *__restrict__ cproj, int nb, const int4 *__restrict__ work) {
-    using C = V3Cfg;
-    constexpr int TX = C::TX, TY = C::TY, SG = C::SG;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    float *sm = reinterpret_cast<float *>(smraw);
-    int *rows = reinterpret_cast<int *>(smraw + C::OFF_ROWS);
-    int *hrows = reinterpret_cast<int *>(smraw + C::OFF_HROWS);
-    float *pv = reinterpret_cast<float *>(smraw + C::OFF_PV);
-    int *pe = reinterpret_cast<int *>(smraw + C::OFF_PE);
-    float4 *eg = reinterpret_cast<float4 *>(smraw + C::OFF_EG);
-    int *ea = reinterpret_cast<int *>(smraw + C::OFF_EA);
-    int *wsum = reinterpret_cast<int *>(smraw + C::OFF_SCAN);
-
-    const int tid = threadIdx.x;
-    const int s = tid % SG;
-    const int patch = tid / SG;
-    const int lx = 2 * (patch % (TX / 2));
-    const int ly = 2 * (patch / (TX / 2));
-    const int4 wk = work[blockIdx.x];
-    const int b1 = wk.x * TY, b2 = wk.y * TX;
-    const int za = wk.z, zb = wk.w;
-    const int nz = zb - za;
-    const int sg0 = blockIdx.y * SG;
-    const float *psig = psi + sg0;
-
-    auto map_at = [&](int a0, int a1, int a2) -> int {
-        if ((unsigned)a0 >= (unsigned)d.d0 || (unsigned)a1 >= (unsigned)d.d1 || (unsigned)a2 >= (unsigned)d.d2)
-            return -1;
-        return __ldg(d.map + ((int64_t)a0 * d.d1 + a1) * d.d2 + a2);
-    };
-    auto halo_pos = [&](int hh, int &hy, int &hx) {
-        if (hh < 8 * TY) {
-            hy = hh >> 3;
-            const int t = hh & 7;
-            hx = t < 4 ? t - 4 : TX + t - 4;
-        } else {
-            const int h2 = hh - 8 * TY;
-            hx = h2 % TX;
-            const int t = h2 / TX;
-            hy = t < 4 ? t - 4 : TY + t - 4;
-        }
-    };
-
-    // ---- stage the work item's rows
-    for (int e = tid; e < (nz + 9) * C::NI; e += C::NT) {
-        const int pl = e / C::NI, pos = e % C::NI;
-        rows[e] = map_at(za - 4 + pl, b1 + pos / TX, b2 + pos % TX);
-    }
-    for (int e = tid; e < nz * C::NH; e += C::NT) {
-        int hy, hx;
-        halo_pos(e % C::NH, hy, hx);
-        hrows[e] = map_at(za + e / C::NH, b1 + hy, b2 + hx);
-    }
-    __syncthreads();
-    // ---- potential and nonlocal entry counts of the output points; exclusive scan
-    constexpr int PPT = ZCHUNK * C::NI / C::NT;   // output points per thread (4)
-    int cnt[PPT], e0[PPT], tot = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int lp = tid * PPT + k;
-        cnt[k] = 0;
-        e0[k] = 0;
-        float v = 0.f;
-        if (lp < nz * C::NI) {
-            const int r = rows[(lp / C::NI + 4) * C::NI + lp % C::NI];
-            if (r >= 0) {
-                const int4 inf = __ldg(d.pinfo + r);
-                e0[k] = inf.x;
-                cnt[k] = inf.y - inf.x;
-                v = __int_as_float(inf.z);
-            }
-            pv[lp] = v;
-        }
-        tot += cnt[k];
-    }
-    // block-wide exclusive scan of tot
-    int incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((tid & 31) >= o) incl += y;
-    }
-    if ((tid & 31) == 31) wsum[tid >> 5] = incl;
-    __syncthreads();
-    if (tid < 32) {
-        int x = tid < C::NT / 32 ? wsum[tid] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (tid >= o) x += y;
-        }
-        wsum[tid] = x;  // inclusive per-warp totals
-    }
-    __syncthreads();
-    int start = incl - tot + ((tid >> 5) ? wsum[(tid >> 5) - 1] : 0);
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int lp = tid * PPT + k;
-        if (lp < nz * C::NI) pe[lp] = (start << 4) | cnt[k];
-        for (int j = 0; j < cnt[k]; ++j) {
-            if (start + j < V3_CAP) {
-                const float4 gv = __ldg(reinterpret_cast<const float4 *>(d.cov_gam) + e0[k] + j);
-                eg[start + j] = gv;
-                ea[start + j] = __ldg(d.cov_atom + e0[k] + j) * nb;
-            }
-        }
-        start += cnt[k];
-    }
-
-    auto row_of = [&](int z, int iy, int ix) -> int { return rows[(z - za + 4) * C::NI + iy * TX + ix]; };
-    auto load_val = [&](int r) -> float { return r >= 0 ? __ldg(psig + (int64_t)r * ldp + s) : 0.f; };
-    auto issue_halo = [&](int z, int slot) {
-        float *base = sm + slot * C::PLANE;
-        const int *hr = hrows + (z - za) * C::NH;
-#pragma unroll
-        for (int j = 0; j < C::HPT; ++j) {
-            const int i = tid + j * C::NT;
-            if (i >= C::NH * C::CPR) continue;
-            const int hh = i / C::CPR, c = i % C::CPR;
-            int hy, hx;
-            halo_pos(hh, hy, hx);
-            const int r = hr[hh];
-            const float *src = r >= 0 ? psig + (int64_t)r * ldp + c * 4 : psig;
-            cp_async<16>(base + ((hy + 4) * C::W2 + (hx + 4)) * SG + c * 4, src, r >= 0);
-        }
-    };
-    __syncthreads();
-
-    float q[2][2][9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) q[dy][dx][k] = load_val(row_of(za - 4 + k, ly + dy, lx + dx));
-    issue_halo(za, 0);
-    cp_async_commit();
-    if (za + 1 < zb) issue_halo(za + 1, 1);
-    cp_async_commit();
-
-    const float w0 = d.w[0], w1 = d.w[1], w2 = d.w[2], w3 = d.w[3], w4 = d.w[4];
-    const float *cpl = cproj + (int64_t)(sg0 + s) * 4;
-    int slot = 0;
-    for (int z = za; z < zb; ++z) {
-        const int pslot = slot == 0 ? 2 : slot - 1;
-        if (z + 2 < zb) issue_halo(z + 2, pslot);
-        cp_async_commit();
-        float nq[2][2];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) nq[dy][dx] = load_val(row_of(z + 5, ly + dy, lx + dx));
-        float *P = sm + slot * C::PLANE;
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) P[((ly + dy + 4) * C::W2 + lx + dx + 4) * SG + s] = q[dy][dx][4];
-        cp_async_wait<2>();
-        __syncthreads();
-
-        float acc[2][2];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx)
-                acc[dy][dx] = w0 * q[dy][dx][4] + w1 * (q[dy][dx][5] + q[dy][dx][3]) + w2 * (q[dy][dx][6] + q[dy][dx][2]) +
-                              w3 * (q[dy][dx][7] + q[dy][dx][1]) + w4 * (q[dy][dx][8] + q[dy][dx][0]);
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-            float v[10];
-#pragma unroll
-            for (int k = 0; k < 10; ++k)
-                if (k != 4 && k != 5) v[k] = P[((ly + dy + 4) * C::W2 + lx + k) * SG + s];
-            v[4] = q[dy][0][4];
-            v[5] = q[dy][1][4];
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx)
-                acc[dy][dx] += w1 * (v[5 + dx] + v[3 + dx]) + w2 * (v[6 + dx] + v[2 + dx]) + w3 * (v[7 + dx] + v[1 + dx]) +
-                               w4 * (v[8 + dx] + v[0 + dx]);
-        }
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-            float v[10];
-#pragma unroll
-            for (int k = 0; k < 10; ++k)
-                if (k != 4 && k != 5) v[k] = P[((ly + k) * C::W2 + lx + dx + 4) * SG + s];
-            v[4] = q[0][dx][4];
-            v[5] = q[1][dx][4];
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
-                acc[dy][dx] += w1 * (v[5 + dy] + v[3 + dy]) + w2 * (v[6 + dy] + v[2 + dy]) + w3 * (v[7 + dy] + v[1 + dy]) +
-                               w4 * (v[8 + dy] + v[0 + dy]);
-        }
-        const int pbase = (z - za) * C::NI;
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int pos = (ly + dy) * TX + lx + dx;
-                const int r = rows[(z - za + 4) * C::NI + pos];
-                if (r < 0) continue;
-                const int code = pe[pbase + pos];
-                float out = acc[dy][dx] + pv[pbase + pos] * q[dy][dx][4];
-                const int e1 = min((code >> 4) + (code & 15), V3_CAP);
-                for (int e = code >> 4; e < e1; ++e) {
-                    const float4 gv = eg[e];
-                    const float4 c4 = __ldg(reinterpret_cast<const float4 *>(cpl + (int64_t)ea[e] * 4) );
-                    out += gv.x * c4.x + gv.y * c4.y + gv.z * c4.z + gv.w * c4.w;
-                }
-                hpsi[(int64_t)r * ldh + sg0 + s] = out;
-            }
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) q[dy][dx][k] = q[dy][dx][k + 1];
-                q[dy][dx][8] = nq[dy][dx];
-            }
-        slot = slot == 2 ? 0 : slot + 1;
-        __syncthreads();
-    }
-    cp_async_wait<0>();
-}
-
-// ------------------------- FP32 kernel v4: two states per lane, packed FMA ---
-// Same work items and staging as k_stencil_v3, but every lane owns two
-// adjacent states (a float2) so that the stencil runs on the packed FP32x2
-// pipes (one FFMA2 / FADD2 per two outputs) and each shared-memory or global
-// access moves 8 bytes; 16 lanes cover a point's 32 states and a warp two
-// 2 x 2 patches.  The 9-deep plane queue is rotated by unrolling the march
-// nine times instead of moving registers.
-
-struct V4Cfg {
-    static constexpr int TX = V3_TX, TY = V3_TY, SG = V3_SG;
-    static constexpr int W2 = TX + 8, W1 = TY + 8;
-    static constexpr int PLANE = W1 * W2 * SG;
-    static constexpr int NT = (TX / 2) * (TY / 2) * (SG / 2);   // 256
-    static constexpr int RING = 3;
-    static constexpr int CPR = 8;
-    static constexpr int NH = 8 * TY + 8 * TX;
-    static constexpr int HPT = (NH * CPR + NT - 1) / NT;       // 4
-    static constexpr int NI = TX * TY;
-    static constexpr size_t OFF_ROWS = (size_t)RING * PLANE * 4;
-    static constexpr size_t OFF_HROWS = OFF_ROWS + (size_t)(ZCHUNK + 9) * NI * 4;
-    static constexpr size_t OFF_PV = OFF_HROWS + (size_t)ZCHUNK * NH * 4;
-    static constexpr size_t OFF_PE = OFF_PV + (size_t)ZCHUNK * NI * 4;
-    static constexpr size_t OFF_EG = OFF_PE + (size_t)ZCHUNK * NI * 4;
-    static constexpr size_t OFF_EA = OFF_EG + (size_t)V3_CAP * 16;
-    static constexpr size_t OFF_SCAN = OFF_EA + (size_t)V3_CAP * 4;
-    static constexpr size_t SMEM = OFF_SCAN + 32 * 4;
-};
-
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 pair_sum(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-template <int N> struct IC { static constexpr int value = N; };
-
-__global__ void __launch_bounds__(V4Cfg::NT, 1)
-    k_stencil_v4(HamDev<float> d, const float *__restrict__ psi, int64_t ldp, float *__restrict__ hpsi, int64_t ldh,
-                 const float *__restrict__ cproj, int nb, const int4 *__restrict__ work) {
-    using C = V4Cfg;
-    constexpr int TX = C::TX, TY = C::TY, SG = C::SG;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    float *sm = reinterpret_cast<float *>(smraw);
-    int *rows = reinterpret_cast<int *>(smraw + C::OFF_ROWS);
-    int *hrows = reinterpret_cast<int *>(smraw + C::OFF_HROWS);
-    float *pv = reinterpret_cast<float *>(smraw + C::OFF_PV);
-    int *pe = reinterpret_cast<int *>(smraw + C::OFF_PE);
-    float4 *eg = reinterpret_cast<float4 *>(smraw + C::OFF_EG);
-    int *ea = reinterpret_cast<int *>(smraw + C::OFF_EA);
-    int *wsum = reinterpret_cast<int *>(smraw + C::OFF_SCAN);
-
-    const int tid = threadIdx.x;
-    const int s2 = tid % (SG / 2);          // state pair: states 2 s2, 2 s2 + 1 of the group
-    const int patch = tid / (SG / 2);
-    const int lx = 2 * (patch % (TX / 2));
-    const int ly = 2 * (patch / (TX / 2));
-    const int4 wk = work[blockIdx.x];
-    const int b1 = wk.x * TY, b2 = wk.y * TX;
-    const int za = wk.z, zb = wk.w;
-    const int nz = zb - za;
-    const int sg0 = blockIdx.y * SG;
-    const float *psig = psi + sg0;
-
-    auto map_at = [&](int a0, int a1, int a2) -> int {
-        if ((unsigned)a0 >= (unsigned)d.d0 || (unsigned)a1 >= (unsigned)d.d1 || (unsigned)a2 >= (unsigned)d.d2)
-            return -1;
-        return __ldg(d.map + ((int64_t)a0 * d.d1 + a1) * d.d2 + a2);
-    };
-    auto halo_pos = [&](int hh, int &hy, int &hx) {
-        if (hh < 8 * TY) {
-            hy = hh >> 3;
-            const int t = hh & 7;
-            hx = t < 4 ? t - 4 : TX + t - 4;
-        } else {
-            const int h2 = hh - 8 * TY;
-            hx = h2 % TX;
-            const int t = h2 / TX;
-            hy = t < 4 ? t - 4 : TY + t - 4;
-        }
-    };
-
-    // ---- stage the work item (as in k_stencil_v3)
-    for (int e = tid; e < (nz + 9) * C::NI; e += C::NT) {
-        const int pl = e / C::NI, pos = e % C::NI;
-        rows[e] = map_at(za - 4 + pl, b1 + pos / TX, b2 + pos % TX);
-    }
-    for (int e = tid; e < nz * C::NH; e += C::NT) {
-        int hy, hx;
-        halo_pos(e % C::NH, hy, hx);
-        hrows[e] = map_at(za + e / C::NH, b1 + hy, b2 + hx);
-    }
-    __syncthreads();
-    constexpr int PPT = ZCHUNK * C::NI / C::NT;   // 8
-    int cnt[PPT], e0[PPT], tot = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int lp = tid * PPT + k;
-        cnt[k] = 0;
-        e0[k] = 0;
-        float v = 0.f;
-        if (lp < nz * C::NI) {
-            const int r = rows[(lp / C::NI + 4) * C::NI + lp % C::NI];
-            if (r >= 0) {
-                const int4 inf = __ldg(d.pinfo + r);
-                e0[k] = inf.x;
-                cnt[k] = inf.y - inf.x;
-                v = __int_as_float(inf.z);
-            }
-            pv[lp] = v;
-        }
-        tot += cnt[k];
-    }
-    int incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((tid & 31) >= o) incl += y;
-    }
-    if ((tid & 31) == 31) wsum[tid >> 5] = incl;
-    __syncthreads();
-    if (tid < 32) {
-        int x = tid < C::NT / 32 ? wsum[tid] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (tid >= o) x += y;
-        }
-        wsum[tid] = x;
-    }
-    __syncthreads();
-    int start = incl - tot + ((tid >> 5) ? wsum[(tid >> 5) - 1] : 0);
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int lp = tid * PPT + k;
-        if (lp < nz * C::NI) pe[lp] = (start << 4) | cnt[k];
-        for (int j = 0; j < cnt[k]; ++j) {
-            if (start + j < V3_CAP) {
-                eg[start + j] = __ldg(reinterpret_cast<const float4 *>(d.cov_gam) + e0[k] + j);
-                ea[start + j] = __ldg(d.cov_atom + e0[k] + j) * nb;
-            }
-        }
-        start += cnt[k];
-    }
-    __syncthreads();
-
-    auto row_of = [&](int z, int iy, int ix) -> int { return rows[(z - za + 4) * C::NI + iy * TX + ix]; };
-    auto load2 = [&](int r) -> float2 {
-        return r >= 0 ? __ldg(reinterpret_cast<const float2 *>(psig + (int64_t)r * ldp) + s2) : make_float2(0.f, 0.f);
-    };
-    auto issue_halo = [&](int z, int slot) {
-        float *base = sm + slot * C::PLANE;
-        const int *hr = hrows + (z - za) * C::NH;
-#pragma unroll
-        for (int j = 0; j < C::HPT; ++j) {
-            const int i = tid + j * C::NT;
-            if (i >= C::NH * C::CPR) continue;
-            const int hh = i / C::CPR, c = i % C::CPR;
-            int hy, hx;
-            halo_pos(hh, hy, hx);
-            const int r = hr[hh];
-            const float *src = r >= 0 ? psig + (int64_t)r * ldp + c * 4 : psig;
-            cp_async<16>(base + ((hy + 4) * C::W2 + (hx + 4)) * SG + c * 4, src, r >= 0);
-        }
-    };
-
-    float2 q[2][2][9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) q[dy][dx][k] = load2(row_of(za - 4 + k, ly + dy, lx + dx));
-    issue_halo(za, 0);
-    cp_async_commit();
-    if (za + 1 < zb) issue_halo(za + 1, 1);
-    cp_async_commit();
-
-    const float2 W0 = f2(d.w[0]), W1 = f2(d.w[1]), W2 = f2(d.w[2]), W3 = f2(d.w[3]), W4 = f2(d.w[4]);
-    const float *cpl = cproj + (int64_t)(sg0 + 2 * s2) * 4;
-    int slot = 0;
-    // one plane of the march; queue slot of plane z + j is (j + 4 + R) % 9
-    auto step = [&](int z, auto Rc) {
-        constexpr int R = decltype(Rc)::value;
-#define QS(dy, dx, j) q[dy][dx][((j) + 4 + R) % 9]
-        const int pslot = slot == 0 ? 2 : slot - 1;
-        if (z + 2 < zb) issue_halo(z + 2, pslot);
-        cp_async_commit();
-        float2 nq[2][2];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) nq[dy][dx] = load2(row_of(z + 5, ly + dy, lx + dx));
-        float *P = sm + slot * C::PLANE;
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx)
-                reinterpret_cast<float2 *>(P + ((ly + dy + 4) * C::W2 + lx + dx + 4) * SG)[s2] = QS(dy, dx, 0);
-        cp_async_wait<2>();
-        __syncthreads();
-
-        float2 acc[2][2];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                float2 a = __fmul2_rn(W0, QS(dy, dx, 0));
-                a = fma2(W1, pair_sum(QS(dy, dx, 1), QS(dy, dx, -1)), a);
-                a = fma2(W2, pair_sum(QS(dy, dx, 2), QS(dy, dx, -2)), a);
-                a = fma2(W3, pair_sum(QS(dy, dx, 3), QS(dy, dx, -3)), a);
-                a = fma2(W4, pair_sum(QS(dy, dx, 4), QS(dy, dx, -4)), a);
-                acc[dy][dx] = a;
-            }
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-            float2 v[10];
-            const float2 *row = reinterpret_cast<const float2 *>(P + ((ly + dy + 4) * C::W2 + lx) * SG) + s2;
-#pragma unroll
-            for (int k = 0; k < 10; ++k)
-                if (k != 4 && k != 5) v[k] = row[k * (SG / 2)];
-            v[4] = QS(dy, 0, 0);
-            v[5] = QS(dy, 1, 0);
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                float2 a = acc[dy][dx];
-                a = fma2(W1, pair_sum(v[5 + dx], v[3 + dx]), a);
-                a = fma2(W2, pair_sum(v[6 + dx], v[2 + dx]), a);
-                a = fma2(W3, pair_sum(v[7 + dx], v[1 + dx]), a);
-                a = fma2(W4, pair_sum(v[8 + dx], v[0 + dx]), a);
-                acc[dy][dx] = a;
-            }
-        }
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-            float2 v[10];
-            const float2 *col = reinterpret_cast<const float2 *>(P + (ly * C::W2 + lx + dx + 4) * SG) + s2;
-#pragma unroll
-            for (int k = 0; k < 10; ++k)
-                if (k != 4 && k != 5) v[k] = col[k * C::W2 * (SG / 2)];
-            v[4] = QS(0, dx, 0);
-            v[5] = QS(1, dx, 0);
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy) {
-                float2 a = acc[dy][dx];
-                a = fma2(W1, pair_sum(v[5 + dy], v[3 + dy]), a);
-                a = fma2(W2, pair_sum(v[6 + dy], v[2 + dy]), a);
-                a = fma2(W3, pair_sum(v[7 + dy], v[1 + dy]), a);
-                a = fma2(W4, pair_sum(v[8 + dy], v[0 + dy]), a);
-                acc[dy][dx] = a;
-            }
-        }
-        const int pbase = (z - za) * C::NI;
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int pos = (ly + dy) * TX + lx + dx;
-                const int r = rows[(z - za + 4) * C::NI + pos];
-                if (r < 0) continue;
-                const int code = pe[pbase + pos];
-                float2 out = fma2(f2(pv[pbase + pos]), QS(dy, dx, 0), acc[dy][dx]);
-                const int e1 = min((code >> 4) + (code & 15), V3_CAP);
-                for (int e = code >> 4; e < e1; ++e) {
-                    const float4 gv = eg[e];
-                    const float4 *cp = reinterpret_cast<const float4 *>(cpl + (int64_t)ea[e] * 4);
-                    const float4 ca = __ldg(cp), cb = __ldg(cp + 1);
-                    out.x += gv.x * ca.x + gv.y * ca.y + gv.z * ca.z + gv.w * ca.w;
-                    out.y += gv.x * cb.x + gv.y * cb.y + gv.z * cb.z + gv.w * cb.w;
-                }
-                reinterpret_cast<float2 *>(hpsi + (int64_t)r * ldh + sg0)[s2] = out;
-            }
-        // the oldest plane's slot receives plane z + 5 (it is plane z + 4 of the next step)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) QS(dy, dx, -4) = nq[dy][dx];
-#undef QS
-        slot = slot == 2 ? 0 : slot + 1;
-        __syncthreads();
-    };
-    for (int z = za; z < zb; z += 9) {
-        step(z, IC<0>{});
-        if (z + 1 < zb) step(z + 1, IC<1>{}); else break;
-        if (z + 2 < zb) step(z + 2, IC<2>{}); else break;
-        if (z + 3 < zb) step(z + 3, IC<3>{}); else break;
-        if (z + 4 < zb) step(z + 4, IC<4>{}); else break;
-        if (z + 5 < zb) step(z + 5, IC<5>{}); else break;
-        if (z + 6 < zb) step(z + 6, IC<6>{}); else break;
-        if (z + 7 < zb) step(z + 7, IC<7>{}); else break;
-        if (z + 8 < zb) step(z + 8, IC<8>{}); else break;
-    }
-    cp_async_wait<0>();
-}
-
 // ----------------------------------------------- face-neighbour filter ---
 // W = alpha R + beta sum_{6 face neighbours} R (zero off the grid); one thread
 // per (point, state), state fastest.
@@ -963,7 +411,6 @@ struct rs_ham {
     DevBuf pinfo64, pinfo32, map, loc, V64, V32, cov_off, cov_atom, cov_gam64, cov_gam32, sph_off, sph_idx, sph_gam64, sph_gam32, E64, E32,
         cproj, dummy, scratch;
     std::map<std::pair<int, int>, WorkList *> work;
-    WorkList *work_v3 = nullptr;   // FP32 32-state kernel with bounded nonlocal entries per item
     RingPlan *ring = nullptr;      // tables of the ring-buffer FP32 kernel (nullptr: not usable)
     // optional per-launch timing (rs_ham_timing)
     bool timing = false;
@@ -971,7 +418,6 @@ struct rs_ham {
     size_t n_recorded = 0;
     ~rs_ham() {
         ring_plan_destroy(ring);
-        delete work_v3;
         for (auto &kv : work) delete kv.second;
         for (cudaEvent_t e : events) cudaEventDestroy(e);
     }
@@ -1070,60 +516,6 @@ static int build_work(rs_ham *H, const rs_grid *g, int tx, int ty) {
     return wl->buf.upload(items.data(), items.size() * sizeof(int4));
 }
 
-// Work items of k_stencil_v3: 8 x 8 tile columns cut into chunks of at most
-// ZCHUNK planes and at most V3_CAP nonlocal entries.  Returns false (no list)
-// when some point is covered by more than 15 projector spheres.
-static int build_work_v3(rs_ham *H, const rs_grid *g, const std::vector<int32_t> &coff, bool *ok) {
-    const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
-    const int tx = V3_TX, ty = V3_TY;
-    *ok = false;
-    for (int64_t p = 0; p < g->npts; ++p)
-        if (coff[p + 1] - coff[p] > 15) return RS_OK;
-    const int n1 = (d1 + ty - 1) / ty, n2 = (d2 + tx - 1) / tx;
-    std::vector<int4> items;
-    for (int t1 = 0; t1 < n1; ++t1)
-        for (int t2 = 0; t2 < n2; ++t2) {
-            int za = -1, entries = 0;
-            for (int a = 0; a < d0; ++a) {
-                int e = 0, any = 0;
-                for (int b = t1 * ty; b < std::min(d1, (t1 + 1) * ty); ++b)
-                    for (int c = t2 * tx; c < std::min(d2, (t2 + 1) * tx); ++c) {
-                        const int32_t p = g->map[((size_t)a * d1 + b) * d2 + c];
-                        if (p >= 0) {
-                            any = 1;
-                            e += coff[p + 1] - coff[p];
-                        }
-                    }
-                if (za >= 0 && (a - za == ZCHUNK || entries + e > V3_CAP)) {
-                    items.push_back(make_int4(t1, t2, za, a));
-                    za = -1;
-                    entries = 0;
-                }
-                if (any && za < 0) za = a;
-                if (za >= 0) entries += e;
-            }
-            if (za >= 0) {
-                // trim trailing empty planes
-                int zb = d0;
-                while (zb > za) {
-                    bool any = false;
-                    for (int b = t1 * ty; b < std::min(d1, (t1 + 1) * ty) && !any; ++b)
-                        for (int c = t2 * tx; c < std::min(d2, (t2 + 1) * tx) && !any; ++c)
-                            any = g->map[((size_t)(zb - 1) * d1 + b) * d2 + c] >= 0;
-                    if (any) break;
-                    --zb;
-                }
-                items.push_back(make_int4(t1, t2, za, zb));
-            }
-        }
-    WorkList *wl = new (std::nothrow) WorkList;
-    if (!wl) return fail(RS_ENOMEM, "host allocation failed");
-    H->work_v3 = wl;
-    wl->count = (int)items.size();
-    *ok = true;
-    return wl->buf.upload(items.data(), items.size() * sizeof(int4));
-}
-
 extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_proj *pr, int order, rs_ham **out) {
     if (!g || !V_host || !out) return fail(RS_EINVAL, "rs_ham_create: null argument");
     if (order < 1 || order > 4) return fail(RS_EINVAL, "rs_ham_create: order must be in 1..4");
@@ -1213,8 +605,6 @@ extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_pr
     }
     for (const Shape &s : kShapes)
         if ((rc = build_work(H, g, s.tx, s.ty))) return bail(rc);
-    bool v3ok = false;
-    if ((rc = build_work_v3(H, g, coff, &v3ok))) return bail(rc);
 #if RS_STENCIL_RING
     if ((rc = ring_plan_build(&H->ring, g, coff, catom, cg32, v32, na, RS_RING_SLAB))) return bail(rc);
 #endif
@@ -1243,35 +633,6 @@ static int launch_stencil(rs_ham *H, const HamDev<T> &d, const T *psi, int64_t l
                                                             wl->buf.as<int4>());
     RS_LAUNCH_CHECK();
     return RS_OK;
-}
-
-template <typename T>
-static int launch_v3(rs_ham *H, const HamDev<T> &d, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, int nb,
-                     cudaStream_t st) {
-    if constexpr (sizeof(T) != 4) {
-        return fail(RS_EINVAL, "launch_v3: FP32 only");
-    } else {
-        const WorkList *wl = H->work_v3;
-        if (wl->count == 0) return RS_OK;
-        dim3 grid((unsigned)wl->count, (unsigned)(nb / V3_SG));
-#if RS_STENCIL_V3
-        static bool attr_done = false;
-        if (!attr_done) {
-            RS_CUDA(cudaFuncSetAttribute(k_stencil_v3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V3Cfg::SMEM));
-            attr_done = true;
-        }
-        k_stencil_v3<<<grid, V3Cfg::NT, V3Cfg::SMEM, st>>>(d, psi, ldp, hpsi, ldh, H->cproj.as<T>(), nb, wl->buf.as<int4>());
-#else
-        static bool attr_done = false;
-        if (!attr_done) {
-            RS_CUDA(cudaFuncSetAttribute(k_stencil_v4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V4Cfg::SMEM));
-            attr_done = true;
-        }
-        k_stencil_v4<<<grid, V4Cfg::NT, V4Cfg::SMEM, st>>>(d, psi, ldp, hpsi, ldh, H->cproj.as<T>(), nb, wl->buf.as<int4>());
-#endif
-        RS_LAUNCH_CHECK();
-        return RS_OK;
-    }
 }
 
 template <typename T>
@@ -1313,10 +674,6 @@ static int apply_t(rs_ham *H, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, i
                         rc = ring_launch(H->ring, psi, ldp, hpsi, ldh, H->cproj.as<float>(), nb, w, st);
                         break;
                     }
-                }
-                if (H->work_v3) {
-                    rc = launch_v3(H, d, psi, ldp, hpsi, ldh, nb, st);
-                    break;
                 }
                 rc = launch_stencil<T, 32, 8, 8>(H, d, psi, ldp, hpsi, ldh, nb, st);
                 break;

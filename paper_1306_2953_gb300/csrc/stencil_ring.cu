@@ -70,7 +70,7 @@ constexpr int REC_HDR = 16;                // record header: entries count
 constexpr int META_BYTES = NPOS * 16;
 constexpr int MAX_REC = 40 * 1024;         // record slot budget (bytes)
 constexpr size_t MAX_SMEM = 227 * 1024;    // dynamic shared memory per CTA
-constexpr int MAX_SLAB = 32;               // planes per z-slab of a unit (at most)
+constexpr int MAX_SLAB = 128;              // planes per z-slab of a unit (at most)
 constexpr int MAX_UNITS = 64;              // units per CTA (shared-memory table)
 constexpr int SUSPEND_NS = 20000;           // suspension limit of one barrier test
 constexpr int SPIN = 100000;               // barrier tests before a wait gives up
