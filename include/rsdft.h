@@ -371,6 +371,13 @@ int rs_solver_psi(rs_solver *s, void **psi_dev);
  * Until weights are set the learned preconditioner refuses to run. */
 int rs_solver_set_precond_weights(rs_solver *s, const float *w_dev);
 
+/* Replaces the solver's preconditioner (RS_PRECOND_NONE / FILTER / LEARNED;
+ * a new learned preconditioner needs its weights set again) for the sweeps
+ * that follow, e.g. the plain filter as the fallback once the learned one
+ * stops reducing the residuals.  Blocking (waits for queued sweeps).
+ * Errors: RS_EINVAL. */
+int rs_solver_set_precond(rs_solver *s, int precond);
+
 int rs_solver_destroy(rs_solver *s);
 
 #ifdef __cplusplus

@@ -262,6 +262,10 @@ class Solver:
         call("rs_solver_psi", self._h, ctypes.byref(p))
         return _device_view(p.value, (self.ham.npts, self.nst), self.dtype, self.device)
 
+    def set_precond(self, kind: int):
+        """rs_solver_set_precond: switch the preconditioner for later sweeps."""
+        call("rs_solver_set_precond", self._h, int(kind))
+
     def set_precond_weights(self, w):
         """Learned-preconditioner weights: FP32 device tensor of 2160 values."""
         call("rs_solver_set_precond_weights", self._h, _c(w.data_ptr()))

@@ -361,9 +361,9 @@ template <typename T>
 __global__ void k_filter(const int32_t *__restrict__ map, const int32_t *__restrict__ loc, int64_t npts, int d1, int d2,
                          const T *__restrict__ R, int64_t ldr, T *__restrict__ W, int64_t ldw, int nb, T alpha,
                          T beta) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t p = t / nb;
-    const int s = (int)(t % nb);
+    // block (nb, 256 / nb): threadIdx.x is the state, threadIdx.y the point
+    const int s = threadIdx.x;
+    const int64_t p = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
     if (p >= npts) return;
     const int64_t L = __ldg(loc + p);
     const int64_t plane = (int64_t)d1 * d2;
@@ -767,14 +767,14 @@ double ham_dV(const rs_ham *h) { return h->dV; }
 
 int ham_filter(const rs_ham *h, const void *R, int64_t ldr, void *W, int64_t ldw, int nb, int dtype, double alpha,
                cudaStream_t st) {
-    const int64_t n = h->npts * nb;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const dim3 blk((unsigned)nb, (unsigned)std::max(1, 256 / nb));
+    const unsigned blocks = (unsigned)((h->npts + blk.y - 1) / blk.y);
     const double beta = (1.0 - alpha) / 6.0;
     if (dtype == RS_F64)
-        k_filter<double><<<blocks, 256, 0, st>>>(h->map.as<int32_t>(), h->loc.as<int32_t>(), h->npts, h->d[1], h->d[2],
+        k_filter<double><<<blocks, blk, 0, st>>>(h->map.as<int32_t>(), h->loc.as<int32_t>(), h->npts, h->d[1], h->d[2],
                                                  (const double *)R, ldr, (double *)W, ldw, nb, alpha, beta);
     else
-        k_filter<float><<<blocks, 256, 0, st>>>(h->map.as<int32_t>(), h->loc.as<int32_t>(), h->npts, h->d[1], h->d[2],
+        k_filter<float><<<blocks, blk, 0, st>>>(h->map.as<int32_t>(), h->loc.as<int32_t>(), h->npts, h->d[1], h->d[2],
                                                 (const float *)R, ldr, (float *)W, ldw, nb, (float)alpha, (float)beta);
     RS_LAUNCH_CHECK();
     return RS_OK;

@@ -32,10 +32,12 @@ namespace rs {
 
 constexpr int G_TM = 64, G_TN = 64, G_TK = 16, G_NT = 256;
 
+// Error-free transformation s + e = a + b (Knuth); the _rn intrinsics keep
+// the compiler from contracting any step into a fused multiply-add.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float z = s - a;
-    e = (a - (s - z)) + (b - z);
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
 // FP64 data: plain FP64 accumulation.  FP32 data: compensated float pairs.
@@ -55,7 +57,7 @@ struct GramAccFast {
 template <> struct GramAcc<float> {
     float hi = 0, lo = 0;
     __device__ __forceinline__ void add(float a, float b) {
-        const float p = a * b;
+        const float p = __fmul_rn(a, b);
         const float pe = fmaf(a, b, -p);   // exact: a*b = p + pe
         float s, e;
         two_sum(hi, p, s, e);

@@ -32,21 +32,41 @@ using namespace rs;
 
 namespace rs {
 
-// out[k] += sum_p A[p][k] B[p][k] for k < ncols (out zeroed by the caller)
+// out[k] += sum_p A[p][k] B[p][k] for k < ncols (out zeroed by the caller),
+// accumulated to FP64-level accuracy
 template <typename T>
 __global__ void k_coldots(const T *__restrict__ A, int64_t lda, const T *__restrict__ B, int64_t ldb, int ncols,
                           int64_t npts, double *out) {
     __shared__ double red[256];
     const int rows = blockDim.x / ncols;
     const int k = threadIdx.x % ncols, r = threadIdx.x / ncols;
-    double acc = 0.0, comp = 0.0;  // Kahan-compensated FP64 sum of exact products
+    double acc = 0.0;
     if (r < rows) {
-        for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
-            const double v = (double)A[p * lda + k] * (double)B[p * ldb + k];
-            const double y = v - comp;
-            const double t = acc + y;
-            comp = (t - acc) - y;
-            acc = t;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 data on the FP32 pipes: every product split exactly
+            // (p + pe = a b) and summed as an unevaluated pair (hi, lo) with
+            // error-free additions, i.e. FP64-level accuracy
+            float hi = 0.f, lo = 0.f;
+            for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+                const float a = A[p * lda + k], b = B[p * ldb + k];
+                const float pr = __fmul_rn(a, b);   // _rn: never contracted
+                const float pe = fmaf(a, b, -pr);
+                const float sum = __fadd_rn(hi, pr);
+                const float bb = __fsub_rn(sum, hi);
+                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(pr, bb));
+                hi = sum;
+                lo = __fadd_rn(lo, __fadd_rn(err, pe));
+            }
+            acc = (double)hi + (double)lo;
+        } else {
+            double comp = 0.0;  // Kahan-compensated FP64 sum of exact products
+            for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+                const double v = (double)A[p * lda + k] * (double)B[p * ldb + k];
+                const double y = v - comp;
+                const double t = acc + y;
+                comp = (t - acc) - y;
+                acc = t;
+            }
         }
     }
     red[threadIdx.x] = r < rows ? acc : 0.0;
@@ -459,6 +479,19 @@ extern "C" int rs_solver_set_precond_weights(rs_solver *S, const float *w_dev) {
     if (!S || !w_dev) return fail(RS_EINVAL, "rs_solver_set_precond_weights: null argument");
     RS_TRY(S->pc->set_weights(w_dev, nullptr));
     RS_CUDA(cudaDeviceSynchronize());
+    return RS_OK;
+}
+
+extern "C" int rs_solver_set_precond(rs_solver *S, int precond) {
+    if (!S) return fail(RS_EINVAL, "rs_solver_set_precond: null solver");
+    if (precond < RS_PRECOND_NONE || precond > RS_PRECOND_LEARNED)
+        return fail(RS_EINVAL, "rs_solver_set_precond: bad preconditioner");
+    Precond *p = Precond::create(precond, S->cfg.filter_alpha, S->npts, S->cfg.nb, S->cfg.dtype);
+    if (!p) return fail(RS_EINVAL, "rs_solver_set_precond: preconditioner %d unavailable", precond);
+    RS_CUDA(cudaDeviceSynchronize());   // no sweep still uses the old one
+    delete S->pc;
+    S->pc = p;
+    S->cfg.precond = precond;
     return RS_OK;
 }
 

@@ -280,17 +280,22 @@ __global__ void k_split_t(const T *__restrict__ X, int64_t ldx, int K, int C, in
     }
 }
 
-// Direct split: P[piece][r][k] = piece of X[r][k], k < K (padded to Kp).
+// Direct split: P[piece][r][k] = piece of X[r][k], k < K (padded to Kp, a
+// multiple of 64).  Block (64, 4): threadIdx.y picks one of four rows,
+// threadIdx.x strides the row's columns.
 template <typename T>
 __global__ void k_split_n(const T *__restrict__ X, int64_t ldx, int R, int K, int Kp, __nv_bfloat16 *__restrict__ P) {
     const int64_t n = (int64_t)R * Kp;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / Kp), k = (int)(e % Kp);
-        __nv_bfloat16 a, b, d;
-        split3(k < K ? (float)X[(int64_t)r * ldx + k] : 0.f, a, b, d);
-        P[e] = a;
-        P[n + e] = b;
-        P[2 * n + e] = d;
+    for (int r = blockIdx.x * 4 + threadIdx.y; r < R; r += gridDim.x * 4) {
+        const T *xr = X + (int64_t)r * ldx;
+        __nv_bfloat16 *pr = P + (int64_t)r * Kp;
+        for (int k = threadIdx.x; k < Kp; k += 64) {
+            __nv_bfloat16 a, b, d;
+            split3(k < K ? (float)xr[k] : 0.f, a, b, d);
+            pr[k] = a;
+            pr[n + k] = b;
+            pr[2 * n + k] = d;
+        }
     }
 }
 
@@ -401,7 +406,7 @@ int umma_rowmul(const float *X, int64_t ldx, int n, const double *C, int64_t ldc
     const int BN = m <= 64 ? 64 : 128;
     __nv_bfloat16 *PA = reinterpret_cast<__nv_bfloat16 *>(work);
     __nv_bfloat16 *PB = PA + 3 * round_up(npts, UM_BM) * Kp;
-    k_split_n<float><<<1024, 256, 0, st>>>(X, ldx, (int)npts, n, (int)Kp, PA);
+    k_split_n<float><<<2048, dim3(64, 4), 0, st>>>(X, ldx, (int)npts, n, (int)Kp, PA);
     // C^T: rows = output columns, K = n
     dim3 tb(32, 8);
     k_split_t<double><<<dim3((unsigned)(Kp / 32), (unsigned)((m + 31) / 32)), tb, 0, st>>>(C, ldc, n, m, (int)Kp, PB);

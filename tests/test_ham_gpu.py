@@ -153,3 +153,17 @@ def test_hpsi_full_size_mol100(dtype):
     tol = 1e-12 if dtype == "f64" else 2e-6
     assert np.max(_rel_err_per_state(out, ref)) <= tol
     assert H.status() == 0
+
+
+def test_hpsi_full_size_mol300_f32():
+    """The 300-atom molecule (1.8 million points, the largest workload) at
+    full size: one FP32 block of 32 states, whose coefficients no longer fit
+    the ring kernel's shared memory (global-memory nonlocal path)."""
+    spec = wl.MOL300.system
+    lg, H, g_ora, H_ora, idx = _lib_system("mol", (spec,))
+    psi_ora = wl.random_block(g_ora.npts, 32, 77).astype(np.float32).astype(np.float64)
+    ref = H_ora.apply(psi_ora)[idx]
+    psi = torch.from_numpy(np.ascontiguousarray(psi_ora[idx])).float().cuda()
+    out = H.apply(psi).double().cpu().numpy()
+    assert np.max(_rel_err_per_state(out, ref)) <= 2e-6
+    assert H.status() == 0
