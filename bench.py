@@ -211,7 +211,7 @@ def build_any(workload):
     return build_system(workload)
 
 
-def train_learned(H, g, solver, n_res=40, n_tiles=4000, epochs=5, seed=11):
+def train_learned(H, g, solver, n_res=40, n_tiles=10000, epochs=5, seed=11):
     """Learned-preconditioner weights from the method's own residuals: Ritz
     residuals of the current orbitals, their 200-iteration shifted-Poisson CG
     solutions, and Adam on tiles cut from the pairs."""

@@ -202,26 +202,70 @@ __global__ void k_tile_bwd_data(const float *__restrict__ gout, const float *__r
     for (int ci = 0; ci < CIN; ++ci) gin[((int64_t)tile * CIN + ci) * D3 + q] = acc[ci];
 }
 
-// dW[co][ci][t] += sum_{tile, p in chunk} gout[co][p] in[ci][p + off_t]
+// dW[co][ci][t] += sum over the tile points p (with p + d_t inside the tile)
+// of gout[co][p] * in[ci][p + d_t].  CTA (tile, slab of WB_PLANES planes):
+// the slab of gout and the slab plus one plane on either side of `in` are
+// staged in shared memory; thread (ci, t) keeps COUT accumulators.
+constexpr int WB_PLANES = 2;
 template <int CIN, int COUT>
 __global__ void k_tile_bwd_weight(const float *__restrict__ gout, const float *__restrict__ in, int ntiles, int D,
-                                  int chunk, float *__restrict__ dW) {
-    const int D3 = D * D * D;
-    const int64_t total = (int64_t)ntiles * D3;
-    const int64_t g0 = (int64_t)blockIdx.x * chunk;
-    const int64_t g1 = min(total, g0 + chunk);
-    for (int widx = threadIdx.x; widx < COUT * CIN * 27; widx += blockDim.x) {
-        const int co = widx / (CIN * 27), ci = (widx / 27) % CIN, t = widx % 27;
-        const int off = tap_offset(t, D);
-        float acc = 0.f;
-        for (int64_t gidx = g0; gidx < g1; ++gidx) {
-            const int tile = (int)(gidx / D3), p = (int)(gidx % D3);
-            const int i = p / (D * D), j = (p / D) % D, k = p % D;
-            if (!tap_inside(t, i, j, k, D)) continue;
-            acc = fmaf(gout[((int64_t)tile * COUT + co) * D3 + p], in[((int64_t)tile * CIN + ci) * D3 + p + off], acc);
-        }
-        atomicAdd(dW + widx, acc);
+                                  float *__restrict__ dW) {
+    extern __shared__ float wsm[];
+    const int D2 = D * D, D3 = D2 * D;
+    const int tile = blockIdx.x, i0 = blockIdx.y * WB_PLANES;
+    const int np = min(WB_PLANES, D - i0);
+    float *gs = wsm;                               // [COUT][np][D2]
+    float *as = wsm + COUT * WB_PLANES * D2;       // [CIN][np + 2][D2], plane i0 - 1 first
+    for (int e = threadIdx.x; e < COUT * np * D2; e += blockDim.x) {
+        const int co = e / (np * D2), r = e - co * np * D2;
+        gs[co * WB_PLANES * D2 + r] = gout[((int64_t)tile * COUT + co) * D3 + (int64_t)i0 * D2 + r];
     }
+    for (int e = threadIdx.x; e < CIN * (np + 2) * D2; e += blockDim.x) {
+        const int ci = e / ((np + 2) * D2), r = e - ci * (np + 2) * D2;
+        const int pl = i0 - 1 + r / D2;
+        as[ci * (WB_PLANES + 2) * D2 + r] =
+            (pl >= 0 && pl < D) ? in[((int64_t)tile * CIN + ci) * D3 + (int64_t)pl * D2 + r % D2] : 0.f;
+    }
+    __syncthreads();
+    const int w = threadIdx.x;
+    if (w >= CIN * 27) return;
+    const int ci = w / 27, t = w - ci * 27;
+    const int di = t / 9 - 1, dj = (t / 3) % 3 - 1, dk = t % 3 - 1;
+    float acc[COUT];
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
+    const float *ab = as + ci * (WB_PLANES + 2) * D2;
+    for (int pl = 0; pl < np; ++pl) {
+        if ((unsigned)(i0 + pl + di) >= (unsigned)D) continue;   // zero padding outside the tile
+        for (int j = max(0, -dj); j < min(D, D - dj); ++j) {
+            const float *arow = ab + (pl + 1 + di) * D2 + (j + dj) * D + dk;
+            const int gofs = pl * D2 + j * D;
+            for (int k = max(0, -dk); k < min(D, D - dk); ++k) {
+                const float x = arow[k];
+#pragma unroll
+                for (int co = 0; co < COUT; ++co) acc[co] = fmaf(gs[co * WB_PLANES * D2 + gofs + k], x, acc[co]);
+            }
+        }
+    }
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) atomicAdd(dW + (co * CIN + ci) * 27 + t, acc[co]);
+}
+
+template <int CIN, int COUT> int tile_bwd_weight(const float *gout, const float *in, int ntiles, int D, float *dW,
+                                                 cudaStream_t st) {
+    const size_t sm = sizeof(float) * (size_t)(COUT * WB_PLANES + CIN * (WB_PLANES + 2)) * D * D;
+    static bool attr = false;
+    if (!attr) {
+        RS_CUDA(cudaFuncSetAttribute(k_tile_bwd_weight<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024));
+        attr = true;
+    }
+    if (sm > 200 * 1024) return fail(RS_EINVAL, "tile_bwd_weight: tile too large");
+    const int threads = ((CIN * 27 + 31) / 32) * 32;
+    k_tile_bwd_weight<CIN, COUT><<<dim3((unsigned)ntiles, (unsigned)((D + WB_PLANES - 1) / WB_PLANES)), threads, sm, st>>>(
+        gout, in, ntiles, D, dW);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
 }
 
 // g = d loss / d y with loss = sum_{valid} (y - t)^2 / nvalid; returns the sum in loss[0]
@@ -324,16 +368,15 @@ int tile_backward(const float *wq, const float *x0, const uint8_t *mask, int nti
                   cudaStream_t st) {
     const int64_t n = (int64_t)ntiles * D * D * D;
     const unsigned blocks = (unsigned)((n + 127) / 128);
-    const int chunk = 2048;
-    const unsigned wblocks = (unsigned)((n + chunk - 1) / chunk);
+
     k_mask_grad<<<1024, 256, 0, st>>>(b.g3, mask, n);
-    k_tile_bwd_weight<NC, 1><<<wblocks, 256, 0, st>>>(b.g3, b.a2, ntiles, D, chunk, grad + W3_OFF);
+    RS_TRY((tile_bwd_weight<NC, 1>(b.g3, b.a2, ntiles, D, grad + W3_OFF, st)));
     k_tile_bwd_data<NC, 1><<<blocks, 128, 0, st>>>(b.g3, wq + W3_OFF, ntiles, D, b.ga2);
     k_relu_grad<<<1024, 256, 0, st>>>(b.ga2, b.z2, mask, ntiles, NC, D);
-    k_tile_bwd_weight<NC, NC><<<wblocks, 256, 0, st>>>(b.ga2, b.a1, ntiles, D, chunk, grad + W2_OFF);
+    RS_TRY((tile_bwd_weight<NC, NC>(b.ga2, b.a1, ntiles, D, grad + W2_OFF, st)));
     k_tile_bwd_data<NC, NC><<<blocks, 128, 0, st>>>(b.ga2, wq + W2_OFF, ntiles, D, b.ga1);
     k_relu_grad<<<1024, 256, 0, st>>>(b.ga1, b.z1, mask, ntiles, NC, D);
-    k_tile_bwd_weight<1, NC><<<wblocks, 256, 0, st>>>(b.ga1, x0, ntiles, D, chunk, grad + W1_OFF);
+    RS_TRY((tile_bwd_weight<1, NC>(b.ga1, x0, ntiles, D, grad + W1_OFF, st)));
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
@@ -537,7 +580,12 @@ extern "C" int rs_precond_train(rs_ham *h, const rs_grid *g, const float *R_dev,
         std::vector<uint8_t> hm((size_t)ntot);
         RS_CUDA(cudaMemcpyAsync(hm.data(), msk.p, hm.size(), cudaMemcpyDeviceToHost, st));
         RS_CUDA(cudaStreamSynchronize(st));
-        for (int64_t e = 0; e < ntot; ++e) tvalid[e / D3] += hm[e] && valid[e % D3];
+        for (int n = 0; n < c.n_tiles; ++n) {
+            const uint8_t *tm = hm.data() + (size_t)n * D3;
+            int cnt = 0;
+            for (int e = 0; e < D3; ++e) cnt += tm[e] && valid[e];
+            tvalid[n] = cnt;
+        }
     }
     TileBufs b(ws.as<float>(), B, D);
     int step = 0;
