@@ -293,6 +293,22 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
     return out
 
 
+def max_over_ranks(value, device):
+    """The largest of every rank's value (all ranks call it; the job's time
+    is its slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, bytes_per_step, steps, ms_max):
+    """Whole-job GB/s of `world` replicas that each moved bytes_per_step per
+    step, timed by the slowest replica."""
+    return world * bytes_per_step * steps / (ms_max * 1e-3) / 1e9
+
+
 def profile_sweeps(workload, n):
     import torch
     from paper_1306_2953_gb300 import api
@@ -382,9 +398,7 @@ def main():
     _lib.call("rs_ham_timing_read", H._h, ctypes.byref(pms), ctypes.byref(sms), ctypes.byref(ncalls))
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
 
     # end to end through the public API: pinned host psi in, H psi back out
     psi_pin = psi_h.pin_memory()
@@ -400,7 +414,7 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     h2d = psi.numel() * 4
 
-    value = world * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+    value = replica_throughput(world, bytes_per_step, args.steps, ms)
     peak, peak_kind = measured_peaks()
     stencil_gbs = sb.value * ncalls.value / (sms.value * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

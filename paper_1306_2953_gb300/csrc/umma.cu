@@ -13,10 +13,12 @@
 // accumulation only.
 //
 // Kernel: one CTA of 128 threads per 128 x BN output tile and K range.
-// Thread 0 drives a two-stage pipeline: TMA (cp.async.bulk.tensor, 128-byte
-// swizzle) brings the three pieces of a 128 x 64 A tile and a BN x 64 B tile
-// into shared memory, then issues 6 x 4 tcgen05.mma (M = 128, K = 16 each)
-// into a TMEM accumulator, committing to the stage's "empty" barrier.  After
+// A multi-stage pipeline (three stages for BN = 64, two for BN = 128):
+// thread 0 streams, by TMA (cp.async.bulk.tensor, 128-byte swizzle), the
+// three pieces of a 128 x 64 A tile and a BN x 64 B tile into the next free
+// stage; thread 32 waits for a full stage, issues 6 x 4 tcgen05.mma
+// (M = 128, K = 16 each) into a TMEM accumulator and commits to the stage's
+// "empty" barrier, which frees it for thread 0.  After
 // the K range the four warps read the accumulator with tcgen05.ld (warp w owns
 // TMEM lanes 32w..32w+31) and apply the epilogue.  Every wait is bounded; on
 // a timeout the kernel raises an error flag, skips the rest and still frees
@@ -36,6 +38,8 @@ namespace rs {
 
 constexpr int UM_BM = 128, UM_BK = 64, UM_NT = 128;
 constexpr int UM_KB_CTA = 32;   // K blocks per CTA of a split-K contraction (2048 points)
+// pipeline stages: three of 72 KB for 64-wide tiles, two of 96 KB for 128-wide
+__host__ __device__ constexpr int um_stages(int BN) { return BN <= 64 ? 3 : 2; }
 constexpr long long UM_SPIN = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -119,10 +123,11 @@ __global__ void __launch_bounds__(UM_NT, 1) k_umma_tn(const __grid_constant__ CU
                                                       const __grid_constant__ CUtensorMap tmB, UmmaArgs args) {
     constexpr int A_BYTES = 3 * UM_BM * UM_BK * 2, B_BYTES = 3 * BN * UM_BK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;
+    constexpr int NS = um_stages(BN);
     extern __shared__ __align__(1024) unsigned char smraw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full[2], empty[2], done;
+    __shared__ uint64_t full[NS], empty[NS], done;
     __shared__ uint32_t tmem_base;
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -131,10 +136,10 @@ __global__ void __launch_bounds__(UM_NT, 1) k_umma_tn(const __grid_constant__ CU
     const int nkb_total = (args.K + UM_BK - 1) / UM_BK;
     const int nk = max(0, min(args.kb_per_cta, nkb_total - kb0));
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&empty[0], 1);
-        mbar_init(&empty[1], 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
         mbar_init(&done, 1);
         bad = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -150,19 +155,25 @@ __global__ void __launch_bounds__(UM_NT, 1) k_umma_tn(const __grid_constant__ CU
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
 
+    // thread 0 streams the operand tiles NS stages ahead; thread 32 issues
+    // the MMAs and releases every stage when its MMAs have read it
     if (tid == 0 && nk > 0) {
-        constexpr uint32_t idesc = umma_idesc(UM_BM, BN);
-        auto issue_tma = [&](int kb, int s) {
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % NS;
+            if (kb >= NS && !mbar_wait(&empty[s], ((kb / NS) - 1) & 1)) {
+                bad = 1;
+                break;
+            }
             unsigned char *sA = base + s * STAGE, *sB = sA + A_BYTES;
             mbar_expect_tx(&full[s], STAGE);
             tma_load_3d(sA, &tmA, &full[s], (kb0 + kb) * UM_BK, m0, 0);
             tma_load_3d(sB, &tmB, &full[s], (kb0 + kb) * UM_BK, n0, 0);
-        };
-        issue_tma(0, 0);
-        if (nk > 1) issue_tma(1, 1);
+        }
+    } else if (tid == 32 && nk > 0) {
+        constexpr uint32_t idesc = umma_idesc(UM_BM, BN);
         for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb & 1;
-            if (!mbar_wait(&full[s], (kb >> 1) & 1)) {
+            const int s = kb % NS;
+            if (!mbar_wait(&full[s], (kb / NS) & 1)) {
                 bad = 1;
                 break;
             }
@@ -178,13 +189,6 @@ __global__ void __launch_bounds__(UM_NT, 1) k_umma_tn(const __grid_constant__ CU
                              (kb > 0 || pr > 0 || k > 0) ? 1u : 0u);
             }
             umma_commit(&empty[s]);
-            if (kb + 2 < nk) {
-                if (!mbar_wait(&empty[s], (kb >> 1) & 1)) {
-                    bad = 1;
-                    break;
-                }
-                issue_tma(kb + 2, s);
-            }
         }
         umma_commit(&done);
     }
@@ -336,7 +340,7 @@ int make_map(CUtensorMap *m, const void *P, int rows, int Kp, int box_rows) {
 
 template <int BN> int launch(const CUtensorMap &ta, const CUtensorMap &tb, const UmmaArgs &a, int splits, cudaStream_t st) {
     constexpr int STAGE = 3 * UM_BM * UM_BK * 2 + 3 * BN * UM_BK * 2;
-    const size_t smem = 2 * (size_t)STAGE + 1024;
+    const size_t smem = (size_t)um_stages(BN) * STAGE + 1024;
     static bool attr = false;
     if (!attr) {
         RS_CUDA(cudaFuncSetAttribute(k_umma_tn<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
