@@ -152,6 +152,7 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *b) {
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 struct Lane {
     float2 W1, W2, W3, W4;
@@ -220,11 +221,12 @@ __device__ __forceinline__ void march(float2 (&A)[9][2], const float *__restrict
             if (k != 4 && k != 5) v[k] = P[wpos(c.ly + dy, c.lx + k - 4) * SG + c.s];
         v[4] = u[dy].x;
         v[5] = u[dy].y;
-        a = fma2(c.W1, add2(make_float2(v[5], v[6]), make_float2(v[3], v[4])), a);
-        a = fma2(c.W2, add2(make_float2(v[6], v[7]), make_float2(v[2], v[3])), a);
-        a = fma2(c.W3, add2(make_float2(v[7], v[8]), make_float2(v[1], v[2])), a);
-        a = fma2(c.W4, add2(make_float2(v[8], v[9]), make_float2(v[0], v[1])), a);
-        A[R][dy] = a;
+        // two short independent chains (j = 1, 3 and j = 2, 4) instead of one
+        float2 x13 = c.W1 * add2(make_float2(v[5], v[6]), make_float2(v[3], v[4]));
+        float2 x24 = c.W2 * add2(make_float2(v[6], v[7]), make_float2(v[2], v[3]));
+        x13 = fma2(c.W3, add2(make_float2(v[7], v[8]), make_float2(v[1], v[2])), x13);
+        x24 = fma2(c.W4, add2(make_float2(v[8], v[9]), make_float2(v[0], v[1])), x24);
+        A[R][dy] = add2(a, add2(x13, x24));
     }
     // axis-1 neighbours: the window columns of the patch, both columns paired
     float2 col[10];
@@ -236,12 +238,11 @@ __device__ __forceinline__ void march(float2 (&A)[9][2], const float *__restrict
     col[5] = u[1];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
-        float2 a = A[R][dy];
-        a = fma2(c.W1, add2(col[5 + dy], col[3 + dy]), a);
-        a = fma2(c.W2, add2(col[6 + dy], col[2 + dy]), a);
-        a = fma2(c.W3, add2(col[7 + dy], col[1 + dy]), a);
-        a = fma2(c.W4, add2(col[8 + dy], col[0 + dy]), a);
-        A[R][dy] = a;
+        float2 y13 = c.W1 * add2(col[5 + dy], col[3 + dy]);
+        float2 y24 = c.W2 * add2(col[6 + dy], col[2 + dy]);
+        y13 = fma2(c.W3, add2(col[7 + dy], col[1 + dy]), y13);
+        y24 = fma2(c.W4, add2(col[8 + dy], col[0 + dy]), y24);
+        A[R][dy] = add2(A[R][dy], add2(y13, y24));
     }
 }
 
