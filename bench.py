@@ -278,10 +278,19 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
                 if stall >= 3:
                     S.set_precond(_lib.RS_PRECOND_FILTER)
                     fallback_at = sweeps
-            if dt == torch.float32 and np.all(r <= 1e-4):
-                # FP32 mode: close with an FP64 Rayleigh-Ritz of the subspace
-                eps = S.rayleigh_ritz_f64()
-            err = float(np.abs(eps.cpu().numpy()[:judged] - ref).max())
+            if dt == torch.float32:
+                # FP32 mode: the eigenvalues come from an FP64 Rayleigh-Ritz of
+                # the subspace, taken every 10 sweeps once the residuals are
+                # small and at every sweep below 1e-4 (its cost is timed)
+                rmax = float(r.max())
+                if rmax <= 1e-4 or (rmax <= 3e-3 and sweeps % 10 == 0):
+                    eps = S.rayleigh_ritz_f64()
+                else:
+                    eps = None
+            if eps is None:
+                err = float("inf")
+            else:
+                err = float(np.abs(eps.cpu().numpy()[:judged] - ref).max())
             el = time.perf_counter() - t0
             if err <= tol or el > max_seconds:
                 break
@@ -332,7 +341,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=wl.MOL100.name, choices=[wl.MOL100.name, wl.MOL300.name])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--eigensolve", default="mol20_h0.35",
+    ap.add_argument("--eigensolve", default="mol20_h0.35,mol100_h0.3",
                     help="workload(s) for the time-to-1e-6 Ha eigensolve, comma separated, or 'none'")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling aid: run this many mixed-precision eigensolver sweeps on --workload, "
