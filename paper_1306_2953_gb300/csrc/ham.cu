@@ -43,7 +43,7 @@
 
 // Height (planes) of the z-slabs of that kernel's work units.
 #ifndef RS_RING_SLAB
-#define RS_RING_SLAB 64
+#define RS_RING_SLAB 48
 #endif
 
 #ifndef RS_STENCIL_MINB_F32

@@ -2,95 +2,106 @@
 // 25-point star kinetic stencil (Sec. V.A), the local potential (Sec. V.B)
 // and the nonlocal gather of Eq. (4), one persistent CTA per SM.
 //
-// Work.  The point map is cut into 8 x 8 columns (map axes 1 and 2) and each
-// column into z-slabs along the march axis 0; a unit is (column, slab).  The
-// host deals the units of every slab to the CTAs, largest first onto the
-// least loaded CTA, and each CTA takes its units slab by slab: at any moment
-// the CTAs march neighbouring columns of the same slab, so the halo rows
-// they share are re-read from L2 rather than HBM.  blockIdx.y is the state
-// group (32 states) of the block.
+// Work.  The point map is cut into 16 x 8 tiles (16 along map axis 2, 8
+// along axis 1) and each tile column into z-slabs along the march axis 0; a
+// unit is (column, slab).  The host deals the units of every slab to the
+// CTAs, largest first onto the least loaded CTA, and each CTA takes its
+// units slab by slab: at any moment the CTAs march neighbouring columns of
+// the same slab, so the halo rows they share are re-read from L2 rather than
+// HBM.  blockIdx.y is the state group (32 states) of the block.
 //
-// Ring.  A CTA keeps RING planes of its column in shared memory.  A slot
-// holds one plane of the 16 x 16 window (the 8 x 8 tile and its 4-point
-// star halo in both in-plane axes), 128 bytes (32 FP32 states) per lattice
-// position, plus the plane's record: per tile point its potential, point
-// index and nonlocal entries (projector values and atom).  Every thread
-// copies its share of plane it + AHEAD while plane it is computed: three
-// 16-byte pieces of point rows (eight threads per row; absent points are
+// Ring.  A CTA keeps RING planes (4, or 3 when 4 do not fit in shared
+// memory) of its column in shared memory.  A slot holds the 320 window
+// positions one plane of the star reads (the tile, 4 rows above and below
+// it, 4 columns left and right of it; the window's corners are not stored),
+// 128 bytes (32 FP32 states) per position, plus the plane's record: the
+// potential and the point index of every tile point and, per 4 x 4 patch,
+// the projector values of each atom whose sphere meets the patch (zero at
+// the patch points outside the sphere).  Every thread copies its share of
+// plane it + 2 while plane it is computed: one 16-byte piece of ten point
+// rows (a warp copies a 4-point brick row per instruction; absent points are
 // zero-filled) and part of the record, all counted on the slot's "full"
 // mbarrier through cp.async.mbarrier.arrive.  A slot is refilled once every
 // warp has released it ("empty" mbarrier).  Points are stored brick by brick
 // (Sec. V.A), so one 32-bit descriptor (first point, presence mask) gives
-// the four points of a brick row.
+// the four points of a brick row; the descriptors are loaded three planes
+// ahead of their copy.  The projection coefficients of the atoms a CTA's
+// records name are staged in shared memory once per launch (the records
+// carry the CTA-local atom numbers).
 //
-// Compute.  Warp w owns the 2 x 2 patch of tile points at (2 (w / 4),
-// 2 (w % 4)); lane s is state s.  Pairs of points along axis 2 share packed
-// FP32x2 instructions.  The march accumulates forward: the values of plane z
-// add w_|j| psi(z) to the outputs of planes z + j (j = -4..4, nine
-// accumulators per point in registers, addressed by z mod 9 through
-// unrolling), and the in-plane star, the potential and the nonlocal sum to
-// plane z's own output, so a slot is read in one step only and output
-// z - 4 is complete, and written once, at step z.  The four planes on either
-// side of a slab contribute only their z-terms (tile rows only, no record).
+// Compute.  Warp w owns the 4 x 4 patch of tile points at rows 4 (w / 4),
+// columns 4 (w % 4); half-warp h takes the patch's rows 2h and 2h + 1 and
+// lane l of the half the states 2l and 2l + 1, so every value is a pair of
+// states and every multiply-add a packed FP32x2 instruction.  The march
+// accumulates forward: the values of plane z add w_|j| psi(z) to the outputs
+// of planes z + j (j = -4..4), and the in-plane star, the potential and the
+// nonlocal sum to plane z's own output, so a slot is read in one step only.
+// Eight accumulators per point hold the outputs z - 4 .. z + 3 (slot z mod 8,
+// addressed through unrolling): at step z output z - 4 is complete and
+// written, and its slot takes output z + 4.  The four planes on either side
+// of a slab contribute only their z-terms (tile rows only, no record).
 //
 // Every mbarrier wait is bounded; on a timeout the kernel sets its status
 // word and leaves the march.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "device.h"
 #include "stencil_ring.h"
 
-#ifndef RS_RING_SLOTS
-#define RS_RING_SLOTS 4
-#endif
-#ifndef RS_RING_AHEAD
-#define RS_RING_AHEAD (RS_RING_SLOTS - 2)
-#endif
-
 namespace rs {
 
 namespace {
 
-constexpr int TT = 8;                      // tile edge (lattice points)
-constexpr int WIN = TT + 8;                // window edge
+constexpr int TX = 16;                     // tile extent along map axis 2
+constexpr int TY = 8;                      // tile extent along map axis 1
 constexpr int SG = 32;                     // states per CTA
 constexpr int ROWB = SG * 4;               // bytes per point row
-constexpr int SLOT_PSI = WIN * WIN * ROWB;
-constexpr int NG = 48;                     // brick rows of four positions per window plane
-constexpr int NG_CORE = 16;                // brick rows of the tile itself
-constexpr int NW = 16;                     // warps: one 2 x 2 patch each
+constexpr int NSLOT = 320;                 // stored window positions
+constexpr int SLOT_PSI = NSLOT * ROWB;
+constexpr int NG = 80;                     // brick rows (four positions) per window plane
+constexpr int NW = 8;                      // warps: one 4 x 4 patch each
 constexpr int NT = NW * 32;
-constexpr int RING = RS_RING_SLOTS;
-constexpr int AHEAD = RS_RING_AHEAD;       // planes in flight ahead of the one computed
-static_assert(AHEAD >= 1 && AHEAD < RING, "copy distance must leave a slot to compute on");
-constexpr int NPOS = TT * TT;
-constexpr int REC_HDR = 16;                // record header: entries count
-constexpr int META_BYTES = NPOS * 16;
-constexpr int MAX_REC = 40 * 1024;         // record slot budget (bytes)
+constexpr int CPW = NG / NW;               // brick rows copied per warp and plane
+
+// march cost of one atom block of a patch, in planes (host load balance)
+constexpr double NL_COST = 0.13;
+constexpr int AHEAD = 2;                   // planes in flight ahead of the one computed
+constexpr int MAX_RING = 4;                // slots per CTA (4, or 3 when 4 do not fit)
+constexpr int NPOS = TX * TY;
+// record: [patch headers {blocks, byte offset}] [potential, tile row-major]
+// [point index, tile row-major] [blocks: {atom} + projector values [16][4]]
+constexpr int REC_V = 128;
+constexpr int REC_IDX = REC_V + NPOS * 4;
+constexpr int REC_BLK = REC_IDX + NPOS * 4;
+constexpr int BLK = 16 + 16 * 16;
+constexpr int MAX_REC = 48 * 1024;         // record slot budget (bytes)
 constexpr size_t MAX_SMEM = 227 * 1024;    // dynamic shared memory per CTA
 constexpr int MAX_SLAB = 128;              // planes per z-slab of a unit (at most)
 constexpr int MAX_UNITS = 64;              // units per CTA (shared-memory table)
-constexpr int SUSPEND_NS = 20000;           // suspension limit of one barrier test
+constexpr int SUSPEND_NS = 20000;          // suspension limit of one barrier test
 constexpr int SPIN = 100000;               // barrier tests before a wait gives up
 
-// Window position (row yw, first column xw) of brick row g: 0..15 the tile,
-// 16..31 the axis-2 halo beside it, 32..47 the axis-1 halo above and below.
-__host__ __device__ __forceinline__ void group_pos(int g, int &yw, int &xw) {
-    if (g < 16) {
-        yw = 4 + (g >> 1);
-        xw = 4 + 4 * (g & 1);
-    } else if (g < 32) {
-        const int h = g - 16;
-        yw = 4 + (h >> 1);
-        xw = (h & 1) ? 12 : 0;
+// Window layout in a slot.  Window rows wy = 0..15 (tile rows at 4..11),
+// columns wx = 0..23 (tile columns at 4..19).  Columns 4..19 of every row
+// are positions wy * 16 + wx - 4 (0..255); columns 0..3 and 20..23 of the
+// tile rows are positions 256 + (wy - 4) * 8 + (0..3 | 4..7).  Brick row g
+// covers positions 4 g .. 4 g + 3: g < 64 row g / 4 of the core columns,
+// g >= 64 the side halo.
+__host__ __device__ __forceinline__ void group_pos(int g, int &wy, int &wx) {
+    if (g < 64) {
+        wy = g >> 2;
+        wx = 4 + 4 * (g & 3);
     } else {
-        const int h = g - 32, r = h >> 1;
-        yw = r < 4 ? r : r + 8;
-        xw = 4 + 4 * (h & 1);
+        const int h = g - 64;
+        wy = 4 + (h >> 1);
+        wx = (h & 1) ? 20 : 0;
     }
 }
+// brick rows of the tile itself (window rows 4..11, core columns)
+constexpr int G_TILE0 = 16, G_TILE1 = 48;
 
 // A unit as the kernel walks it: planes zm0..zm1 (the slab's output planes
 // zo0..zo1-1 and up to four on either side), record / descriptor index of
@@ -101,8 +112,9 @@ struct UnitDev {
 
 struct Args {
     const UnitDev *units;   // per CTA, concatenated
-    const int2 *cta;        // [CTA]: first unit, unit count
-    const uint32_t *desc;   // [plane][48]: first point | presence mask << 28
+    const int4 *cta;        // [CTA]: first unit, unit count, first atom, atom count
+    const int *cta_atoms;   // per CTA, concatenated: the atoms its records name (in local order)
+    const uint32_t *desc;   // [plane][80]: first point | presence mask << 28
     const uint2 *recs;      // [plane]: {offset / 16, bytes}
     const unsigned char *rec;
     const float *psi;       // [npts][ldp]
@@ -110,7 +122,7 @@ struct Args {
     const float *cproj;     // [atom][nb][4]
     float *hpsi;
     int64_t ldh;
-    int nb, n_atoms, rec_slot;
+    int nb, rec_slot, cs_atoms;   // cs_atoms: the largest atom count of a CTA
     float w[5];
     int *status;
 };
@@ -151,140 +163,153 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *b) {
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Per-thread constants.  Offsets are in float2 units (one state pair) from
+// a slot's start.
 struct Lane {
     float2 W1, W2, W3, W4;
     float w0;
-    int lx, ly, s;
+    int cb;        // centre of patch row 0, column 0 (window row 4 + ty0)
+    int lb0, lb1;  // first of the four axis-2 neighbours left of rows 0 / 1
+    int rb0, rb1;  // first of the four right of rows 0 / 1
+    int to;        // tile index of patch row 0, column 0 (record tables)
+    int w, h, sl;
 };
 
-// Window position index of tile point (y, x) shifted by (dy, dx).
-__device__ __forceinline__ int wpos(int y, int x) { return (y + 4) * WIN + x + 4; }
+// position p -> float2 offset of the lane's state pair: p * PS + lane
+constexpr int PS = ROWB / 8;
 
-// One march step over plane z (R = z mod 9).  A[k][dy] holds the outputs of
-// the patch row dy (x: point dx = 0, y: dx = 1) for plane z' = k mod 9.
-template <int R>
-__device__ __forceinline__ void march(float2 (&A)[9][2], const float *__restrict__ P, const unsigned char *rs,
-                                      int *rowring, bool full, const float *__restrict__ cpl, int nb4, const Lane &c) {
-    float2 u[2];
+// The plane's own terms of its output (everything but the z-terms): the
+// centre of the star with the potential, the in-plane star and the
+// nonlocal gather, for the patch rows r and columns x of this thread.
+__device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc)[2][4], const float2 *__restrict__ P,
+                                            const unsigned char *__restrict__ rs, const float2 *__restrict__ cs,
+                                            const Lane &c) {
+    const float4 *V4 = reinterpret_cast<const float4 *>(rs + REC_V) + (c.to >> 2);
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-        u[dy] = make_float2(P[wpos(c.ly + dy, c.lx) * SG + c.s], P[wpos(c.ly + dy, c.lx + 1) * SG + c.s]);
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-        const float2 v = u[dy];
-        A[(R + 1) % 9][dy] = fma2(c.W1, v, A[(R + 1) % 9][dy]);
-        A[(R + 8) % 9][dy] = fma2(c.W1, v, A[(R + 8) % 9][dy]);
-        A[(R + 2) % 9][dy] = fma2(c.W2, v, A[(R + 2) % 9][dy]);
-        A[(R + 7) % 9][dy] = fma2(c.W2, v, A[(R + 7) % 9][dy]);
-        A[(R + 3) % 9][dy] = fma2(c.W3, v, A[(R + 3) % 9][dy]);
-        A[(R + 6) % 9][dy] = fma2(c.W3, v, A[(R + 6) % 9][dy]);
-        A[(R + 4) % 9][dy] = fma2(c.W4, v, A[(R + 4) % 9][dy]);
-        A[(R + 5) % 9][dy] = fma2(c.W4, v, A[(R + 5) % 9][dy]);
+    for (int r = 0; r < 2; ++r) {
+        const float4 v = V4[r * (TX / 4)];
+        T[r][0] = f2(c.w0 + v.x) * cc[r][0];
+        T[r][1] = f2(c.w0 + v.y) * cc[r][1];
+        T[r][2] = f2(c.w0 + v.z) * cc[r][2];
+        T[r][3] = f2(c.w0 + v.w) * cc[r][3];
     }
-    if (!full) return;
-    const int E = *reinterpret_cast<const int *>(rs);
-    const int4 *meta = reinterpret_cast<const int4 *>(rs + REC_HDR);
-    const float4 *gam = reinterpret_cast<const float4 *>(rs + REC_HDR + META_BYTES);
-    const int *atom = reinterpret_cast<const int *>(rs + REC_HDR + META_BYTES + 16 * E);
+    // axis-2 neighbours: the four left and right of each patch row
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-        const int pos = (c.ly + dy) * TT + c.lx;
-        const int4 m0 = meta[pos], m1 = meta[pos + 1];
-        if (c.s == 0) {
-            rowring[R * NPOS + pos] = m0.y;
-            rowring[R * NPOS + pos + 1] = m1.y;
-        }
-        // centre of the star and the potential
-        float2 a = fma2(make_float2(c.w0 + __int_as_float(m0.x), c.w0 + __int_as_float(m1.x)), u[dy], A[R][dy]);
-        // nonlocal gather over the atoms whose spheres cover each point: the
-        // two points' entry lists are walked side by side (independent load
-        // and multiply chains), each projection a two-level sum
-        const int n0 = m0.w, n1 = m1.w, nmax = max(n0, n1);
-        for (int k = 0; k < nmax; ++k) {
-            const int e0 = m0.z + min(k, n0 - 1), e1 = m1.z + min(k, n1 - 1);
-            const float4 g0 = gam[max(e0, 0)], g1 = gam[max(e1, 0)];
-            const int a0 = atom[max(e0, 0)], a1 = atom[max(e1, 0)];
-            const float4 c0 = *reinterpret_cast<const float4 *>(cpl + a0 * nb4);
-            const float4 c1 = *reinterpret_cast<const float4 *>(cpl + a1 * nb4);
-            const float p0 = (g0.x * c0.x + g0.y * c0.y) + (g0.z * c0.z + g0.w * c0.w);
-            const float p1 = (g1.x * c1.x + g1.y * c1.y) + (g1.z * c1.z + g1.w * c1.w);
-            if (k < n0) a.x += p0;
-            if (k < n1) a.y += p1;
-        }
-        // axis-2 neighbours: the window row of the patch row
-        float v[10];
+    for (int r = 0; r < 2; ++r) {
+        float2 v[12];
+        const int lb = r ? c.lb1 : c.lb0, rb = r ? c.rb1 : c.rb0;
 #pragma unroll
-        for (int k = 0; k < 10; ++k)
-            if (k != 4 && k != 5) v[k] = P[wpos(c.ly + dy, c.lx + k - 4) * SG + c.s];
-        v[4] = u[dy].x;
-        v[5] = u[dy].y;
-        // two short independent chains (j = 1, 3 and j = 2, 4) instead of one
-        float2 x13 = c.W1 * add2(make_float2(v[5], v[6]), make_float2(v[3], v[4]));
-        float2 x24 = c.W2 * add2(make_float2(v[6], v[7]), make_float2(v[2], v[3]));
-        x13 = fma2(c.W3, add2(make_float2(v[7], v[8]), make_float2(v[1], v[2])), x13);
-        x24 = fma2(c.W4, add2(make_float2(v[8], v[9]), make_float2(v[0], v[1])), x24);
-        A[R][dy] = add2(a, add2(x13, x24));
+        for (int k = 0; k < 4; ++k) {
+            v[k] = P[lb + k * PS];
+            v[8 + k] = P[rb + k * PS];
+            v[4 + k] = cc[r][k];
+        }
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            const float2 W = j == 1 ? c.W1 : j == 2 ? c.W2 : j == 3 ? c.W3 : c.W4;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) T[r][x] = fma2(W, add2(v[x + 4 + j], v[x + 4 - j]), T[r][x]);
+        }
     }
-    // axis-1 neighbours: the window columns of the patch, both columns paired
-    float2 col[10];
+    // axis-1 neighbours: window rows ty0 .. ty0 + 9 of each patch column
 #pragma unroll
-    for (int k = 0; k < 10; ++k)
-        if (k != 4 && k != 5)
-            col[k] = make_float2(P[wpos(c.ly + k - 4, c.lx) * SG + c.s], P[wpos(c.ly + k - 4, c.lx + 1) * SG + c.s]);
-    col[4] = u[0];
-    col[5] = u[1];
+    for (int x = 0; x < 4; ++x) {
+        float2 y[10];
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-        float2 y13 = c.W1 * add2(col[5 + dy], col[3 + dy]);
-        float2 y24 = c.W2 * add2(col[6 + dy], col[2 + dy]);
-        y13 = fma2(c.W3, add2(col[7 + dy], col[1 + dy]), y13);
-        y24 = fma2(c.W4, add2(col[8 + dy], col[0 + dy]), y24);
-        A[R][dy] = add2(A[R][dy], add2(y13, y24));
+        for (int m = 0; m < 10; ++m) {
+            if (m == 4 || m == 5) y[m] = cc[m - 4][x];
+            else y[m] = P[c.cb + ((m - 4) * 16 + x) * PS];
+        }
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            const float2 W = j == 1 ? c.W1 : j == 2 ? c.W2 : j == 3 ? c.W3 : c.W4;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) T[r][x] = fma2(W, add2(y[r + 4 + j], y[r + 4 - j]), T[r][x]);
+        }
+    }
+    // nonlocal gather: per atom meeting the patch, the projection
+    // coefficients of the lane's two states (staged in shared memory)
+    // against the patch's projector values
+    const int2 hd = reinterpret_cast<const int2 *>(rs)[c.w];
+    const unsigned char *blk = rs + hd.y;
+    for (int k = 0; k < hd.x; ++k, blk += BLK) {
+        const float2 *cq = cs + *reinterpret_cast<const int *>(blk) * (4 * SG / 2) + c.sl;
+        const float2 c0 = cq[0], c1 = cq[SG / 2], c2 = cq[SG], c3 = cq[3 * SG / 2];
+        const float4 *g = reinterpret_cast<const float4 *>(blk + 16) + 8 * c.h;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const float4 gv = g[r * 4 + x];
+                float2 a = T[r][x];
+                a = fma2(f2(gv.x), c0, a);
+                a = fma2(f2(gv.y), c1, a);
+                a = fma2(f2(gv.z), c2, a);
+                a = fma2(f2(gv.w), c3, a);
+                T[r][x] = a;
+            }
     }
 }
 
-// Writes the finished output of plane o (R = o mod 9) when `store`, and
-// clears its accumulators for plane o + 9.
+// Writes the finished output of the plane in accumulator slot R.
 template <int R>
-__device__ __forceinline__ void emit(float2 (&A)[9][2], const int *rowring, float *hp, int64_t ldh, bool store,
+__device__ __forceinline__ void emit(const float2 (&A)[8][2][4], const int *rowring, float *hp, int64_t ldh,
                                      const Lane &c) {
+    const int4 *ring4 = reinterpret_cast<const int4 *>(rowring + R * NPOS) + (c.to >> 2);
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-        if (store) {
-            const int pos = (c.ly + dy) * TT + c.lx;
-            const int r0 = rowring[R * NPOS + pos], r1 = rowring[R * NPOS + pos + 1];
-            if (r0 >= 0) hp[(int64_t)r0 * ldh] = A[R][dy].x;
-            if (r1 >= 0) hp[(int64_t)r1 * ldh] = A[R][dy].y;
-        }
-        A[R][dy] = make_float2(0.f, 0.f);
+    for (int r = 0; r < 2; ++r) {
+        const int4 id = ring4[r * (TX / 4)];
+        if (id.x >= 0) *reinterpret_cast<float2 *>(hp + (int64_t)id.x * ldh) = A[R][r][0];
+        if (id.y >= 0) *reinterpret_cast<float2 *>(hp + (int64_t)id.y * ldh) = A[R][r][1];
+        if (id.z >= 0) *reinterpret_cast<float2 *>(hp + (int64_t)id.z * ldh) = A[R][r][2];
+        if (id.w >= 0) *reinterpret_cast<float2 *>(hp + (int64_t)id.w * ldh) = A[R][r][3];
     }
 }
 
+// The z-terms of plane z (R = z mod 8): slot k holds output z' = k mod 8 for
+// z' = z - 4 .. z + 3 before the step.  Plane z is the last contribution to
+// output z - 4, which is then written (when `store`), and its slot takes
+// output z + 4, whose first contribution plane z is.
 template <int R>
-__device__ __forceinline__ void step(float2 (&A)[9][2], const float *P, const unsigned char *rs, int *rowring,
-                                     uint64_t *ebar, bool full, const float *cpl, int nb4, float *hp, int64_t ldh,
-                                     bool store, const Lane &c) {
-    march<R>(A, P, rs, rowring, full, cpl, nb4, c);
-    __syncwarp();
-    if (c.s == 0) bar_arrive(ebar);   // the slot is no longer read by this warp
-    emit<(R + 5) % 9>(A, rowring, hp, ldh, store, c);
+__device__ __forceinline__ void zterms(float2 (&A)[8][2][4], const float2 (&cc)[2][4], const float2 (&T)[2][4],
+                                       bool full, bool store, const int *rowring, float *hp, int64_t ldh,
+                                       const Lane &c) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const float2 v = cc[r][x];
+            A[(R + 4) % 8][r][x] = fma2(c.W4, v, A[(R + 4) % 8][r][x]);
+            A[(R + 1) % 8][r][x] = fma2(c.W1, v, A[(R + 1) % 8][r][x]);
+            A[(R + 7) % 8][r][x] = fma2(c.W1, v, A[(R + 7) % 8][r][x]);
+            A[(R + 2) % 8][r][x] = fma2(c.W2, v, A[(R + 2) % 8][r][x]);
+            A[(R + 6) % 8][r][x] = fma2(c.W2, v, A[(R + 6) % 8][r][x]);
+            A[(R + 3) % 8][r][x] = fma2(c.W3, v, A[(R + 3) % 8][r][x]);
+            A[(R + 5) % 8][r][x] = fma2(c.W3, v, A[(R + 5) % 8][r][x]);
+            if (full) A[R][r][x] = add2(A[R][r][x], T[r][x]);
+        }
+    if (store) emit<(R + 4) % 8>(A, rowring, hp, ldh, c);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) A[(R + 4) % 8][r][x] = c.W4 * cc[r][x];
 }
 
-__device__ __forceinline__ void emit_any(int r, float2 (&A)[9][2], const int *rowring, float *hp, int64_t ldh,
-                                         const Lane &c) {
+__device__ __forceinline__ void emit_any(int r, const float2 (&A)[8][2][4], const int *rowring, float *hp,
+                                         int64_t ldh, const Lane &c) {
     switch (r) {
-        case 0: emit<0>(A, rowring, hp, ldh, true, c); break;
-        case 1: emit<1>(A, rowring, hp, ldh, true, c); break;
-        case 2: emit<2>(A, rowring, hp, ldh, true, c); break;
-        case 3: emit<3>(A, rowring, hp, ldh, true, c); break;
-        case 4: emit<4>(A, rowring, hp, ldh, true, c); break;
-        case 5: emit<5>(A, rowring, hp, ldh, true, c); break;
-        case 6: emit<6>(A, rowring, hp, ldh, true, c); break;
-        case 7: emit<7>(A, rowring, hp, ldh, true, c); break;
-        default: emit<8>(A, rowring, hp, ldh, true, c); break;
+        case 0: emit<0>(A, rowring, hp, ldh, c); break;
+        case 1: emit<1>(A, rowring, hp, ldh, c); break;
+        case 2: emit<2>(A, rowring, hp, ldh, c); break;
+        case 3: emit<3>(A, rowring, hp, ldh, c); break;
+        case 4: emit<4>(A, rowring, hp, ldh, c); break;
+        case 5: emit<5>(A, rowring, hp, ldh, c); break;
+        case 6: emit<6>(A, rowring, hp, ldh, c); break;
+        default: emit<7>(A, rowring, hp, ldh, c); break;
     }
 }
 
@@ -294,23 +319,20 @@ struct Cursor {
     UnitDev U;
 };
 
-// CPS: the projection coefficients of the CTA's state group are staged in
-// shared memory (when they fit), so the nonlocal gather reads no global memory.
-template <bool CPS>
+template <int RING>
 __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    unsigned char *psi_ring = base;                                         // [RING] windows
-    unsigned char *rec_ring = base + (size_t)RING * SLOT_PSI;              // [RING] records
-    UnitDev *ut = reinterpret_cast<UnitDev *>(rec_ring + (size_t)RING * a.rec_slot);   // [MAX_UNITS]
-    int *rowring = reinterpret_cast<int *>(ut + MAX_UNITS);                 // [9][NPOS] output rows
-    int *wrow = rowring + 9 * NPOS;                                         // [NG * 4] window position of each row
-    float *cps = reinterpret_cast<float *>(wrow + NG * 4);                  // [atom][32 states][4] when CPS
+    static_assert(AHEAD < RING, "copy distance must leave a slot to compute on");
+    extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint64_t fullb[RING], emptyb[RING];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int grp = blockIdx.y;
-    const int2 mine = a.cta[blockIdx.x];
+    const int4 mine = a.cta[blockIdx.x];   // first unit, units, first atom, atoms
     const int nu = min(mine.y, MAX_UNITS);
+    unsigned char *psi_ring = smraw;                                       // [RING] windows
+    unsigned char *rec_ring = smraw + (size_t)RING * SLOT_PSI;            // [RING] records
+    float *cs = reinterpret_cast<float *>(rec_ring + (size_t)RING * a.rec_slot);   // [atom][4][32]
+    UnitDev *ut = reinterpret_cast<UnitDev *>(cs + (size_t)a.cs_atoms * 4 * SG);   // [MAX_UNITS]
+    int *rowring = reinterpret_cast<int *>(ut + MAX_UNITS);               // [8][NPOS] output rows
     if (tid == 0) {
         for (int i = 0; i < RING; ++i) {
             bar_init(&fullb[i], NT);    // every thread's copy completions
@@ -319,73 +341,28 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     for (int k = tid; k < nu; k += NT) ut[k] = a.units[mine.x + k];
-    for (int r = tid; r < NG * 4; r += NT) {
-        int yw, xw;
-        group_pos(r >> 2, yw, xw);
-        wrow[r] = yw * WIN + xw + (r & 3);
-    }
-    if (CPS) {
-        const float4 *src = reinterpret_cast<const float4 *>(a.cproj);
-        float4 *dst = reinterpret_cast<float4 *>(cps);
-        for (int e = tid; e < a.n_atoms * SG; e += NT) {
-            const int at = e / SG, st = e - at * SG;
-            dst[e] = __ldg(src + (int64_t)at * a.nb + grp * SG + st);
-        }
+    // projection coefficients of the CTA's atoms, [local atom][projector][state]
+    for (int e = tid; e < mine.w * 4 * SG; e += NT) {
+        const int la = e >> 7, q = (e >> 5) & 3, st = e & 31;
+        const int at = __ldg(a.cta_atoms + mine.z + la);
+        cs[e] = __ldg(a.cproj + ((int64_t)at * a.nb + grp * SG + st) * 4 + q);
     }
     __syncthreads();
     if (nu == 0) return;
 
-    // ---- copies: plane of cursor q into slot j % RING.  The plane's
-    // descriptors (the three window rows this thread copies) and record
-    // address are loaded one plane ahead.
+    // ---- copies: plane qi into slot j % RING.  Lane l of warp w copies
+    // bytes 16 (l % 8) .. of position l / 8 of brick rows w + 8 k.  The
+    // descriptors of the next three planes to copy are held by lane groups
+    // 0..9, 10..19, 20..29 (plane j in group j mod 3, brick row w + 8 (lane
+    // mod 10)), their record addresses by lanes 0, 10, 20; a group is
+    // reloaded, for plane j + 3 (cursor qd), as soon as plane j is issued.
     bool ok = true;
-    const float *src0 = a.psi + grp * SG + 4 * (tid & 7);
-    // this thread copies bytes 16 (tid % 8) .. of window rows tid / 8 + 64 k:
-    // their slot offsets and brick-row bit are fixed
-    int doff[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) doff[k] = wrow[(tid >> 3) + (NT / 8) * k] * ROWB + 16 * (tid & 7);
-    const uint32_t rbit = 1u << ((tid >> 3) & 3);
-    struct Pre {
-        uint32_t d[3];
-        uint2 rc;
-        bool full;
-    };
-    auto prefetch = [&](const Cursor &q, Pre &f) {
-        const UnitDev &U = q.U;
-        f.full = q.z >= U.zo0 && q.z < U.zo1;
-        const int64_t pt = (int64_t)U.pz + q.z;
-        const int nrow = f.full ? NG * 4 : NG_CORE * 4;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int r = (tid >> 3) + (NT / 8) * k;
-            f.d[k] = r < nrow ? __ldg(a.desc + pt * NG + (r >> 2)) : 0u;
-        }
-        f.rc = f.full ? __ldg(a.recs + pt) : make_uint2(0u, 0u);
-    };
-    auto issue = [&](int j, const Pre &f) {
-        const int slot = j % RING;
-        if (!__all_sync(0xffffffffu, j < RING || bar_wait(&emptyb[slot], ((j / RING) - 1) & 1))) {
-            ok = false;
-            return;
-        }
-        unsigned char *dst = psi_ring + (size_t)slot * SLOT_PSI;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (k > 0 && !f.full) break;   // edge planes: the tile rows only (r < 64)
-            const uint32_t d = f.d[k];
-            const uint32_t mask = d >> 28;
-            const bool has = (mask & rbit) != 0;
-            const int pnt = (int)(d & 0x0fffffffu) + __popc(mask & (rbit - 1u));
-            cp_async16(dst + doff[k], has ? src0 + (int64_t)pnt * a.ldp : src0, has);
-        }
-        if (f.full) {
-            const unsigned char *rsrc = a.rec + (size_t)f.rc.x * 16;
-            unsigned char *rdst = rec_ring + (size_t)slot * a.rec_slot;
-            for (int o = tid * 16; o < (int)f.rc.y; o += NT * 16) cp_async16(rdst + o, rsrc + o, true);
-        }
-        cp_async_arrive(&fullb[slot]);
-    };
+    const float *src0 = a.psi + grp * SG + 4 * (lane & 7);
+    const int doff = (4 * warp + (lane >> 3)) * ROWB + 16 * (lane & 7);   // + k * 32 * ROWB
+    const uint32_t rbit = 1u << (lane >> 3);
+    const int lgrp = lane < 30 ? lane / 10 : -1, lsub = lane % 10;
+    uint32_t dq = 0u;
+    uint2 rq = make_uint2(0u, 0u);
     auto advance = [&](Cursor &q) {
         if (++q.z > q.U.zm1) {
             ++q.k;
@@ -395,6 +372,49 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
             }
         }
     };
+    auto load_desc = [&](const Cursor &q, int g) {
+        if (q.k < nu && lgrp == g) {
+            const int64_t pt = (int64_t)q.U.pz + q.z;
+            dq = __ldg(a.desc + pt * NG + warp + NW * lsub);
+            if (lsub == 0) rq = (q.z >= q.U.zo0 && q.z < q.U.zo1) ? __ldg(a.recs + pt) : make_uint2(0u, 0u);
+        }
+    };
+    Cursor qi{0, ut[0].zm0, ut[0]}, qc = qi, qd = qi;
+    for (int g = 0; g < 3; ++g) {
+        load_desc(qd, g);
+        if (qd.k < nu) advance(qd);
+    }
+    int j = 0;   // planes issued
+    auto issue = [&]() {
+        const int slot = j % RING, g = j % 3;
+        if (!__all_sync(0xffffffffu, j < RING || bar_wait(&emptyb[slot], ((j / RING) - 1) & 1))) {
+            ok = false;
+            return;
+        }
+        const bool pfull = qi.z >= qi.U.zo0 && qi.z < qi.U.zo1;
+        unsigned char *dst = psi_ring + (size_t)slot * SLOT_PSI + doff;
+#pragma unroll
+        for (int k = 0; k < CPW; ++k) {
+            // edge planes: the tile's own brick rows only (16 .. 47)
+            if (!pfull && (k < G_TILE0 / NW || k >= G_TILE1 / NW)) continue;
+            const uint32_t d = __shfl_sync(0xffffffffu, dq, 10 * g + k);
+            const uint32_t mask = d >> 28;
+            const bool has = (mask & rbit) != 0;
+            const int pnt = (int)(d & 0x0fffffffu) + __popc(mask & (rbit - 1u));
+            cp_async16(dst + k * (NW * 4 * ROWB), has ? src0 + (int64_t)pnt * a.ldp : src0, has);
+        }
+        if (pfull) {
+            const uint32_t rx = __shfl_sync(0xffffffffu, rq.x, 10 * g), ry = __shfl_sync(0xffffffffu, rq.y, 10 * g);
+            const unsigned char *rsrc = a.rec + (size_t)rx * 16;
+            unsigned char *rdst = rec_ring + (size_t)slot * a.rec_slot;
+            for (int o = tid * 16; o < (int)ry; o += NT * 16) cp_async16(rdst + o, rsrc + o, true);
+        }
+        cp_async_arrive(&fullb[slot]);
+        ++j;
+        advance(qi);
+        load_desc(qd, g);
+        if (qd.k < nu) advance(qd);
+    };
 
     Lane c;
     c.w0 = a.w[0];
@@ -402,31 +422,29 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
     c.W2 = f2(a.w[2]);
     c.W3 = f2(a.w[3]);
     c.W4 = f2(a.w[4]);
-    c.s = lane;
-    c.lx = 2 * (warp & 3);
-    c.ly = 2 * (warp >> 2);
-    const int nb4 = CPS ? SG * 4 : a.nb * 4;
-    const float *cpl = CPS ? cps + lane * 4 : a.cproj + (int64_t)(grp * SG + lane) * 4;
-    float *hp = a.hpsi + grp * SG + lane;
-    float2 A[9][2];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) A[k][0] = A[k][1] = make_float2(0.f, 0.f);
-
-    Cursor qi{0, ut[0].zm0, ut[0]}, qc{0, ut[0].zm0, ut[0]};
-    Pre pre;
-    prefetch(qi, pre);
-    int j = 0;   // planes issued
-    for (; j < AHEAD && qi.k < nu && ok; ++j) {
-        issue(j, pre);
-        advance(qi);
-        if (qi.k < nu) prefetch(qi, pre);
+    c.w = warp;
+    c.h = lane >> 4;
+    c.sl = lane & 15;
+    {
+        const int px = warp & 3, ty0 = 4 * (warp >> 2) + 2 * c.h, sl = c.sl;
+        const int tx0 = 4 * px;
+        c.cb = ((ty0 + 4) * 16 + tx0) * PS + sl;
+        c.to = ty0 * TX + tx0;
+        // left / right neighbours: core columns, or the side halo at the tile's edges
+        c.lb0 = (px == 0 ? 256 + ty0 * 8 : (ty0 + 4) * 16 + tx0 - 4) * PS + sl;
+        c.lb1 = (px == 0 ? 256 + (ty0 + 1) * 8 : (ty0 + 5) * 16 + tx0 - 4) * PS + sl;
+        c.rb0 = (px == 3 ? 256 + ty0 * 8 + 4 : (ty0 + 4) * 16 + tx0 + 4) * PS + sl;
+        c.rb1 = (px == 3 ? 256 + (ty0 + 1) * 8 + 4 : (ty0 + 5) * 16 + tx0 + 4) * PS + sl;
     }
+    const float2 *cs2 = reinterpret_cast<const float2 *>(cs);
+    float *hp = a.hpsi + grp * SG + 2 * c.sl;
+    float2 A[8][2][4];
+
+    while (j < AHEAD && qi.k < nu && ok) issue();
     for (int it = 0; qc.k < nu && ok; ++it) {
         if (qi.k < nu) {
-            issue(j++, pre);
-            advance(qi);
+            issue();
             if (!ok) break;
-            if (qi.k < nu) prefetch(qi, pre);
         }
         const int slot = it % RING;
         if (!__all_sync(0xffffffffu, bar_wait(&fullb[slot], (it / RING) & 1))) {
@@ -437,30 +455,48 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
         const int z = qc.z;
         if (z == U.zm0) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) A[k][0] = A[k][1] = make_float2(0.f, 0.f);
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) A[k][r][x] = make_float2(0.f, 0.f);
         }
         const bool full = z >= U.zo0 && z < U.zo1;
-        const float *P = reinterpret_cast<const float *>(psi_ring + (size_t)slot * SLOT_PSI);
+        const float2 *P = reinterpret_cast<const float2 *>(psi_ring + (size_t)slot * SLOT_PSI);
         const unsigned char *rs = rec_ring + (size_t)slot * a.rec_slot;
-        uint64_t *eb = &emptyb[slot];
+        float2 cc[2][4], T[2][4];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) cc[r][x] = P[c.cb + (r * 16 + x) * PS];
+        if (full) {
+            plane_terms(T, cc, P, rs, cs2, c);
+            // the plane's point indices to the output ring (one lane per half-warp)
+            if (c.sl == 0) {
+                const int4 *I4 = reinterpret_cast<const int4 *>(rs + REC_IDX) + (c.to >> 2);
+                int4 *ring4 = reinterpret_cast<int4 *>(rowring + (z & 7) * NPOS) + (c.to >> 2);
+                ring4[0] = I4[0];
+                ring4[TX / 4] = I4[TX / 4];
+            }
+        }
+        __syncwarp();
+        if (lane == 0) bar_arrive(&emptyb[slot]);   // the slot is no longer read by this warp
         const bool st = z - 4 >= U.zo0 && z - 4 < U.zo1;
-        switch (z % 9) {
-            case 0: step<0>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            case 1: step<1>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            case 2: step<2>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            case 3: step<3>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            case 4: step<4>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            case 5: step<5>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            case 6: step<6>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            case 7: step<7>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
-            default: step<8>(A, P, rs, rowring, eb, full, cpl, nb4, hp, a.ldh, st, c); break;
+        switch (z & 7) {
+            case 0: zterms<0>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
+            case 1: zterms<1>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
+            case 2: zterms<2>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
+            case 3: zterms<3>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
+            case 4: zterms<4>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
+            case 5: zterms<5>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
+            case 6: zterms<6>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
+            default: zterms<7>(A, cc, T, full, st, rowring, hp, a.ldh, c); break;
         }
         // last plane of the column inside the unit: planes beyond it are
         // empty, so the outputs still open are complete
         if (z == U.zm1 && z < U.zo1 + 3) {
-            __syncwarp();
             for (int o = z - 3; o <= z; ++o)
-                if (o >= U.zo0 && o < U.zo1) emit_any(o % 9, A, rowring, hp, a.ldh, c);
+                if (o >= U.zo0 && o < U.zo1) emit_any(o & 7, A, rowring, hp, a.ldh, c);
         }
         advance(qc);
     }
@@ -471,18 +507,18 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
 }  // namespace
 
 struct RingPlan {
-    DevBuf units, cta, desc, recs, rec, status;
-    int n_cta = 0, rec_slot = 0, n_atoms = 0;
+    DevBuf units, cta, cta_atoms, desc, recs, rec, status;
+    int n_cta = 0, rec_slot = 0, cs_atoms = 0, ring = MAX_RING;
     int64_t npts = 0;
-    size_t smem = 0;          // without staged coefficients
-    size_t smem_cps = 0;      // with the coefficients of one state group staged
-    int smem_set[2] = {0, 0};
+    size_t smem = 0;
+    int smem_set = 0;
 };
 
 void ring_plan_destroy(RingPlan *p) { delete p; }
 
 int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t> &coff, const std::vector<int32_t> &catom,
                     const std::vector<float> &cg32, const std::vector<float> &v32, int n_atoms, int slab) {
+    (void)n_atoms;
     *out = nullptr;
     if (g->npts >= (1 << 28) || slab < 1 || slab > MAX_SLAB) return RS_OK;
     const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
@@ -490,7 +526,7 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
         if (a0 < 0 || a1 < 0 || a2 < 0 || a0 >= d0 || a1 >= d1 || a2 >= d2) return -1;
         return g->map[((size_t)a0 * d1 + a1) * d2 + a2];
     };
-    const int n1 = (d1 + TT - 1) / TT, n2 = (d2 + TT - 1) / TT;
+    const int n1 = (d1 + TY - 1) / TY, n2 = (d2 + TX - 1) / TX;
     struct Col {
         int zmin, zmax;
         int64_t p0;   // record / descriptor index of plane zmin
@@ -498,17 +534,23 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
     std::vector<Col> cols;
     std::vector<uint32_t> desc;
     std::vector<uint2> recs;
+    std::vector<double> pcost;   // march cost of each full plane (planes of the nonlocal-heaviest patch cost more)
     std::vector<int32_t> blob;   // 4-byte words; records start on 16-byte boundaries
     int max_rec = 0;
     int64_t nplanes = 0;
+    auto word = [](float f) {
+        int32_t b;
+        memcpy(&b, &f, 4);
+        return b;
+    };
     try {
         for (int t1 = 0; t1 < n1; ++t1)
             for (int t2 = 0; t2 < n2; ++t2) {
-                const int b1 = t1 * TT, b2 = t2 * TT;
+                const int b1 = t1 * TY, b2 = t2 * TX;
                 int zmin = d0, zmax = -1;
                 for (int a0 = 0; a0 < d0; ++a0)
-                    for (int iy = 0; iy < TT; ++iy)
-                        for (int ix = 0; ix < TT; ++ix)
+                    for (int iy = 0; iy < TY; ++iy)
+                        for (int ix = 0; ix < TX; ++ix)
                             if (at(a0, b1 + iy, b2 + ix) >= 0) {
                                 zmin = std::min(zmin, a0);
                                 zmax = std::max(zmax, a0);
@@ -517,12 +559,12 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                 cols.push_back({zmin, zmax, nplanes});
                 for (int z = zmin; z <= zmax; ++z) {
                     for (int gi = 0; gi < NG; ++gi) {
-                        int yw, xw;
-                        group_pos(gi, yw, xw);
+                        int wy, wx;
+                        group_pos(gi, wy, wx);
                         uint32_t mask = 0;
                         int32_t first = -1, prev = -1;
                         for (int i = 0; i < 4; ++i) {
-                            const int32_t m = at(z, b1 + yw - 4, b2 + xw - 4 + i);
+                            const int32_t m = at(z, b1 + wy - 4, b2 + wx - 4 + i);
                             if (m < 0) continue;
                             if (first < 0) first = m;
                             else if (m != prev + 1) return fail(RS_EINVAL, "stencil plan: brick row not consecutive");
@@ -531,50 +573,51 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                         }
                         desc.push_back((mask << 28) | (uint32_t)(first < 0 ? 0 : first));
                     }
-                    // record: {entries}, meta[64] {V bits, point, first entry, entries},
-                    // projector values [entries][4], atoms [entries] (padded)
+                    // record of plane z
                     const size_t off = blob.size();
-                    int4 meta[NPOS];
-                    std::vector<float> gm;
-                    std::vector<int32_t> am;
-                    for (int iy = 0; iy < TT; ++iy)
-                        for (int ix = 0; ix < TT; ++ix) {
+                    std::vector<int32_t> hdr(REC_V / 4, 0), vv(NPOS, 0), ii(NPOS, -1), blocks;
+                    for (int iy = 0; iy < TY; ++iy)
+                        for (int ix = 0; ix < TX; ++ix) {
                             const int32_t m = at(z, b1 + iy, b2 + ix);
-                            if (m < 0) {
-                                meta[iy * TT + ix] = make_int4(0, -1, 0, 0);
-                                continue;
-                            }
-                            int32_t vb;
-                            memcpy(&vb, &v32[m], 4);
-                            const int e0 = coff[m], e1 = coff[m + 1];
-                            meta[iy * TT + ix] = make_int4(vb, m, (int)am.size(), e1 - e0);
-                            for (int e = e0; e < e1; ++e) {
-                                for (int q = 0; q < 4; ++q) gm.push_back(cg32[(size_t)e * 4 + q]);
-                                am.push_back(catom[e]);
-                            }
+                            if (m < 0) continue;
+                            vv[iy * TX + ix] = word(v32[m]);
+                            ii[iy * TX + ix] = m;
                         }
-                    const int E = (int)am.size();
-                    while (am.size() % 4) am.push_back(0);
-                    blob.push_back(E);
-                    blob.push_back(0);
-                    blob.push_back(0);
-                    blob.push_back(0);
-                    for (int i = 0; i < NPOS; ++i) {
-                        blob.push_back(meta[i].x);
-                        blob.push_back(meta[i].y);
-                        blob.push_back(meta[i].z);
-                        blob.push_back(meta[i].w);
+                    for (int w = 0; w < NW; ++w) {
+                        const int py = w >> 2, px = w & 3;
+                        // atom -> projector values of the 16 patch points
+                        std::map<int32_t, std::vector<float>> per_atom;
+                        for (int rr = 0; rr < 4; ++rr)
+                            for (int xx = 0; xx < 4; ++xx) {
+                                const int32_t m = ii[(4 * py + rr) * TX + 4 * px + xx];
+                                if (m < 0) continue;
+                                for (int e = coff[m]; e < coff[m + 1]; ++e) {
+                                    std::vector<float> &gv = per_atom[catom[e]];
+                                    if (gv.empty()) gv.assign(64, 0.f);
+                                    for (int q = 0; q < 4; ++q) gv[(rr * 4 + xx) * 4 + q] = cg32[(size_t)e * 4 + q];
+                                }
+                            }
+                        hdr[2 * w] = (int32_t)per_atom.size();
+                        hdr[2 * w + 1] = REC_BLK + (int32_t)blocks.size() * 4;
+                        for (const auto &pa : per_atom) {
+                            blocks.push_back(pa.first);
+                            blocks.push_back(0);
+                            blocks.push_back(0);
+                            blocks.push_back(0);
+                            for (float f : pa.second) blocks.push_back(word(f));
+                        }
                     }
-                    for (float f : gm) {
-                        int32_t b;
-                        memcpy(&b, &f, 4);
-                        blob.push_back(b);
-                    }
-                    blob.insert(blob.end(), am.begin(), am.end());
+                    blob.insert(blob.end(), hdr.begin(), hdr.end());
+                    blob.insert(blob.end(), vv.begin(), vv.end());
+                    blob.insert(blob.end(), ii.begin(), ii.end());
+                    blob.insert(blob.end(), blocks.begin(), blocks.end());
                     const int bytes = (int)((blob.size() - off) * 4);
                     max_rec = std::max(max_rec, bytes);
                     if (off / 4 > UINT32_MAX) return RS_OK;
                     recs.push_back(make_uint2((uint32_t)(off / 4), (uint32_t)bytes));
+                    int maxblk = 0;
+                    for (int w = 0; w < NW; ++w) maxblk = std::max(maxblk, hdr[2 * w]);
+                    pcost.push_back(1.0 + NL_COST * maxblk);
                     ++nplanes;
                 }
             }
@@ -602,7 +645,8 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                 const int64_t pz = cl.p0 - cl.zmin;
                 if (pz < INT32_MIN || pz > INT32_MAX) return RS_OK;
                 u.pz = (int)pz;
-                const double cost = (zo1 - zo0) + 0.25 * ((u.zm1 - u.zm0 + 1) - (zo1 - zo0));
+                double cost = 0.25 * ((u.zm1 - u.zm0 + 1) - (zo1 - zo0));
+                for (int z = zo0; z < zo1; ++z) cost += pcost[(size_t)(pz + z)];
                 us.push_back({cost, u});
             }
             std::stable_sort(us.begin(), us.end(), [](const std::pair<double, UnitDev> &x, const std::pair<double, UnitDev> &y) {
@@ -614,13 +658,38 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                 load[k] += cu.first;
             }
         }
+        // per CTA: the atoms its records name, renumbered in the records to
+        // the CTA's local order (a record belongs to the one unit whose
+        // output planes hold it)
         std::vector<UnitDev> flat;
-        std::vector<int2> cta(G);
+        std::vector<int4> cta(G);
+        std::vector<int32_t> cta_atoms;
+        int cs_atoms = 0;
         for (int k = 0; k < G; ++k) {
             if (per[k].size() > (size_t)MAX_UNITS) return RS_OK;
-            cta[k] = make_int2((int)flat.size(), (int)per[k].size());
+            std::map<int32_t, int32_t> local;
+            const int first_atom = (int)cta_atoms.size();
+            for (const UnitDev &u : per[k])
+                for (int z = u.zo0; z < u.zo1; ++z) {
+                    const size_t w0 = (size_t)recs[(size_t)((int64_t)u.pz + z)].x * 4;
+                    for (int w = 0; w < NW; ++w) {
+                        const int cnt = blob[w0 + 2 * w], b0 = blob[w0 + 2 * w + 1];
+                        for (int q = 0; q < cnt; ++q) {
+                            int32_t &aw = blob[w0 + (size_t)(b0 + q * BLK) / 4];
+                            auto it = local.find(aw);
+                            if (it == local.end()) {
+                                it = local.emplace(aw, (int32_t)local.size()).first;
+                                cta_atoms.push_back(aw);
+                            }
+                            aw = it->second;
+                        }
+                    }
+                }
+            cs_atoms = std::max(cs_atoms, (int)local.size());
+            cta[k] = make_int4((int)flat.size(), (int)per[k].size(), first_atom, (int)local.size());
             flat.insert(flat.end(), per[k].begin(), per[k].end());
         }
+        if (cta_atoms.empty()) cta_atoms.push_back(0);
         RingPlan *P = new (std::nothrow) RingPlan;
         if (!P) return fail(RS_ENOMEM, "host allocation failed");
         auto bail = [&](int rc) {
@@ -629,7 +698,8 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
         };
         int rc;
         if ((rc = P->units.upload(flat.data(), flat.size() * sizeof(UnitDev))) ||
-            (rc = P->cta.upload(cta.data(), cta.size() * sizeof(int2))) ||
+            (rc = P->cta.upload(cta.data(), cta.size() * sizeof(int4))) ||
+            (rc = P->cta_atoms.upload(cta_atoms.data(), cta_atoms.size() * sizeof(int32_t))) ||
             (rc = P->desc.upload(desc.data(), desc.size() * sizeof(uint32_t))) ||
             (rc = P->recs.upload(recs.data(), recs.size() * sizeof(uint2))) ||
             (rc = P->rec.upload(blob.data(), blob.size() * sizeof(int32_t))) || (rc = P->status.alloc(sizeof(int))))
@@ -637,11 +707,13 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
         if (cudaMemset(P->status.p, 0, sizeof(int)) != cudaSuccess) return bail(fail(RS_ECUDA, "cudaMemset failed"));
         P->n_cta = G;
         P->rec_slot = (max_rec + 127) & ~127;
+        P->cs_atoms = cs_atoms;
         P->npts = g->npts;
-        P->n_atoms = n_atoms;
-        P->smem = 1024 + (size_t)RING * (SLOT_PSI + P->rec_slot) + MAX_UNITS * sizeof(UnitDev) + 9 * NPOS * sizeof(int) +
-                  NG * 4 * sizeof(int);
-        P->smem_cps = P->smem + (size_t)n_atoms * SG * 4 * sizeof(float);
+        const size_t fixed = (size_t)cs_atoms * 4 * SG * sizeof(float) + MAX_UNITS * sizeof(UnitDev) + 8 * NPOS * sizeof(int);
+        for (P->ring = MAX_RING; P->ring > AHEAD; --P->ring) {
+            P->smem = (size_t)P->ring * (SLOT_PSI + P->rec_slot) + fixed;
+            if (P->smem <= MAX_SMEM) break;
+        }
         if (P->smem > MAX_SMEM) return bail(RS_OK);
         *out = P;
     } catch (const std::bad_alloc &) {
@@ -658,7 +730,9 @@ int ring_launch(RingPlan *p, const float *psi, int64_t ldp, float *hpsi, int64_t
                 const float w[5], cudaStream_t st) {
     Args a;
     a.units = p->units.as<UnitDev>();
-    a.cta = p->cta.as<int2>();
+    a.cta = p->cta.as<int4>();
+    a.cta_atoms = p->cta_atoms.as<int>();
+    a.cs_atoms = p->cs_atoms;
     a.desc = p->desc.as<uint32_t>();
     a.recs = p->recs.as<uint2>();
     a.rec = p->rec.as<unsigned char>();
@@ -668,24 +742,19 @@ int ring_launch(RingPlan *p, const float *psi, int64_t ldp, float *hpsi, int64_t
     a.hpsi = hpsi;
     a.ldh = ldh;
     a.nb = nb;
-    a.n_atoms = p->n_atoms;
     a.rec_slot = p->rec_slot;
     for (int j = 0; j < 5; ++j) a.w[j] = w[j];
     a.status = p->status.as<int>();
     const dim3 grid((unsigned)p->n_cta, (unsigned)(nb / SG));
-    if (p->n_atoms > 0 && p->smem_cps <= MAX_SMEM) {
-        if (p->smem_set[1] < (int)p->smem_cps) {
-            RS_CUDA(cudaFuncSetAttribute(k_hpsi_ring<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_cps));
-            p->smem_set[1] = (int)p->smem_cps;
-        }
-        k_hpsi_ring<true><<<grid, NT, p->smem_cps, st>>>(a);
-    } else {
-        if (p->smem_set[0] < (int)p->smem) {
-            RS_CUDA(cudaFuncSetAttribute(k_hpsi_ring<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
-            p->smem_set[0] = (int)p->smem;
-        }
-        k_hpsi_ring<false><<<grid, NT, p->smem, st>>>(a);
+    if (p->smem_set < (int)p->smem) {
+        if (p->ring == 4)
+            RS_CUDA(cudaFuncSetAttribute(k_hpsi_ring<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
+        else
+            RS_CUDA(cudaFuncSetAttribute(k_hpsi_ring<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
+        p->smem_set = (int)p->smem;
     }
+    if (p->ring == 4) k_hpsi_ring<4><<<grid, NT, p->smem, st>>>(a);
+    else k_hpsi_ring<3><<<grid, NT, p->smem, st>>>(a);
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
