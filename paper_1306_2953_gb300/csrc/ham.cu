@@ -6,6 +6,9 @@
 //     per (atom, state group), each a block-wide tree reduction over its share
 //     of the sphere points added to the zeroed coefficients; stored
 //     [atom][state][q] so that one 16-byte load gives a state's four.
+//     FP32 blocks of 32-state groups take k_project_f32 (four states per lane
+//     and four sphere entries per warp step, the atom split sized to fill the
+//     GPU).
 //  2. k_stencil: the 25-point star kinetic stencil (Sec. V.A), the local
 //     potential (Sec. V.B) and the nonlocal sum of Eq. (4), fused.  Each CTA
 //     owns a TX x TY column of lattice points (axes 2 and 1 of the point
@@ -143,6 +146,56 @@ __global__ void __launch_bounds__(NT) k_project(HamDev<T> d, const T *__restrict
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             atomicAdd(cproj + ((int64_t)A * nb + sg0 + s) * 4 + q, __ldg(d.E + 4 * A + q) * d.dV * red[q][s]);
+    }
+}
+
+// FP32 blocks of 32-state groups: lane l of a warp takes sphere entry
+// l / 8 of the warp's four and the states 4 (l % 8) .. + 3 (one 16-byte
+// load of the psi row), so a warp reads four psi rows per step; the grid is
+// (atoms * split, state groups) with the split sized to fill the GPU.
+constexpr int NTP4 = 256;
+
+__global__ void __launch_bounds__(NTP4) k_project_f32(HamDev<float> d, const float *__restrict__ psi, int64_t ldp,
+                                                     int nb, int split, float *__restrict__ cproj) {
+    __shared__ float red[NTP4 / 32][8][16];
+    const int A = blockIdx.x / split, part = blockIdx.x - A * split;
+    const int sg0 = blockIdx.y * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = lane & 7;
+    const int o = __ldg(d.sph_off + A), e = __ldg(d.sph_off + A + 1);
+    const int per = (e - o + split - 1) / split;
+    const int i0 = o + part * per, i1 = min(e, i0 + per);
+    const float *ps = psi + sg0 + 4 * q;
+    float acc[16];   // [projector][state]
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+#pragma unroll 4
+    for (int i = i0 + 4 * warp + (lane >> 3); i < i1; i += 4 * (NTP4 / 32)) {
+        const int p = __ldg(d.sph_idx + i);
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(ps + (int64_t)p * ldp));
+        const float4 g = __ldg(reinterpret_cast<const float4 *>(d.sph_gam) + i);
+        const float gv[4] = {g.x, g.y, g.z, g.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int st = 0; st < 4; ++st) acc[4 * l + st] = fmaf(gv[l], vv[st], acc[4 * l + st]);
+    }
+    // the four entries of a warp, then the warps
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 8);
+        acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 16);
+    }
+    if (lane < 8) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) red[warp][q][k] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 128 && i0 < i1) {
+        const int qq = threadIdx.x >> 4, k = threadIdx.x & 15, l = k >> 2, st = k & 3;
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < NTP4 / 32; ++w) t += red[w][qq][k];
+        atomicAdd(cproj + ((int64_t)A * nb + sg0 + 4 * qq + st) * 4 + l, __ldg(d.E + 4 * A + l) * d.dV * t);
     }
 }
 
@@ -407,6 +460,7 @@ struct rs_ham {
     int n_atoms = 0;
     int64_t n_entries = 0;
     int device = 0;
+    int n_sm = 1;                  // SMs of the device (grid sizing)
     double w[5] = {0, 0, 0, 0, 0};
     DevBuf pinfo64, pinfo32, map, loc, V64, V32, cov_off, cov_atom, cov_gam64, cov_gam32, sph_off, sph_idx, sph_gam64, sph_gam32, E64, E32,
         cproj, dummy, scratch;
@@ -529,6 +583,8 @@ extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_pr
         return rc;
     };
     H->device = dev;
+    if (cudaDeviceGetAttribute(&H->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || H->n_sm < 1)
+        return bail(fail(RS_ECUDA, "device query failed"));
     H->npts = g->npts;
     for (int i = 0; i < 3; ++i) H->d[i] = g->dims[i];
     H->h = g->h;
@@ -645,7 +701,17 @@ static int apply_t(rs_ham *H, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, i
         dim3 grid((unsigned)(H->n_atoms * PSPLIT), (unsigned)(nb / sgp));
         T *cp = H->cproj.as<T>();
         RS_CUDA(cudaMemsetAsync(cp, 0, sizeof(T) * (size_t)H->n_atoms * 4 * nb, st));
-        switch (sgp) {
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (nb % 32 == 0 && ldp % 4 == 0 && aligned16(psi)) {
+                // about eight CTAs of 256 threads per SM
+                const int split = std::max(1, std::min(64, (8 * H->n_sm + H->n_atoms - 1) / H->n_atoms));
+                k_project_f32<<<dim3((unsigned)(H->n_atoms * split), (unsigned)(nb / 32)), NTP4, 0, st>>>(d, psi, ldp, nb,
+                                                                                                        split, cp);
+                done = true;
+            }
+        }
+        if (!done) switch (sgp) {
             case 1: k_project<T, 1, 512><<<grid, 512, 0, st>>>(d, psi, ldp, nb, cp); break;
             case 2: k_project<T, 2, 512><<<grid, 512, 0, st>>>(d, psi, ldp, nb, cp); break;
             case 4: k_project<T, 4, 512><<<grid, 512, 0, st>>>(d, psi, ldp, nb, cp); break;

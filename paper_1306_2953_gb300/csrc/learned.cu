@@ -410,51 +410,64 @@ __global__ void k_rms(const double *ss, int n, double inv_np, double *rms) {
 }
 
 // --------------------------------------------- inference on the grid ---
-// Weights (BF16 values) in constant memory so that the FMAs take them as
-// constant-bank operands.
-__constant__ float c_w[W_TOTAL];
 
 // xhat = bf16(r / rms) and the per-column rms
 __global__ void k_net_input(const float *__restrict__ R, int64_t ldr, const double *__restrict__ rms, int nb,
-                            int64_t npts, float *__restrict__ x) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                            int npts, float *__restrict__ x) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npts * nb) return;
-    const int64_t p = t / nb;
-    const int s = (int)(t % nb);
-    x[t] = bf16_round(R[p * ldr + s] * (float)(1.0 / rms[s]));
+    const int p = t / nb, s = t - p * nb;
+    x[t] = bf16_round(R[(int64_t)p * ldr + s] * (float)(1.0 / rms[s]));
 }
 
-// layer on the grid: out[p][co][s] = act(sum_t sum_ci w[co][ci][t] in[nbr_t(p)][ci][s])
+// layer on the grid: out[p][co][s] = act(sum_t sum_ci w[co][ci][t] in[nbr_t(p)][ci][s]).
+// The layer's weights (BF16 values) are staged in shared memory as
+// [tap][ci][co], so one 16-byte load gives four output channels' weights
+// (a broadcast: every lane reads the same word).
 template <int CIN, int COUT, bool RELU, bool FINAL, int WOFF>
 __global__ void __launch_bounds__(256) k_net_layer(const int32_t *__restrict__ map, const int32_t *__restrict__ loc,
-                                                   int d1, int d2, int64_t npts, int nb, const float *__restrict__ in,
-                                                   float *__restrict__ out, int64_t ldo, const double *__restrict__ rms) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                                                   int d1, int d2, int npts, int nb, const float *__restrict__ wq,
+                                                   const float *__restrict__ in, float *__restrict__ out, int64_t ldo,
+                                                   const double *__restrict__ rms) {
+    constexpr int CO4 = (COUT + 3) / 4 * 4;
+    __shared__ __align__(16) float ws[27 * CIN * CO4];
+    for (int e = threadIdx.x; e < 27 * CIN * CO4; e += blockDim.x) {
+        const int co = e % CO4, ci = (e / CO4) % CIN, tap = e / (CO4 * CIN);
+        ws[e] = co < COUT ? __ldg(wq + WOFF + (co * CIN + ci) * 27 + tap) : 0.f;
+    }
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npts * nb) return;
-    const int64_t p = t / nb;
-    const int s = (int)(t % nb);
+    const int p = t / nb, s = t - p * nb;
     const int64_t L = __ldg(loc + p);
-    float acc[COUT];
+    float acc[CO4];
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
-#pragma unroll
+    for (int co = 0; co < CO4; ++co) acc[co] = 0.f;
+#pragma unroll 3
     for (int tap = 0; tap < 27; ++tap) {
         const int64_t off = ((int64_t)(tap / 9 - 1) * d1 + ((tap / 3) % 3 - 1)) * d2 + (tap % 3 - 1);
         const int q = __ldg(map + L + off);
         if (q < 0) continue;
         const float *src = in + ((int64_t)q * CIN) * nb + s;
+        const float4 *w4 = reinterpret_cast<const float4 *>(ws + tap * CIN * CO4);
 #pragma unroll
         for (int ci = 0; ci < CIN; ++ci) {
             const float x = __ldg(src + (int64_t)ci * nb);
 #pragma unroll
-            for (int co = 0; co < COUT; ++co) acc[co] = fmaf(c_w[WOFF + (co * CIN + ci) * 27 + tap], x, acc[co]);
+            for (int c4 = 0; c4 < CO4 / 4; ++c4) {
+                const float4 w = w4[ci * (CO4 / 4) + c4];
+                acc[4 * c4 + 0] = fmaf(w.x, x, acc[4 * c4 + 0]);
+                if (4 * c4 + 1 < COUT) acc[4 * c4 + 1] = fmaf(w.y, x, acc[4 * c4 + 1]);
+                if (4 * c4 + 2 < COUT) acc[4 * c4 + 2] = fmaf(w.z, x, acc[4 * c4 + 2]);
+                if (4 * c4 + 3 < COUT) acc[4 * c4 + 3] = fmaf(w.w, x, acc[4 * c4 + 3]);
+            }
         }
     }
     if (FINAL) {
-        out[p * ldo + s] = acc[0] * (float)rms[s];
+        out[(int64_t)p * ldo + s] = acc[0] * (float)rms[s];
     } else {
 #pragma unroll
-        for (int co = 0; co < COUT; ++co) out[(p * COUT + co) * nb + s] = RELU ? fmaxf(acc[co], 0.f) : acc[co];
+        for (int co = 0; co < COUT; ++co) out[((int64_t)p * COUT + co) * nb + s] = RELU ? fmaxf(acc[co], 0.f) : acc[co];
     }
 }
 
@@ -629,15 +642,16 @@ int learned_apply(const rs_ham *h, const float *R, int64_t ldr, float *W, int64_
     double *ss = dots, *rms = dots + 64;
     RS_TRY(coldots(RS_F32, R, ldr, R, ldr, nb, np, ss, st));
     k_rms<<<1, 64, 0, st>>>(ss, nb, 1.0 / (double)np, rms);
-    RS_CUDA(cudaMemcpyToSymbolAsync(c_w, wq_dev, sizeof(float) * W_TOTAL, 0, cudaMemcpyDeviceToDevice, st));
+    if (np * nb >= (int64_t)INT32_MAX) return fail(RS_EINVAL, "learned preconditioner: npts * nb above 2^31");
+    const int n32 = (int)np;
     float *x = act, *a1 = x + np * nb, *a2 = a1 + np * NC * nb;
     const unsigned blocks = (unsigned)((np * nb + 255) / 256);
-    k_net_input<<<blocks, 256, 0, st>>>(R, ldr, rms, nb, np, x);
+    k_net_input<<<blocks, 256, 0, st>>>(R, ldr, rms, nb, n32, x);
     const int32_t *map = ham_map(h), *loc = ham_loc(h);
     const int d1 = ham_dim(h, 1), d2 = ham_dim(h, 2);
-    k_net_layer<1, NC, true, false, W1_OFF><<<blocks, 256, 0, st>>>(map, loc, d1, d2, np, nb, x, a1, 0, rms);
-    k_net_layer<NC, NC, true, false, W2_OFF><<<blocks, 256, 0, st>>>(map, loc, d1, d2, np, nb, a1, a2, 0, rms);
-    k_net_layer<NC, 1, false, true, W3_OFF><<<blocks, 256, 0, st>>>(map, loc, d1, d2, np, nb, a2, W, ldw, rms);
+    k_net_layer<1, NC, true, false, W1_OFF><<<blocks, 256, 0, st>>>(map, loc, d1, d2, n32, nb, wq_dev, x, a1, 0, rms);
+    k_net_layer<NC, NC, true, false, W2_OFF><<<blocks, 256, 0, st>>>(map, loc, d1, d2, n32, nb, wq_dev, a1, a2, 0, rms);
+    k_net_layer<NC, 1, false, true, W3_OFF><<<blocks, 256, 0, st>>>(map, loc, d1, d2, n32, nb, wq_dev, a2, W, ldw, rms);
     RS_LAUNCH_CHECK();
     return RS_OK;
 }

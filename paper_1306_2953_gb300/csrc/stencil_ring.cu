@@ -78,7 +78,7 @@ constexpr int REC_IDX = REC_V + NPOS * 4;
 constexpr int REC_BLK = REC_IDX + NPOS * 4;
 constexpr int BLK = 16 + 16 * 16;
 constexpr int MAX_REC = 48 * 1024;         // record slot budget (bytes)
-constexpr size_t MAX_SMEM = 227 * 1024;    // dynamic shared memory per CTA
+constexpr size_t MAX_SMEM = 226 * 1024;    // dynamic shared memory per CTA (227 KB less the static part)
 constexpr int MAX_SLAB = 128;              // planes per z-slab of a unit (at most)
 constexpr int MAX_UNITS = 64;              // units per CTA (shared-memory table)
 constexpr int SUSPEND_NS = 20000;          // suspension limit of one barrier test
@@ -511,7 +511,6 @@ struct RingPlan {
     int n_cta = 0, rec_slot = 0, cs_atoms = 0, ring = MAX_RING;
     int64_t npts = 0;
     size_t smem = 0;
-    int smem_set = 0;
 };
 
 void ring_plan_destroy(RingPlan *p) { delete p; }
@@ -746,14 +745,24 @@ int ring_launch(RingPlan *p, const float *psi, int64_t ldp, float *hpsi, int64_t
     for (int j = 0; j < 5; ++j) a.w[j] = w[j];
     a.status = p->status.as<int>();
     const dim3 grid((unsigned)p->n_cta, (unsigned)(nb / SG));
-    if (p->smem_set < (int)p->smem) {
-        if (p->ring == 4)
-            RS_CUDA(cudaFuncSetAttribute(k_hpsi_ring<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
-        else
-            RS_CUDA(cudaFuncSetAttribute(k_hpsi_ring<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem));
-        p->smem_set = (int)p->smem;
+    // the shared-memory limit is an attribute of the kernel, not of the plan:
+    // it is raised once to the largest any plan may ask for
+    // (the device's opt-in maximum less the kernel's static shared memory)
+    static bool limit_set[2] = {false, false};
+    const int r4 = p->ring == 4 ? 1 : 0;
+    if (!limit_set[r4]) {
+        const void *fn = r4 ? (const void *)k_hpsi_ring<4> : (const void *)k_hpsi_ring<3>;
+        cudaFuncAttributes fa;
+        int dev = 0, optin = 0;
+        RS_CUDA(cudaFuncGetAttributes(&fa, fn));
+        RS_CUDA(cudaGetDevice(&dev));
+        RS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const int lim = optin - (int)fa.sharedSizeBytes;
+        if (lim < (int)p->smem) return fail(RS_ECUDA, "ring kernel: %zu bytes of shared memory above the device limit", p->smem);
+        RS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        limit_set[r4] = true;
     }
-    if (p->ring == 4) k_hpsi_ring<4><<<grid, NT, p->smem, st>>>(a);
+    if (r4) k_hpsi_ring<4><<<grid, NT, p->smem, st>>>(a);
     else k_hpsi_ring<3><<<grid, NT, p->smem, st>>>(a);
     RS_LAUNCH_CHECK();
     return RS_OK;

@@ -113,6 +113,25 @@ def test_hpsi_f32_mol20_repeated_calls():
     assert H.status() == 0
 
 
+def test_hpsi_f32_interleaved_handles():
+    """Two Hamiltonians whose FP32 kernels need different shared memory
+    (a molecule with projectors and a box without), applied alternately:
+    the second handle's launch configuration must not break the first's."""
+    spec = wl.MOL20.system
+    lg_m, H_m, g_m, Ho_m, idx_m = _lib_system("mol", (spec,))
+    lg_b, H_b, g_b, Ho_b, idx_b = _lib_system("box", (17, 0.3, 1.0))
+    psi_m32 = wl.random_block(g_m.npts, 32, 41).astype(np.float32)
+    psi_b32 = wl.random_block(g_b.npts, 32, 42).astype(np.float32)
+    ref_m = Ho_m.apply(psi_m32.astype(np.float64))[idx_m]
+    ref_b = Ho_b.apply(psi_b32.astype(np.float64))[idx_b]
+    pm = torch.from_numpy(np.ascontiguousarray(psi_m32[idx_m])).cuda()
+    pb = torch.from_numpy(np.ascontiguousarray(psi_b32[idx_b])).cuda()
+    for H, p, ref in ((H_m, pm, ref_m), (H_b, pb, ref_b), (H_m, pm, ref_m), (H_b, pb, ref_b)):
+        o = H.apply(p, nb=32).cpu().numpy().astype(np.float64)
+        assert np.max(_rel_err_per_state(o, ref)) <= 3e-5
+    assert H_m.status() == 0 and H_b.status() == 0
+
+
 def test_hpsi_strided_block_and_untouched_columns():
     kind, params = SYSTEMS["small_mol"]
     lg, H, g_ora, H_ora, idx = _lib_system(kind, params)
