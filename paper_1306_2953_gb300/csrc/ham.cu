@@ -44,9 +44,10 @@
 #define RS_STENCIL_RING 1
 #endif
 
-// Height (planes) of the z-slabs of that kernel's work units.
+// Height (planes) of the z-slabs the ring kernel lays its columns out in
+// before cutting them into per-CTA runs (the default: whole columns).
 #ifndef RS_RING_SLAB
-#define RS_RING_SLAB 48
+#define RS_RING_SLAB 4096
 #endif
 
 #ifndef RS_STENCIL_MINB_F32
@@ -662,7 +663,7 @@ extern "C" int rs_ham_create(const rs_grid *g, const double *V_host, const rs_pr
     for (const Shape &s : kShapes)
         if ((rc = build_work(H, g, s.tx, s.ty))) return bail(rc);
 #if RS_STENCIL_RING
-    if ((rc = ring_plan_build(&H->ring, g, coff, catom, cg32, v32, na, RS_RING_SLAB))) return bail(rc);
+    if ((rc = ring_plan_build(&H->ring, g, coff, catom, cg32, v32, (float)H->w[0], na, RS_RING_SLAB))) return bail(rc);
 #endif
     *out = H;
     return RS_OK;

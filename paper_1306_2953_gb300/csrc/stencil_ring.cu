@@ -3,12 +3,12 @@
 // and the nonlocal gather of Eq. (4), one persistent CTA per SM.
 //
 // Work.  The point map is cut into 16 x 8 tiles (16 along map axis 2, 8
-// along axis 1) and each tile column into z-slabs along the march axis 0; a
-// unit is (column, slab).  The host deals the units of every slab to the
-// CTAs, largest first onto the least loaded CTA, and each CTA takes its
-// units slab by slab: at any moment the CTAs march neighbouring columns of
-// the same slab, so the halo rows they share are re-read from L2 rather than
-// HBM.  blockIdx.y is the state group (32 states) of the block.
+// along axis 1); a tile column is marched along axis 0.  The host lays the
+// columns out slab by slab (z-slabs of a given height; the default is one
+// slab, whole columns) in raster order and cuts that sequence into one
+// contiguous run per CTA of equal modelled cost, splitting a column at a
+// plane where a run ends; a unit is such a piece of a column.  blockIdx.y is
+// the state group (32 states) of the block.
 //
 // Ring.  A CTA keeps RING planes (4, or 3 when 4 do not fit in shared
 // memory) of its column in shared memory.  A slot holds the 320 window
@@ -73,13 +73,20 @@ constexpr int MAX_RING = 4;                // slots per CTA (4, or 3 when 4 do n
 constexpr int NPOS = TX * TY;
 // record: [patch headers {blocks, byte offset}] [potential, tile row-major]
 // [point index, tile row-major] [blocks: {atom} + projector values [16][4]]
+#ifndef RS_RING_VW0
+#define RS_RING_VW0 0
+#endif
+#ifndef RS_RING_GDUP
+#define RS_RING_GDUP 0
+#endif
 constexpr int REC_V = 128;
-constexpr int REC_IDX = REC_V + NPOS * 4;
+constexpr int REC_IDX = REC_V + NPOS * (RS_RING_VW0 ? 8 : 4);
 constexpr int REC_BLK = REC_IDX + NPOS * 4;
-constexpr int BLK = 16 + 16 * 16;
+constexpr int GW = RS_RING_GDUP ? 8 : 4;   // floats per point in a block
+constexpr int BLK = 16 + 16 * GW * 4;
 constexpr int MAX_REC = 48 * 1024;         // record slot budget (bytes)
 constexpr size_t MAX_SMEM = 226 * 1024;    // dynamic shared memory per CTA (227 KB less the static part)
-constexpr int MAX_SLAB = 128;              // planes per z-slab of a unit (at most)
+constexpr int MAX_SLAB = 1 << 16;          // planes per z-slab (at most)
 constexpr int MAX_UNITS = 64;              // units per CTA (shared-memory table)
 constexpr int SUSPEND_NS = 20000;          // suspension limit of one barrier test
 constexpr int SPIN = 100000;               // barrier tests before a wait gives up
@@ -188,6 +195,17 @@ constexpr int PS = ROWB / 8;
 __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc)[2][4], const float2 *__restrict__ P,
                                             const unsigned char *__restrict__ rs, const float2 *__restrict__ cs,
                                             const Lane &c) {
+#if RS_RING_VW0
+    const float4 *V4 = reinterpret_cast<const float4 *>(rs + REC_V) + (c.to >> 1);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float4 v01 = V4[r * (TX / 2)], v23 = V4[r * (TX / 2) + 1];
+        T[r][0] = make_float2(v01.x, v01.y) * cc[r][0];
+        T[r][1] = make_float2(v01.z, v01.w) * cc[r][1];
+        T[r][2] = make_float2(v23.x, v23.y) * cc[r][2];
+        T[r][3] = make_float2(v23.z, v23.w) * cc[r][3];
+    }
+#else
     const float4 *V4 = reinterpret_cast<const float4 *>(rs + REC_V) + (c.to >> 2);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -197,6 +215,7 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
         T[r][2] = f2(c.w0 + v.z) * cc[r][2];
         T[r][3] = f2(c.w0 + v.w) * cc[r][3];
     }
+#endif
     // axis-2 neighbours: the four left and right of each patch row
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -239,6 +258,21 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
     for (int k = 0; k < hd.x; ++k, blk += BLK) {
         const float2 *cq = cs + *reinterpret_cast<const int *>(blk) * (4 * SG / 2) + c.sl;
         const float2 c0 = cq[0], c1 = cq[SG / 2], c2 = cq[SG], c3 = cq[3 * SG / 2];
+#if RS_RING_GDUP
+        const float4 *g = reinterpret_cast<const float4 *>(blk + 16) + 16 * c.h;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const float4 g01 = g[2 * (r * 4 + x)], g23 = g[2 * (r * 4 + x) + 1];
+                float2 a = T[r][x];
+                a = fma2(make_float2(g01.x, g01.y), c0, a);
+                a = fma2(make_float2(g01.z, g01.w), c1, a);
+                a = fma2(make_float2(g23.x, g23.y), c2, a);
+                a = fma2(make_float2(g23.z, g23.w), c3, a);
+                T[r][x] = a;
+            }
+#else
         const float4 *g = reinterpret_cast<const float4 *>(blk + 16) + 8 * c.h;
 #pragma unroll
         for (int r = 0; r < 2; ++r)
@@ -252,6 +286,7 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
                 a = fma2(f2(gv.w), c3, a);
                 T[r][x] = a;
             }
+#endif
     }
 }
 
@@ -516,7 +551,8 @@ struct RingPlan {
 void ring_plan_destroy(RingPlan *p) { delete p; }
 
 int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t> &coff, const std::vector<int32_t> &catom,
-                    const std::vector<float> &cg32, const std::vector<float> &v32, int n_atoms, int slab) {
+                    const std::vector<float> &cg32, const std::vector<float> &v32, float w0, int n_atoms, int slab) {
+    (void)w0;
     (void)n_atoms;
     *out = nullptr;
     if (g->npts >= (1 << 28) || slab < 1 || slab > MAX_SLAB) return RS_OK;
@@ -574,12 +610,18 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                     }
                     // record of plane z
                     const size_t off = blob.size();
-                    std::vector<int32_t> hdr(REC_V / 4, 0), vv(NPOS, 0), ii(NPOS, -1), blocks;
+                    std::vector<int32_t> hdr(REC_V / 4, 0), vv(NPOS * (RS_RING_VW0 ? 2 : 1), 0), ii(NPOS, -1), blocks;
                     for (int iy = 0; iy < TY; ++iy)
                         for (int ix = 0; ix < TX; ++ix) {
                             const int32_t m = at(z, b1 + iy, b2 + ix);
                             if (m < 0) continue;
+#if RS_RING_VW0
+                            // the centre weight plus the potential, as the kernel would add them
+                            const float vw = w0 + v32[m];
+                            vv[2 * (iy * TX + ix)] = vv[2 * (iy * TX + ix) + 1] = word(vw);
+#else
                             vv[iy * TX + ix] = word(v32[m]);
+#endif
                             ii[iy * TX + ix] = m;
                         }
                     for (int w = 0; w < NW; ++w) {
@@ -592,8 +634,10 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                                 if (m < 0) continue;
                                 for (int e = coff[m]; e < coff[m + 1]; ++e) {
                                     std::vector<float> &gv = per_atom[catom[e]];
-                                    if (gv.empty()) gv.assign(64, 0.f);
-                                    for (int q = 0; q < 4; ++q) gv[(rr * 4 + xx) * 4 + q] = cg32[(size_t)e * 4 + q];
+                                    if (gv.empty()) gv.assign(16 * GW, 0.f);
+                                    for (int q = 0; q < 4; ++q)
+                                        for (int u = 0; u < GW / 4; ++u)
+                                            gv[(rr * 4 + xx) * GW + q * (GW / 4) + u] = cg32[(size_t)e * 4 + q];
                                 }
                             }
                         hdr[2 * w] = (int32_t)per_atom.size();
@@ -625,38 +669,87 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return fail(RS_ECUDA, "device query failed");
-        // units slab by slab; within a slab, largest unit first onto the least
-        // loaded CTA (cost: planes marched, edge planes at a quarter)
+        // Units slab by slab, columns in raster order within a slab; the
+        // sequence is cut into one contiguous run per CTA of equal modelled
+        // cost (an output plane costs 1 plus NL_COST per nonlocal block of its
+        // heaviest patch, an edge plane a quarter), a unit split at a plane
+        // where a run ends.
         const int G = std::max(1, n_sm);
-        std::vector<std::vector<UnitDev>> per(G);
-        std::vector<double> load(G, 0.0);
+        struct Piece {
+            int zmin, zmax, zo0, zo1;
+            int64_t pz;
+        };
+        std::vector<Piece> seq;
         const int nslab = (d0 + slab - 1) / slab;
-        for (int s = 0; s < nslab; ++s) {
-            std::vector<std::pair<double, UnitDev>> us;
+        for (int sl = 0; sl < nslab; ++sl)
             for (const Col &cl : cols) {
-                const int zo0 = std::max(cl.zmin, s * slab), zo1 = std::min(cl.zmax + 1, (s + 1) * slab);
-                if (zo0 >= zo1) continue;
-                UnitDev u{};
-                u.zo0 = zo0;
-                u.zo1 = zo1;
-                u.zm0 = std::max(cl.zmin, zo0 - 4);
-                u.zm1 = std::min(cl.zmax, zo1 + 3);
-                const int64_t pz = cl.p0 - cl.zmin;
-                if (pz < INT32_MIN || pz > INT32_MAX) return RS_OK;
-                u.pz = (int)pz;
-                double cost = 0.25 * ((u.zm1 - u.zm0 + 1) - (zo1 - zo0));
-                for (int z = zo0; z < zo1; ++z) cost += pcost[(size_t)(pz + z)];
-                us.push_back({cost, u});
+                const int zo0 = std::max(cl.zmin, sl * slab), zo1 = std::min(cl.zmax + 1, (sl + 1) * slab);
+                if (zo0 < zo1) seq.push_back({cl.zmin, cl.zmax, zo0, zo1, cl.p0 - cl.zmin});
             }
-            std::stable_sort(us.begin(), us.end(), [](const std::pair<double, UnitDev> &x, const std::pair<double, UnitDev> &y) {
-                return x.first > y.first;
-            });
-            for (const auto &cu : us) {
-                const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-                per[k].push_back(cu.second);
-                load[k] += cu.first;
-            }
+        auto edges = [](const Piece &u, int a, int b) {   // edge planes of output planes [a, b)
+            return 0.25 * ((a - std::max(u.zmin, a - 4)) + (std::min(u.zmax, b + 3) - b + 1));
+        };
+        double total = 0;
+        for (const Piece &u : seq) {
+            total += edges(u, u.zo0, u.zo1);
+            for (int z = u.zo0; z < u.zo1; ++z) total += pcost[(size_t)(u.pz + z)];
         }
+        // Greedy fill of runs up to a cost T (a run takes whole planes while
+        // it stays within T; a plane that fits no run alone opens one); the
+        // smallest T that needs at most G runs, by bisection.
+        std::vector<std::vector<UnitDev>> per;
+        auto fill = [&](double T, bool keep) -> int {
+            if (keep) per.assign(1, {});
+            int runs = 1;
+            double load = 0;
+            for (const Piece &u : seq) {
+                int a = u.zo0;
+                while (a < u.zo1) {
+                    double c = edges(u, a, a + 1) + pcost[(size_t)(u.pz + a)];
+                    if (load > 0 && load + c > T) {
+                        ++runs;
+                        if (keep) per.emplace_back();
+                        load = 0;
+                        continue;
+                    }
+                    int b = a + 1;
+                    while (b < u.zo1) {
+                        const double nc = c - edges(u, a, b) + edges(u, a, b + 1) + pcost[(size_t)(u.pz + b)];
+                        if (load + nc > T) break;
+                        c = nc;
+                        ++b;
+                    }
+                    if (keep) {
+                        UnitDev d{};
+                        d.zo0 = a;
+                        d.zo1 = b;
+                        d.zm0 = std::max(u.zmin, a - 4);
+                        d.zm1 = std::min(u.zmax, b + 3);
+                        d.pz = (int)u.pz;
+                        per.back().push_back(d);
+                    }
+                    load += c;
+                    a = b;
+                    if (a < u.zo1) {
+                        ++runs;
+                        if (keep) per.emplace_back();
+                        load = 0;
+                    }
+                }
+            }
+            return runs;
+        };
+        for (const Piece &u : seq)
+            if (u.pz < INT32_MIN || u.pz > INT32_MAX) return RS_OK;
+        double lo = total / G, hi = 2.0 * total / G + 16.0;
+        for (int i = 0; i < 50; ++i) {
+            const double mid = 0.5 * (lo + hi);
+            if (fill(mid, false) <= G) hi = mid;
+            else lo = mid;
+        }
+        fill(hi, true);
+        if ((int)per.size() > G) return RS_OK;
+        per.resize(G);
         // per CTA: the atoms its records name, renumbered in the records to
         // the CTA's local order (a record belongs to the one unit whose
         // output planes hold it)

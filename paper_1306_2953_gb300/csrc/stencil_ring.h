@@ -15,12 +15,13 @@ struct RingPlan;
 
 // Builds the kernel's tables from the host grid, the point-major nonlocal
 // tables (coff [npts+1], catom / cg32 [entries] with four projector values
-// per entry), the FP32 potential, the number of atoms and the z-slab height
+// per entry), the FP32 potential, the FP32 centre weight of the star, the
+// number of atoms and the z-slab height
 // of a work unit.  Returns RS_OK with *out == nullptr when the grid cannot
 // use the kernel (2^28 points or more, a plane record or a CTA's unit list
 // above the shared-memory budget).
 int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t> &coff, const std::vector<int32_t> &catom,
-                    const std::vector<float> &cg32, const std::vector<float> &v32, int n_atoms, int slab);
+                    const std::vector<float> &cg32, const std::vector<float> &v32, float w0, int n_atoms, int slab);
 void ring_plan_destroy(RingPlan *p);
 
 // True when the kernel takes this block: nb a multiple of 32 and 16-byte
