@@ -71,19 +71,12 @@ constexpr double NL_COST = 0.13;
 constexpr int AHEAD = 2;                   // planes in flight ahead of the one computed
 constexpr int MAX_RING = 4;                // slots per CTA (4, or 3 when 4 do not fit)
 constexpr int NPOS = TX * TY;
-// record: [patch headers {blocks, byte offset}] [potential, tile row-major]
+// record: [patch headers {blocks, byte offset}] [w0 + potential, as pairs, tile row-major]
 // [point index, tile row-major] [blocks: {atom} + projector values [16][4]]
-#ifndef RS_RING_VW0
-#define RS_RING_VW0 0
-#endif
-#ifndef RS_RING_GDUP
-#define RS_RING_GDUP 0
-#endif
-constexpr int REC_V = 128;
-constexpr int REC_IDX = REC_V + NPOS * (RS_RING_VW0 ? 8 : 4);
+constexpr int REC_V = 128;                 // [point] (w0 + V, w0 + V): the star's centre weight plus the potential
+constexpr int REC_IDX = REC_V + NPOS * 8;
 constexpr int REC_BLK = REC_IDX + NPOS * 4;
-constexpr int GW = RS_RING_GDUP ? 8 : 4;   // floats per point in a block
-constexpr int BLK = 16 + 16 * GW * 4;
+constexpr int BLK = 16 + 16 * 16;
 constexpr int MAX_REC = 48 * 1024;         // record slot budget (bytes)
 constexpr size_t MAX_SMEM = 226 * 1024;    // dynamic shared memory per CTA (227 KB less the static part)
 constexpr int MAX_SLAB = 1 << 16;          // planes per z-slab (at most)
@@ -178,7 +171,6 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 // a slot's start.
 struct Lane {
     float2 W1, W2, W3, W4;
-    float w0;
     int cb;        // centre of patch row 0, column 0 (window row 4 + ty0)
     int lb0, lb1;  // first of the four axis-2 neighbours left of rows 0 / 1
     int rb0, rb1;  // first of the four right of rows 0 / 1
@@ -195,7 +187,6 @@ constexpr int PS = ROWB / 8;
 __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc)[2][4], const float2 *__restrict__ P,
                                             const unsigned char *__restrict__ rs, const float2 *__restrict__ cs,
                                             const Lane &c) {
-#if RS_RING_VW0
     const float4 *V4 = reinterpret_cast<const float4 *>(rs + REC_V) + (c.to >> 1);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -205,17 +196,6 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
         T[r][2] = make_float2(v23.x, v23.y) * cc[r][2];
         T[r][3] = make_float2(v23.z, v23.w) * cc[r][3];
     }
-#else
-    const float4 *V4 = reinterpret_cast<const float4 *>(rs + REC_V) + (c.to >> 2);
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const float4 v = V4[r * (TX / 4)];
-        T[r][0] = f2(c.w0 + v.x) * cc[r][0];
-        T[r][1] = f2(c.w0 + v.y) * cc[r][1];
-        T[r][2] = f2(c.w0 + v.z) * cc[r][2];
-        T[r][3] = f2(c.w0 + v.w) * cc[r][3];
-    }
-#endif
     // axis-2 neighbours: the four left and right of each patch row
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -258,21 +238,6 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
     for (int k = 0; k < hd.x; ++k, blk += BLK) {
         const float2 *cq = cs + *reinterpret_cast<const int *>(blk) * (4 * SG / 2) + c.sl;
         const float2 c0 = cq[0], c1 = cq[SG / 2], c2 = cq[SG], c3 = cq[3 * SG / 2];
-#if RS_RING_GDUP
-        const float4 *g = reinterpret_cast<const float4 *>(blk + 16) + 16 * c.h;
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const float4 g01 = g[2 * (r * 4 + x)], g23 = g[2 * (r * 4 + x) + 1];
-                float2 a = T[r][x];
-                a = fma2(make_float2(g01.x, g01.y), c0, a);
-                a = fma2(make_float2(g01.z, g01.w), c1, a);
-                a = fma2(make_float2(g23.x, g23.y), c2, a);
-                a = fma2(make_float2(g23.z, g23.w), c3, a);
-                T[r][x] = a;
-            }
-#else
         const float4 *g = reinterpret_cast<const float4 *>(blk + 16) + 8 * c.h;
 #pragma unroll
         for (int r = 0; r < 2; ++r)
@@ -286,7 +251,6 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
                 a = fma2(f2(gv.w), c3, a);
                 T[r][x] = a;
             }
-#endif
     }
 }
 
@@ -452,7 +416,6 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
     };
 
     Lane c;
-    c.w0 = a.w[0];
     c.W1 = f2(a.w[1]);
     c.W2 = f2(a.w[2]);
     c.W3 = f2(a.w[3]);
@@ -552,7 +515,6 @@ void ring_plan_destroy(RingPlan *p) { delete p; }
 
 int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t> &coff, const std::vector<int32_t> &catom,
                     const std::vector<float> &cg32, const std::vector<float> &v32, float w0, int n_atoms, int slab) {
-    (void)w0;
     (void)n_atoms;
     *out = nullptr;
     if (g->npts >= (1 << 28) || slab < 1 || slab > MAX_SLAB) return RS_OK;
@@ -610,18 +572,14 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                     }
                     // record of plane z
                     const size_t off = blob.size();
-                    std::vector<int32_t> hdr(REC_V / 4, 0), vv(NPOS * (RS_RING_VW0 ? 2 : 1), 0), ii(NPOS, -1), blocks;
+                    std::vector<int32_t> hdr(REC_V / 4, 0), vv(2 * NPOS, 0), ii(NPOS, -1), blocks;
                     for (int iy = 0; iy < TY; ++iy)
                         for (int ix = 0; ix < TX; ++ix) {
                             const int32_t m = at(z, b1 + iy, b2 + ix);
                             if (m < 0) continue;
-#if RS_RING_VW0
                             // the centre weight plus the potential, as the kernel would add them
                             const float vw = w0 + v32[m];
                             vv[2 * (iy * TX + ix)] = vv[2 * (iy * TX + ix) + 1] = word(vw);
-#else
-                            vv[iy * TX + ix] = word(v32[m]);
-#endif
                             ii[iy * TX + ix] = m;
                         }
                     for (int w = 0; w < NW; ++w) {
@@ -634,10 +592,8 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                                 if (m < 0) continue;
                                 for (int e = coff[m]; e < coff[m + 1]; ++e) {
                                     std::vector<float> &gv = per_atom[catom[e]];
-                                    if (gv.empty()) gv.assign(16 * GW, 0.f);
-                                    for (int q = 0; q < 4; ++q)
-                                        for (int u = 0; u < GW / 4; ++u)
-                                            gv[(rr * 4 + xx) * GW + q * (GW / 4) + u] = cg32[(size_t)e * 4 + q];
+                                    if (gv.empty()) gv.assign(64, 0.f);
+                                    for (int q = 0; q < 4; ++q) gv[(rr * 4 + xx) * 4 + q] = cg32[(size_t)e * 4 + q];
                                 }
                             }
                         hdr[2 * w] = (int32_t)per_atom.size();
