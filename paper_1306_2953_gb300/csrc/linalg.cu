@@ -534,6 +534,34 @@ __device__ __forceinline__ void circle_pair(int r, int k, int m, int &p, int &q)
     }
 }
 
+// Jacobi rotation (c, s) that zeroes a_pq of the 2 x 2 block [[app, apq],
+// [apq, aqq]]: t = tan(theta) is the smaller root of t^2 + 2 tau t - 1 = 0,
+// tau = (aqq - app) / (2 apq), written t = sign(tau) |2 apq| /
+// (|aqq - app| + sqrt((aqq - app)^2 + (2 apq)^2)) (one square root and one
+// division on the dependent path), c = 1 / sqrt(1 + t^2) by the reciprocal
+// square root with one Newton step, s = t c.  An off-diagonal entry whose
+// square underflows is left alone.
+template <typename T> __device__ __forceinline__ void jacobi_cs(T app, T aqq, T apq, T &c, T &s) {
+    c = T(1);
+    s = T(0);
+    const T d = aqq - app, a2 = T(2) * apq;
+    // an entry whose square underflows is below any rounding of the block:
+    // no rotation (and no 0 / 0 when the diagonal entries are equal)
+    if (!(a2 * a2 > T(0))) return;
+    T t = fabs(a2) / (fabs(d) + sqrt(d * d + a2 * a2));
+    if ((d < T(0)) != (a2 < T(0))) t = -t;   // sign(tau) = sign(d) sign(apq)
+    const T x = T(1) + t * t;
+    T r;
+    if constexpr (sizeof(T) == 4) {
+        r = rsqrtf(x);
+        r = r * (1.5f - 0.5f * x * r * r);
+    } else {
+        r = T(1) / sqrt(x);
+    }
+    c = r;
+    s = t * r;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_jacobi_pk(const double *__restrict__ Ag, int lda, int n, int max_sweeps,
                                                     double tol, T *__restrict__ rot, double *__restrict__ w,
@@ -550,10 +578,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_pk(const double *__restrict__ A
     __shared__ double red[32];
     __shared__ double fro2, off2;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    __shared__ double shift;
     for (int i = tid; i < n; i += nt) ro[i] = i * (2 * n - i - 1) / 2;
-    __syncthreads();
-    for (int i = warp; i < n; i += nw)
-        for (int j = i + lane; j < n; j += 32) a[ro[i] + j] = (T)Ag[(int64_t)i * lda + j];
     auto block_sum = [&](double v) -> double {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         __syncthreads();
@@ -566,6 +592,20 @@ __global__ void __launch_bounds__(1024) k_jacobi_pk(const double *__restrict__ A
         }
         return t;  // valid in thread 0
     };
+    // FP32: rotate A - sigma I, sigma the mean of the diagonal (the same
+    // eigenvectors), so that the rounding of the rotations and the stopping
+    // test scale with the spread of the spectrum rather than its offset
+    {
+        double d = 0;
+        if constexpr (sizeof(T) == 4)
+            for (int i = tid; i < n; i += nt) d += Ag[(int64_t)i * lda + i];
+        const double t = block_sum(d);
+        if (tid == 0) shift = t / n;
+    }
+    __syncthreads();
+    for (int i = warp; i < n; i += nw)
+        for (int j = i + lane; j < n; j += 32)
+            a[ro[i] + j] = (T)(j == i ? Ag[(int64_t)i * lda + j] - shift : Ag[(int64_t)i * lda + j]);
     __syncthreads();
     {
         double d = 0, o = 0;
@@ -599,14 +639,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_pk(const double *__restrict__ A
                 int p, q;
                 circle_pair(r, k, m, p, q);
                 const int lo = min(p, q), hi = max(p, q);
-                const T apq = a[ro[lo] + hi];
-                T c = 1, s_ = 0;
-                if (apq != T(0)) {
-                    const T theta = (a[ro[q] + q] - a[ro[p] + p]) / (T(2) * apq);
-                    const T tt = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-                    c = T(1) / sqrt(tt * tt + T(1));
-                    s_ = tt * c;
-                }
+                T c, s_;
+                jacobi_cs(a[ro[p] + p], a[ro[q] + q], a[ro[lo] + hi], c, s_);
                 cs[k] = c;
                 sn[k] = s_;
                 pp[k] = p;
@@ -655,7 +689,133 @@ __global__ void __launch_bounds__(1024) k_jacobi_pk(const double *__restrict__ A
             rk += (dj < di) || (dj == di && j < i);
         }
         perm[i] = rk;
-        w[rk] = (double)di;
+        w[rk] = (double)di + shift;
+    }
+    if (tid == 0) info[0] = done ? sweep : -1;
+}
+
+// Single-CTA cyclic Jacobi for FP32 with the full matrix in shared memory
+// (row stride n + 1, so that a warp's accesses along a row and down a column
+// fall in distinct banks), for orders whose full matrix fits.  Same circle
+// ordering, rotation log, eigenvalue order and outputs as k_jacobi_pk; a
+// round applies the h disjoint rotations as J^T A (rows p, q of every pair,
+// all columns) and then A J (columns p, q, all rows), one warp per pair.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_jacobi_full(const double *__restrict__ Ag, int lda, int n, int max_sweeps,
+                                                      double tol, T *__restrict__ rot, double *__restrict__ w,
+                                                      int *__restrict__ perm, int *__restrict__ info) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int h = n / 2, m = n - 1, ld = n + 1;
+    T *cs = reinterpret_cast<T *>(smraw);
+    T *sn = cs + h;
+    int *pp = reinterpret_cast<int *>(sn + h);
+    int *qq = pp + h;
+    T *a = reinterpret_cast<T *>(qq + h);
+    __shared__ double red[32];
+    __shared__ double fro2, off2, shift;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        double t = 0;
+        if (tid < 32) {
+            t = tid < nw ? red[tid] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        }
+        return t;  // valid in thread 0
+    };
+    // rotate A - sigma I, sigma the mean of the diagonal (see k_jacobi_pk)
+    {
+        double d = 0;
+        for (int i = tid; i < n; i += nt) d += Ag[(int64_t)i * lda + i];
+        const double t = block_sum(d);
+        if (tid == 0) shift = t / n;
+    }
+    __syncthreads();
+    for (int i = warp; i < n; i += nw)
+        for (int j = lane; j < n; j += 32)
+            a[i * ld + j] = (T)(j == i ? Ag[(int64_t)i * lda + j] - shift : Ag[(int64_t)i * lda + j]);
+    __syncthreads();
+    {
+        double f = 0;
+        for (int i = warp; i < n; i += nw)
+            for (int j = lane; j < n; j += 32) {
+                const double x = (double)a[i * ld + j];
+                f += x * x;
+            }
+        const double t = block_sum(f);
+        if (tid == 0) fro2 = t;
+    }
+    __syncthreads();
+    int sweep = 0, done = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double o = 0;
+        for (int i = warp; i < n; i += nw)
+            for (int j = lane; j < n; j += 32)
+                if (j != i) {
+                    const double x = (double)a[i * ld + j];
+                    o += x * x;
+                }
+        const double t = block_sum(o);
+        if (tid == 0) off2 = t;
+        __syncthreads();
+        if (off2 <= tol * tol * fro2) {
+            done = 1;
+            break;
+        }
+        for (int r = 0; r < m; ++r) {
+            for (int k = tid; k < h; k += nt) {
+                int p, q;
+                circle_pair(r, k, m, p, q);
+                T c, s_;
+                jacobi_cs(a[p * ld + p], a[q * ld + q], a[p * ld + q], c, s_);
+                cs[k] = c;
+                sn[k] = s_;
+                pp[k] = p;
+                qq[k] = q;
+                T *lg = rot + 2 * (((int64_t)sweep * m + r) * h + k);
+                lg[0] = c;
+                lg[1] = s_;
+            }
+            __syncthreads();
+            // rows p, q of every pair
+            for (int k = warp; k < h; k += nw) {
+                const int p = pp[k], q = qq[k];
+                const T c = cs[k], s_ = sn[k];
+                T *rp = a + p * ld, *rq = a + q * ld;
+                for (int j = lane; j < n; j += 32) {
+                    const T x = rp[j], y = rq[j];
+                    rp[j] = c * x - s_ * y;
+                    rq[j] = s_ * x + c * y;
+                }
+            }
+            __syncthreads();
+            // columns p, q of every pair; the pair's own off-diagonal entry is zero
+            for (int k = warp; k < h; k += nw) {
+                const int p = pp[k], q = qq[k];
+                const T c = cs[k], s_ = sn[k];
+                for (int j = lane; j < n; j += 32) {
+                    T *rj = a + j * ld;
+                    const T x = rj[p], y = rj[q];
+                    rj[p] = (j == q) ? T(0) : c * x - s_ * y;
+                    rj[q] = (j == p) ? T(0) : s_ * x + c * y;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ascending order (ties by index)
+    for (int i = tid; i < n; i += nt) {
+        const T di = a[i * ld + i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const T dj = a[j * ld + j];
+            rk += (dj < di) || (dj == di && j < i);
+        }
+        perm[i] = rk;
+        w[rk] = (double)di + shift;
     }
     if (tid == 0) info[0] = done ? sweep : -1;
 }
@@ -678,32 +838,43 @@ __global__ void k_jacobi_vacc(const T *__restrict__ rot, int n, int max_sweeps, 
     __syncthreads();
     const int sweeps = info[0] < 0 ? max_sweeps : info[0];
     const int64_t rounds = (int64_t)sweeps * m;
-    T c = 1, s_ = 0;
-    if (tid < h && rounds > 0) {
-        c = rot[2 * tid];
-        s_ = rot[2 * tid + 1];
-    }
-    for (int64_t R = 0; R < rounds; ++R) {
-        T cn = 1, sn_ = 0;
-        if (tid < h && R + 1 < rounds) {
-            const T *lg = rot + 2 * ((R + 1) * h + tid);
-            cn = lg[0];
-            sn_ = lg[1];
-        }
-        if (tid < h) {
-            int p, q;
-            circle_pair((int)(R % m), tid, m, p, q);
+    // the rotations of rounds R .. R + 3 are in flight (log reads hidden
+    // behind three rounds of work)
+    constexpr int PF = 4;
+    T cq[PF], sq[PF];
 #pragma unroll
-            for (int r = 0; r < VACC_RB; ++r) {
-                T *row = v + r * n;
-                const T va = row[p], vb = row[q];
-                row[p] = c * va - s_ * vb;
-                row[q] = s_ * va + c * vb;
-            }
+    for (int i = 0; i < PF; ++i) {
+        cq[i] = 1;
+        sq[i] = 0;
+        if (tid < h && i < rounds) {
+            cq[i] = rot[2 * (i * h + tid)];
+            sq[i] = rot[2 * (i * h + tid) + 1];
         }
-        __syncthreads();
-        c = cn;
-        s_ = sn_;
+    }
+    for (int64_t R0 = 0; R0 < rounds; R0 += PF) {
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int64_t R = R0 + i;
+            if (R >= rounds) break;
+            const T c = cq[i], s_ = sq[i];
+            if (tid < h && R + PF < rounds) {
+                const T *lg = rot + 2 * ((R + PF) * h + tid);
+                cq[i] = lg[0];
+                sq[i] = lg[1];
+            }
+            if (tid < h) {
+                int p, q;
+                circle_pair((int)(R % m), tid, m, p, q);
+#pragma unroll
+                for (int r = 0; r < VACC_RB; ++r) {
+                    T *row = v + r * n;
+                    const T va = row[p], vb = row[q];
+                    row[p] = c * va - s_ * vb;
+                    row[q] = s_ * va + c * vb;
+                }
+            }
+            __syncthreads();
+        }
     }
     for (int e = tid; e < nr * n; e += blockDim.x) {
         const int r = e / n, j = e - r * n;
@@ -717,6 +888,11 @@ size_t jacobi_pk_smem(int n, size_t es) {
     return es * (2 * h + (size_t)n * (n + 1) / 2) + sizeof(int) * ((size_t)n + 2 * h) + 64;
 }
 constexpr size_t JACOBI_PK_MAX_SMEM = 220 * 1024;
+// shared memory of k_jacobi_full (row stride n + 1)
+size_t jacobi_full_smem(int n, size_t es) {
+    const size_t h = n / 2;
+    return es * (2 * h + (size_t)n * (n + 1)) + sizeof(int) * 2 * h + 64;
+}
 // (c, s) entries of the rotation log of up to max_sweeps sweeps
 size_t jacobi_log_elems(int n, int max_sweeps) { return 2 * (size_t)max_sweeps * (n - 1) * (n / 2); }
 
@@ -743,12 +919,22 @@ int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *
         // rotation log and rank array in the scratch
         T *rot = reinterpret_cast<T *>(scratch);
         int *perm = reinterpret_cast<int *>(rot + jacobi_log_elems(n, max_sweeps));
-        static int pk_attr = 0;   // largest dynamic shared memory granted so far (per instantiation)
-        if ((int)pk > pk_attr) {
-            RS_CUDA(cudaFuncSetAttribute(k_jacobi_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk));
-            pk_attr = (int)pk;
+        const size_t fs = jacobi_full_smem(n, sizeof(T));
+        if (sizeof(T) == 4 && fs <= JACOBI_PK_MAX_SMEM) {
+            static int fs_attr = 0;
+            if ((int)fs > fs_attr) {
+                RS_CUDA(cudaFuncSetAttribute(k_jacobi_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+                fs_attr = (int)fs;
+            }
+            k_jacobi_full<T><<<1, 1024, fs, st>>>(A, lda, n, max_sweeps, tol, rot, w, perm, info);
+        } else {
+            static int pk_attr = 0;   // largest dynamic shared memory granted so far (per instantiation)
+            if ((int)pk > pk_attr) {
+                RS_CUDA(cudaFuncSetAttribute(k_jacobi_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk));
+                pk_attr = (int)pk;
+            }
+            k_jacobi_pk<T><<<1, 1024, pk, st>>>(A, lda, n, max_sweeps, tol, rot, w, perm, info);
         }
-        k_jacobi_pk<T><<<1, 1024, pk, st>>>(A, lda, n, max_sweeps, tol, rot, w, perm, info);
         RS_LAUNCH_CHECK();
         const int threads = std::max(32, ((n / 2 + 31) / 32) * 32);
         const size_t vs = (size_t)VACC_RB * n * sizeof(T);
