@@ -214,7 +214,9 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
             for (int x = 0; x < 4; ++x) T[r][x] = fma2(W, add2(v[x + 4 + j], v[x + 4 - j]), T[r][x]);
         }
     }
-    // axis-1 neighbours: window rows ty0 .. ty0 + 9 of each patch column
+    // axis-1 neighbours: window rows ty0 .. ty0 + 9 of each patch column,
+    // summed apart from the rest (shorter dependent chains) and added at the end
+    float2 Ty[2][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
         float2 y[10];
@@ -227,9 +229,15 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
         for (int j = 1; j <= 4; ++j) {
             const float2 W = j == 1 ? c.W1 : j == 2 ? c.W2 : j == 3 ? c.W3 : c.W4;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) T[r][x] = fma2(W, add2(y[r + 4 + j], y[r + 4 - j]), T[r][x]);
+            for (int r = 0; r < 2; ++r)
+                Ty[r][x] = j == 1 ? W * add2(y[r + 4 + j], y[r + 4 - j])
+                                  : fma2(W, add2(y[r + 4 + j], y[r + 4 - j]), Ty[r][x]);
         }
     }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) T[r][x] = add2(T[r][x], Ty[r][x]);
     // nonlocal gather: per atom meeting the patch, the projection
     // coefficients of the lane's two states (staged in shared memory)
     // against the patch's projector values
