@@ -302,6 +302,38 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
     return out
 
 
+def nb_sweep(workload):
+    """H psi throughput against the block size: for nb = 1..64 states and
+    FP32 / FP64, the algorithmic bytes of one block application
+    (rs_ham_apply_bytes) over its CUDA-event time, ψ [npts][64] resident."""
+    import torch
+    from paper_1306_2953_gb300 import _lib
+    g, H = build_system(workload)
+    peak, kind = measured_peaks()
+    out = {"workload": workload.name, "npts": g.npts, "peak_gbs": peak, "peak_source": kind, "rows": []}
+    for dt, code in ((torch.float32, _lib.RS_F32), (torch.float64, _lib.RS_F64)):
+        psi = torch.from_numpy(wl.random_block(g.npts, 64, 5)).to(dt).cuda()
+        hpsi = torch.empty_like(psi)
+        for nb in (1, 2, 4, 8, 16, 32, 64):
+            reps = max(3, min(200, int(2e9 / max(H.apply_bytes(nb, code), 1))))
+            for _ in range(3):
+                H.apply(psi[:, :nb], hpsi[:, :nb], nb=nb)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                H.apply(psi[:, :nb], hpsi[:, :nb], nb=nb)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = H.apply_bytes(nb, code) / (ms * 1e-3) / 1e9
+            out["rows"].append({"dtype": "f32" if code == _lib.RS_F32 else "f64", "nb": nb, "us_per_apply": ms * 1e3,
+                                "gbs": gbs, "frac_of_peak": gbs / peak})
+        del psi, hpsi
+    print(json.dumps(out))
+    return 0
+
+
 def max_over_ranks(value, device):
     """The largest of every rank's value (all ranks call it; the job's time
     is its slowest replica's)."""
@@ -343,6 +375,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eigensolve", default="mol20_h0.35,mol100_h0.3",
                     help="workload(s) for the time-to-1e-6 Ha eigensolve, comma separated, or 'none'")
+    ap.add_argument("--nb-sweep", action="store_true",
+                    help="print H psi GB/s of algorithmic bytes for blocks of 1..64 states (FP32 and FP64) on "
+                         "--workload and exit (no benchmark line)")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling aid: run this many mixed-precision eigensolver sweeps on --workload, "
                          "print their times and exit (no benchmark line)")
@@ -352,6 +387,8 @@ def main():
         return run_reference(args, workload)
     if args.profile_sweeps > 0:
         return profile_sweeps(workload, args.profile_sweeps)
+    if args.nb_sweep:
+        return nb_sweep(workload)
 
     import torch
     import torch.distributed as dist
