@@ -168,10 +168,13 @@ def run_reference(args, workload):
     return 0
 
 
-def profiled_traffic():
+def profiled_traffic(workload_name):
     """DRAM bytes (read + write) per launch of the H psi kernel from the
-    committed ncu summary, or None when the kernel source has changed since
-    that capture (the summary records the source's SHA-1)."""
+    committed ncu summary of the 100-atom workload, or None for another
+    workload or when the kernel source has changed since that capture (the
+    summary records the source's SHA-1)."""
+    if workload_name != wl.MOL100.name:
+        return None
     import hashlib
     prof = os.path.join(ROOT, "profiles", "k_hpsi_ring_mol100.md")
     src = os.path.join(ROOT, "paper_1306_2953_gb300", "csrc", "stencil_ring.cu")
@@ -495,11 +498,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload.name, "npts": npts, "states": nst, "block": NB,
-                       "psi_bytes": psi.numel() * 4, "l2": "inputs (psi, 0.73 GB) larger than L2 (129 MB)",
+                       "psi_bytes": psi.numel() * 4,
+                       "l2": f"inputs (psi, {psi.numel() * 4 / 1e9:.2f} GB) larger than L2 (129 MB)",
                        "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "kernel": "k_hpsi_ring (fused stencil + V + nonlocal gather)",
                          "achieved": stencil_gbs, "peak": peak, "unit": "GB/s", "frac": stencil_gbs / peak,
-                         "peak_source": peak_kind, "traffic": profiled_traffic(),
+                         "peak_source": peak_kind, "traffic": profiled_traffic(workload.name),
                          "algorithmic_bytes_per_launch": sb.value,
                          "stencil_ms_per_launch": sms.value / max(ncalls.value, 1),
                          "project_ms_per_launch": pms.value / max(ncalls.value, 1)},
