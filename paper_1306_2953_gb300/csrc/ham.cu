@@ -150,6 +150,10 @@ __global__ void __launch_bounds__(NT) k_project(HamDev<T> d, const T *__restrict
     }
 }
 
+#ifndef RS_PROJ_CTAS
+#define RS_PROJ_CTAS 5
+#endif
+
 // FP32 blocks of 32-state groups: lane l of a warp takes sphere entry
 // l / 8 of the warp's four and the states 4 (l % 8) .. + 3 (one 16-byte
 // load of the psi row), so a warp reads four psi rows per step; the grid is
@@ -705,8 +709,8 @@ static int apply_t(rs_ham *H, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, i
         bool done = false;
         if constexpr (sizeof(T) == 4) {
             if (nb % 32 == 0 && ldp % 4 == 0 && aligned16(psi)) {
-                // about eight CTAs of 256 threads per SM
-                const int split = std::max(1, std::min(64, (8 * H->n_sm + H->n_atoms - 1) / H->n_atoms));
+                // one wave: at most RS_PROJ_CTAS CTAs of 256 threads per SM in all
+                const int split = std::max(1, std::min(64, RS_PROJ_CTAS * H->n_sm / H->n_atoms));
                 k_project_f32<<<dim3((unsigned)(H->n_atoms * split), (unsigned)(nb / 32)), NTP4, 0, st>>>(d, psi, ldp, nb,
                                                                                                         split, cp);
                 done = true;

@@ -240,7 +240,8 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
         for (int x = 0; x < 4; ++x) T[r][x] = add2(T[r][x], Ty[r][x]);
     // nonlocal gather: per atom meeting the patch, the projection
     // coefficients of the lane's two states (staged in shared memory)
-    // against the patch's projector values
+    // against the patch's projector values (scalar FMAs: a projector value
+    // multiplies both states without being paired with itself first)
     const int2 hd = reinterpret_cast<const int2 *>(rs)[c.w];
     const unsigned char *blk = rs + hd.y;
     for (int k = 0; k < hd.x; ++k, blk += BLK) {
@@ -253,10 +254,14 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
             for (int x = 0; x < 4; ++x) {
                 const float4 gv = g[r * 4 + x];
                 float2 a = T[r][x];
-                a = fma2(f2(gv.x), c0, a);
-                a = fma2(f2(gv.y), c1, a);
-                a = fma2(f2(gv.z), c2, a);
-                a = fma2(f2(gv.w), c3, a);
+                a.x = __fmaf_rn(gv.x, c0.x, a.x);
+                a.y = __fmaf_rn(gv.x, c0.y, a.y);
+                a.x = __fmaf_rn(gv.y, c1.x, a.x);
+                a.y = __fmaf_rn(gv.y, c1.y, a.y);
+                a.x = __fmaf_rn(gv.z, c2.x, a.x);
+                a.y = __fmaf_rn(gv.z, c2.y, a.y);
+                a.x = __fmaf_rn(gv.w, c3.x, a.x);
+                a.y = __fmaf_rn(gv.w, c3.y, a.y);
                 T[r][x] = a;
             }
     }
