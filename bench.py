@@ -353,18 +353,27 @@ def replica_throughput(world, bytes_per_step, steps, ms_max):
     return world * bytes_per_step * steps / (ms_max * 1e-3) / 1e9
 
 
-def profile_sweeps(workload, n):
+def profile_sweeps(workload, n, precision="f32"):
+    """Solver creation and n eigensolver sweeps (filter preconditioner) in
+    FP32 (mixed: FP32 orbitals, FP64 subspace steps) or FP64, one JSON line
+    per sweep with its wall time and largest residual."""
     import torch
     from paper_1306_2953_gb300 import api
     g, H = build_system(workload)
-    psi0 = torch.from_numpy(wl.random_block(g.npts, workload.n_states, workload.seed)).float().cuda()
+    dt = torch.float64 if precision == "f64" else torch.float32
+    psi0 = torch.from_numpy(wl.random_block(g.npts, workload.n_states, workload.seed)).to(dt).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     S = api.Solver(H, psi0, workload.block, 1e-4)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": workload.name, "precision": precision, "npts": g.npts, "states": workload.n_states,
+                      "solver_create_seconds": time.perf_counter() - t0}))
     for _ in range(n):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S.step()
+        _, res, _ = S.step()
         torch.cuda.synchronize()
-        print(json.dumps({"sweep_seconds": time.perf_counter() - t0}))
+        print(json.dumps({"sweep_seconds": time.perf_counter() - t0, "max_residual": float(res.max())}))
     return 0
 
 
@@ -381,6 +390,8 @@ def main():
     ap.add_argument("--nb-sweep", action="store_true",
                     help="print H psi GB/s of algorithmic bytes for blocks of 1..64 states (FP32 and FP64) on "
                          "--workload and exit (no benchmark line)")
+    ap.add_argument("--sweep-precision", default="f32", choices=["f32", "f64"],
+                    help="precision of the --profile-sweeps solver")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling aid: run this many mixed-precision eigensolver sweeps on --workload, "
                          "print their times and exit (no benchmark line)")
@@ -389,7 +400,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, workload)
     if args.profile_sweeps > 0:
-        return profile_sweeps(workload, args.profile_sweeps)
+        return profile_sweeps(workload, args.profile_sweeps, args.sweep_precision)
     if args.nb_sweep:
         return nb_sweep(workload)
 
