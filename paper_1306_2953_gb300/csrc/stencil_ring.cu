@@ -39,7 +39,7 @@
 // Eight accumulators per point hold the outputs z - 4 .. z + 3 (slot z mod 8,
 // addressed through unrolling): at step z output z - 4 is complete and
 // written, and its slot takes output z + 4.  The four planes on either side
-// of a slab contribute only their z-terms (tile rows only, no record).
+// of a unit contribute only their z-terms (tile rows only, no record).
 //
 // Every mbarrier wait is bounded; on a timeout the kernel sets its status
 // word and leaves the march.
@@ -66,8 +66,10 @@ constexpr int NW = 8;                      // warps: one 4 x 4 patch each
 constexpr int NT = NW * 32;
 constexpr int CPW = NG / NW;               // brick rows copied per warp and plane
 
-// march cost of one atom block of a patch, in planes (host load balance)
-constexpr double NL_COST = 0.13;
+// host load balance: march cost of an edge plane and of one atom block of a
+// plane's heaviest patch, in full planes (fitted to per-CTA clock counts)
+constexpr double EDGE_COST = 0.38;
+constexpr double NL_COST = 0.09;
 constexpr int AHEAD = 2;                   // planes in flight ahead of the one computed
 constexpr int MAX_RING = 4;                // slots per CTA (4, or 3 when 4 do not fit)
 constexpr int NPOS = TX * TY;
@@ -641,7 +643,7 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
         // Units slab by slab, columns in raster order within a slab; the
         // sequence is cut into one contiguous run per CTA of equal modelled
         // cost (an output plane costs 1 plus NL_COST per nonlocal block of its
-        // heaviest patch, an edge plane a quarter), a unit split at a plane
+        // heaviest patch, an edge plane EDGE_COST), a unit split at a plane
         // where a run ends.
         const int G = std::max(1, n_sm);
         struct Piece {
@@ -656,7 +658,7 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                 if (zo0 < zo1) seq.push_back({cl.zmin, cl.zmax, zo0, zo1, cl.p0 - cl.zmin});
             }
         auto edges = [](const Piece &u, int a, int b) {   // edge planes of output planes [a, b)
-            return 0.25 * ((a - std::max(u.zmin, a - 4)) + (std::min(u.zmax, b + 3) - b + 1));
+            return EDGE_COST * ((a - std::max(u.zmin, a - 4)) + (std::min(u.zmax, b + 3) - b + 1));
         };
         double total = 0;
         for (const Piece &u : seq) {
