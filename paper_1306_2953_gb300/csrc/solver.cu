@@ -144,8 +144,9 @@ struct rs_solver {
     double dV = 0;
     int es = 8;
     int nblk = 0;
-    DevBuf psi, hpsi, P, Z, HZ, R, small, la, eig, res, tcbuf, psi64, hpsi64, rr64;
+    DevBuf psi, hpsi, P, Z, HZ, R, small, la, eig, res, tcbuf, psi64, hpsi64, rr64, gs_tbuf, gs_nbuf;
     TcWork tc;
+    UmmaSplitCache gs_t, gs_n;   // FP32 mode: splits of Psi[:, :(b+1) nb] within a block step
     std::vector<char> has_p;
     Precond *pc = nullptr;
     // small FP64 buffers (inside `small`)
@@ -176,20 +177,23 @@ int copy_cols(int dtype, const void *S, int64_t lds, void *D, int64_t ldd, int n
 // inner-iteration contractions: FP32 mode on the tensor cores (FP32-level
 // accuracy), FP64 mode on the FP64 pipes
 int gram_any(int dtype, const void *X, int64_t ldx, int nx, const void *Y, int64_t ldy, int ny, int64_t npts, double dV,
-             double *S, int64_t lds, cudaStream_t st, const TcWork &tc) {
+             double *S, int64_t lds, cudaStream_t st, const TcWork &tc, UmmaSplitCache *xcache = nullptr) {
     if (dtype == RS_F64)
         return gram<double>((const double *)X, ldx, nx, (const double *)Y, ldy, ny, npts, dV, S, lds, st);
     if (tc.p && tc.bytes >= umma_work_bytes(nx, ny, npts))
-        return umma_gram((const float *)X, ldx, nx, (const float *)Y, ldy, ny, npts, dV, S, lds, tc.p, tc.err, st);
+        return umma_gram((const float *)X, ldx, nx, (const float *)Y, ldy, ny, npts, dV, S, lds, tc.p, tc.err, st,
+                         xcache);
     return gram<float>((const float *)X, ldx, nx, (const float *)Y, ldy, ny, npts, dV, S, lds, st, true);
 }
 
 int rowmul_any(int dtype, const void *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, void *Y, int64_t ldy,
-               int64_t npts, double alpha, double beta, cudaStream_t st, const TcWork &tc) {
+               int64_t npts, double alpha, double beta, cudaStream_t st, const TcWork &tc,
+               UmmaSplitCache *xcache = nullptr) {
     if (dtype == RS_F64)
         return rowmul<double>((const double *)X, ldx, n, C, ldc, m, (double *)Y, ldy, npts, alpha, beta, st);
     if (tc.p && tc.bytes >= umma_work_bytes(npts, m, n))
-        return umma_rowmul((const float *)X, ldx, n, C, ldc, m, (float *)Y, ldy, npts, alpha, beta, tc.p, tc.err, st);
+        return umma_rowmul((const float *)X, ldx, n, C, ldc, m, (float *)Y, ldy, npts, alpha, beta, tc.p, tc.err, st,
+                           xcache);
     return rowmul<float>((const float *)X, ldx, n, C, ldc, m, (float *)Y, ldy, npts, alpha, beta, st);
 }
 
@@ -240,10 +244,13 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
     void *Y = offw(S->Z, nb, es);
 
     // 3. classical Gram-Schmidt, twice, against Psi[:, :(b+1) nb]
+    // (Psi does not change between the passes: its two BF16x3 splits, one per
+    // contraction layout, are made in the first pass and reused in the second)
     const int nq = (b + 1) * nb;
+    S->gs_t.valid = S->gs_n.valid = false;
     for (int pass = 0; pass < 2; ++pass) {
-        RS_TRY(gram_any(dt, S->psi.p, nst, nq, Y, ldz, ny, np, S->dV, S->M, ny, st, S->tc));
-        RS_TRY(rowmul_any(dt, S->psi.p, nst, nq, S->M, ny, ny, Y, ldz, np, -1.0, 1.0, st, S->tc));
+        RS_TRY(gram_any(dt, S->psi.p, nst, nq, Y, ldz, ny, np, S->dV, S->M, ny, st, S->tc, &S->gs_t));
+        RS_TRY(rowmul_any(dt, S->psi.p, nst, nq, S->M, ny, ny, Y, ldz, np, -1.0, 1.0, st, S->tc, &S->gs_n));
     }
     RS_TRY(coldots(dt, Y, ldz, Y, ldz, ny, np, nrm, st));
     if (dt == RS_F64)
@@ -331,6 +338,11 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
                                        umma_work_bytes(3 * c.nb, 3 * c.nb, S->npts),
                                        umma_work_bytes(c.nst, c.nst, S->npts)});
         if ((rc = S->tcbuf.alloc((size_t)need + 256))) return bail(rc);
+        // the Gram-Schmidt splits of Psi, one per contraction layout
+        if ((rc = S->gs_tbuf.alloc((size_t)umma_split_cache_bytes(true, S->npts, c.nst)))) return bail(rc);
+        if ((rc = S->gs_nbuf.alloc((size_t)umma_split_cache_bytes(false, S->npts, c.nst)))) return bail(rc);
+        S->gs_t.buf = S->gs_tbuf.p;
+        S->gs_n.buf = S->gs_nbuf.p;
         S->tc.p = S->tcbuf.p;
         S->tc.bytes = need;
         S->tc.err = reinterpret_cast<int *>((char *)S->tcbuf.p + need);

@@ -362,18 +362,41 @@ int64_t umma_work_bytes(int64_t rows_a, int64_t rows_b, int64_t K) {
 }
 
 // S (nx x ny, FP64, lds) = dV X^T Y for FP32 X [npts][ldx], Y [npts][ldy].
+int64_t umma_split_cache_bytes(bool gram, int64_t npts, int64_t ncols) {
+    return gram ? 3 * round_up(ncols, UM_BM) * round_up(npts, UM_BK) * 2 : 3 * round_up(npts, UM_BM) * round_up(ncols, UM_BK) * 2;
+}
+
+namespace {
+bool cache_hit(const UmmaSplitCache *c, const float *X, int n, int64_t ld, int64_t rows) {
+    return c && c->buf && c->valid && c->src == X && c->n == n && c->ld == ld && c->rows == rows;
+}
+void cache_set(UmmaSplitCache *c, const float *X, int n, int64_t ld, int64_t rows) {
+    if (!c || !c->buf) return;
+    c->src = X;
+    c->n = n;
+    c->ld = ld;
+    c->rows = rows;
+    c->valid = true;
+}
+}  // namespace
+
 int umma_gram(const float *X, int64_t ldx, int nx, const float *Y, int64_t ldy, int ny, int64_t npts, double dV,
-              double *S, int64_t lds, void *work, int *err, cudaStream_t st) {
+              double *S, int64_t lds, void *work, int *err, cudaStream_t st, UmmaSplitCache *xcache) {
     const int64_t Kp = round_up(npts, UM_BK);
     if (Kp > INT32_MAX / 2) return fail(RS_EINVAL, "umma_gram: too many points");
     const int BN = ny <= 64 ? 64 : 128;
-    __nv_bfloat16 *PA = reinterpret_cast<__nv_bfloat16 *>(work);
-    __nv_bfloat16 *PB = PA + 3 * round_up(nx, UM_BM) * Kp;
+    const bool cached = xcache && xcache->buf;
+    __nv_bfloat16 *PA = reinterpret_cast<__nv_bfloat16 *>(cached ? xcache->buf : work);
+    __nv_bfloat16 *PB = cached ? reinterpret_cast<__nv_bfloat16 *>(work) : PA + 3 * round_up(nx, UM_BM) * Kp;
     dim3 tb(32, 8);
     // S = X^T X: one split serves both operands
     const bool same = X == Y && ldx == ldy && nx == ny;
     if (same) PB = PA;
-    k_split_t<float><<<dim3((unsigned)(Kp / 32), (unsigned)((nx + 31) / 32)), tb, 0, st>>>(X, ldx, (int)npts, nx, (int)Kp, PA);
+    if (!cache_hit(xcache, X, nx, ldx, npts)) {
+        k_split_t<float><<<dim3((unsigned)(Kp / 32), (unsigned)((nx + 31) / 32)), tb, 0, st>>>(X, ldx, (int)npts, nx,
+                                                                                             (int)Kp, PA);
+        cache_set(xcache, X, nx, ldx, npts);
+    }
     if (!same)
         k_split_t<float><<<dim3((unsigned)(Kp / 32), (unsigned)((ny + 31) / 32)), tb, 0, st>>>(Y, ldy, (int)npts, ny, (int)Kp,
                                                                                              PB);
@@ -405,12 +428,17 @@ int umma_gram(const float *X, int64_t ldx, int nx, const float *Y, int64_t ldy, 
 // Y (FP32, [npts][ldy], m columns) = alpha X C + beta Y, X FP32 [npts][ldx]
 // (n columns), C FP64 [n][ldc].  Y must not alias X.
 int umma_rowmul(const float *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, float *Y, int64_t ldy,
-                int64_t npts, double alpha, double beta, void *work, int *err, cudaStream_t st) {
+                int64_t npts, double alpha, double beta, void *work, int *err, cudaStream_t st,
+                UmmaSplitCache *xcache) {
     const int64_t Kp = round_up(n, UM_BK);
     const int BN = m <= 64 ? 64 : 128;
-    __nv_bfloat16 *PA = reinterpret_cast<__nv_bfloat16 *>(work);
-    __nv_bfloat16 *PB = PA + 3 * round_up(npts, UM_BM) * Kp;
-    k_split_n<float><<<2048, dim3(64, 4), 0, st>>>(X, ldx, (int)npts, n, (int)Kp, PA);
+    const bool cached = xcache && xcache->buf;
+    __nv_bfloat16 *PA = reinterpret_cast<__nv_bfloat16 *>(cached ? xcache->buf : work);
+    __nv_bfloat16 *PB = cached ? reinterpret_cast<__nv_bfloat16 *>(work) : PA + 3 * round_up(npts, UM_BM) * Kp;
+    if (!cache_hit(xcache, X, n, ldx, npts)) {
+        k_split_n<float><<<2048, dim3(64, 4), 0, st>>>(X, ldx, (int)npts, n, (int)Kp, PA);
+        cache_set(xcache, X, n, ldx, npts);
+    }
     // C^T: rows = output columns, K = n
     dim3 tb(32, 8);
     k_split_t<double><<<dim3((unsigned)(Kp / 32), (unsigned)((m + 31) / 32)), tb, 0, st>>>(C, ldc, n, m, (int)Kp, PB);
