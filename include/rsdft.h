@@ -146,7 +146,9 @@ int rs_ham_destroy(rs_ham *h);
  *   psi_dev   device [npts][ld_psi] (first nb columns used), dtype elements
  *   hpsi_dev  device [npts][ld_hpsi]; must not overlap psi_dev
  *   nb        1, 2, 4, 8, 16, 32 or 64 (a power of two, Sec. IV)
- * Asynchronous.  Errors: RS_EINVAL (nb, ld, alignment, null), RS_ECUDA. */
+ * Asynchronous.  Calls on one handle share its projection-coefficient
+ * scratch: issue them on one stream (or order them with events).
+ * Errors: RS_EINVAL (nb, ld, alignment, null), RS_ECUDA. */
 int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi, void *hpsi_dev, int64_t ld_hpsi,
                        int nb, int dtype, void *stream);
 
