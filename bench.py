@@ -337,6 +337,30 @@ def nb_sweep(workload):
     return 0
 
 
+def learned_apply_timing(workload, n):
+    """n applications of the learned preconditioner (the 1-8-8-1 network on
+    the point map) to one 32-state residual block, after three untimed ones;
+    prints the mean time per application."""
+    import torch
+    from paper_1306_2953_gb300 import api
+    g, H = build_system(workload)
+    w = torch.from_numpy(np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel()
+                                         for a in wl.conv_init(11)]).astype(np.float32)).cuda()
+    R = torch.from_numpy(wl.random_block(g.npts, 32, 3)).float().cuda()
+    for _ in range(3):
+        api.precond_apply(H, w, R)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        api.precond_apply(H, w, R)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": workload.name, "npts": g.npts, "states": 32,
+                      "ms_per_apply": e0.elapsed_time(e1) / n}))
+    return 0
+
+
 def max_over_ranks(value, device):
     """The largest of every rank's value (all ranks call it; the job's time
     is its slowest replica's)."""
@@ -390,6 +414,9 @@ def main():
     ap.add_argument("--nb-sweep", action="store_true",
                     help="print H psi GB/s of algorithmic bytes for blocks of 1..64 states (FP32 and FP64) on "
                          "--workload and exit (no benchmark line)")
+    ap.add_argument("--learned-apply", type=int, default=0,
+                    help="profiling aid: time this many learned-preconditioner applications to one 32-state "
+                         "block of --workload (seeded initial weights) and exit (no benchmark line)")
     ap.add_argument("--sweep-precision", default="f32", choices=["f32", "f64"],
                     help="precision of the --profile-sweeps solver")
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -403,6 +430,8 @@ def main():
         return profile_sweeps(workload, args.profile_sweeps, args.sweep_precision)
     if args.nb_sweep:
         return nb_sweep(workload)
+    if args.learned_apply > 0:
+        return learned_apply_timing(workload, args.learned_apply)
 
     import torch
     import torch.distributed as dist
