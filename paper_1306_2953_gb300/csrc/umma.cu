@@ -325,7 +325,7 @@ int encoder(PFN_cuTensorMapEncodeTiled_v12000 *out) {
 
 // 3-D map over pieces [3][rows][Kp] (bf16), box {64, box_rows, 3}, 128-byte swizzle
 int make_map(CUtensorMap *m, const void *P, int rows, int Kp, int box_rows) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
     RS_TRY(encoder(&enc));
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
     cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
@@ -491,7 +491,7 @@ extern "C" int rs_overlap_block_tc(const rs_grid *g, const float *X_dev, int64_t
     if (!g || !X_dev || !Y_dev || !S_dev) return fail(RS_EINVAL, "rs_overlap_block_tc: null argument");
     if (nx < 1 || ny < 1 || ldx < nx || ldy < ny || lds < ny) return fail(RS_EINVAL, "rs_overlap_block_tc: bad sizes");
     cudaStream_t st = (cudaStream_t)stream;
-    int *err;
+    int *err = nullptr;
     RS_TRY(tc_check(work_dev, nx, ny, g->npts, &err, st));
     RS_TRY(umma_gram(X_dev, ldx, nx, Y_dev, ldy, ny, g->npts, g->h * g->h * g->h, S_dev, lds, work_dev, err, st));
     return tc_finish(err, st);
@@ -502,7 +502,7 @@ extern "C" int rs_rotate_block(const float *X_dev, int64_t ldx, int n, const dou
     if (!X_dev || !C_dev || !Y_dev) return fail(RS_EINVAL, "rs_rotate_block: null argument");
     if (n < 1 || m < 1 || npts < 1 || ldx < n || ldy < m || ldc < m) return fail(RS_EINVAL, "rs_rotate_block: bad sizes");
     cudaStream_t st = (cudaStream_t)stream;
-    int *err;
+    int *err = nullptr;
     RS_TRY(tc_check(work_dev, npts, m, n, &err, st));
     RS_TRY(umma_rowmul(X_dev, ldx, n, C_dev, ldc, m, Y_dev, ldy, npts, 1.0, 0.0, work_dev, err, st));
     return tc_finish(err, st);
