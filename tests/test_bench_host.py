@@ -30,3 +30,28 @@ def test_profiled_traffic_other_workload_is_none():
 def test_replica_throughput_is_whole_job():
     # two replicas, each 1 GB per step, 4 steps in 10 ms (slowest replica)
     assert abs(bench.replica_throughput(2, 1e9, 4, 10.0) - 800.0) < 1e-9
+
+
+def test_reference_arm_json_line():
+    # the reference arm times the FP64 oracle on the host cores and prints
+    # one JSON line with the same metric and workload as the CUDA arm
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run(
+        [sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+         "--steps", "1", "--warmup", "0"],
+        cwd=bench.ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    r = json.loads(lines[0])
+    assert r["impl"] == "reference"
+    assert r["unit"] == "GB/s" and r["higher_is_better"] is True
+    assert r["value"] > 0 and r["steps"] == 1 and r["n_gpus"] == 1
+    assert r["dtype"] == "f64" and r["data"] == "synthetic"
+    assert r["config"]["workload"] == wl.MOL100.name
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"]
+    assert r["e2e"] == {"value": r["value"], "unit": r["unit"],
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
