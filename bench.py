@@ -103,6 +103,20 @@ def build_system(workload):
     return g, api.Hamiltonian(g, V, pr)
 
 
+def omp_threads() -> int:
+    """Threads the oracle's OpenMP loops run on: OMP_NUM_THREADS when set,
+    else the CPUs this process may run on (libgomp sizes its team from the
+    affinity mask, which a container's cpuset can make smaller than the
+    machine)."""
+    env = os.environ.get("OMP_NUM_THREADS", "").split(",")[0].strip()
+    if env.isdigit() and int(env) > 0:
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(workload, nb_sample: int, budget_s: float = 20.0):
     """The FP64 oracle's H psi (plain C loops, OpenMP on all host cores) on a
     bounded sample: one block of nb_sample states of the same molecule."""
@@ -122,7 +136,7 @@ def cpu_baseline(workload, nb_sample: int, budget_s: float = 20.0):
         if time.perf_counter() - t0 > budget_s or n >= 50:
             break
     dt = (time.perf_counter() - t0) / n
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = omp_threads()
     return g, dt, cores
 
 
@@ -154,7 +168,7 @@ def run_reference(args, workload):
     for _ in range(args.steps):
         H.apply(psi)
     dt = (time.perf_counter() - t0) / args.steps
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = omp_threads()
     by = algorithmic_bytes_f32(g.npts, int(pr.sph_off[-1]), spec.n_atoms, nb, nb=nb)
     v = by / dt / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,

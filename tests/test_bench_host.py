@@ -55,3 +55,10 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"]
     assert r["e2e"] == {"value": r["value"], "unit": r["unit"],
                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_omp_threads(monkeypatch):
+    monkeypatch.setenv("OMP_NUM_THREADS", "3")
+    assert bench.omp_threads() == 3
+    monkeypatch.delenv("OMP_NUM_THREADS")
+    assert bench.omp_threads() == len(os.sched_getaffinity(0))
