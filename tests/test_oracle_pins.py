@@ -215,6 +215,24 @@ def test_projector_normalisation_and_kb_eigen():
         assert np.abs(out - E[0, 0 if q == 0 else 1] * v).max() < 1e-12
 
 
+def test_projector_sphere_lists_exact():
+    # dyadic atoms, h and r_cut: FP64 distances are exact, so the point list
+    # of each projector sphere is the exact lattice set d^2 <= r_cut^2
+    atoms = np.array([[0.25, 0.5, -0.75], [1.5, 0.0, 0.25]])
+    h, R, r_cut = 0.25, 1.5, 1.0
+    g = og.sphere_union_grid(atoms, R, h)
+    pr = oh.make_projectors(g, atoms, np.ones((2, 2)), 1.0, r_cut)
+    hF, rF = Fraction(h), Fraction(r_cut)
+    for A, a in enumerate(atoms):
+        aF = [Fraction(v) for v in a]
+        want = sorted(p for p, ijk in enumerate(g.ijk.tolist())
+                      if sum((ijk[d] * hF - aF[d]) ** 2 for d in range(3)) <= rF * rF)
+        assert pr.points(A).tolist() == want
+        on_sphere = sum(1 for ijk in g.ijk.tolist()
+                        if sum((ijk[d] * hF - aF[d]) ** 2 for d in range(3)) == rF * rF)
+        assert on_sphere > 0          # the boundary case is exercised
+
+
 def test_nonlocal_psd_rank_and_dense_agree():
     g, H, atoms, _ = small_molecule(h=0.5, R=2.5)
     n = g.npts
@@ -241,6 +259,20 @@ def test_cholesky_triinv_against_library():
         ol.cholesky_upper(-S)
 
 
+def test_overlap_is_the_grid_integral():
+    # <g|g> = dV sum g^2 for g = exp(-r^2/2) on a fine box is the integral of
+    # exp(-r^2), pi^(3/2) (the lattice sum of a Gaussian converges
+    # exponentially in 1/h; the box edge at 4.9 Bohr cuts off e^-24)
+    g = og.box_grid(40, 0.25)
+    r2 = np.sum(g.coords ** 2, axis=1)
+    f = np.exp(-0.5 * r2)[:, None]
+    assert abs(ol.overlap(f, f, g.dV)[0, 0] - np.pi ** 1.5) < 1e-9
+    # and x exp(-r^2/2) is orthogonal to it, with norm pi^(3/2) / 2
+    fx = (g.coords[:, 0] * np.exp(-0.5 * r2))[:, None]
+    S = ol.overlap(np.hstack([f, fx]), np.hstack([f, fx]), g.dV)
+    assert abs(S[0, 1]) < 1e-12 and abs(S[1, 1] - np.pi ** 1.5 / 2) < 1e-9
+
+
 def test_orthonormalize_invariants():
     g, H, _, _ = small_molecule()
     psi = wl.random_block(g.npts, 12, 3)
@@ -265,6 +297,26 @@ def test_rayleigh_ritz_on_exact_separable_eigenvectors():
     eps, _, _, _ = ol.subspace_diag(H.apply, psi, g.dV)
     expect = np.sort([e1[a] + e1[b] + e1[c] for a, b, c in idx])
     assert np.abs(eps - expect).max() < 1e-11
+
+
+def test_rayleigh_ritz_vectors_are_exact_eigenvectors():
+    # a rotated set of exact (non-degenerate) separable eigenvectors: the Ritz
+    # vectors must be those eigenvectors again, H phi_k = eps_k phi_k
+    n, h = 10, 0.35
+    g = og.box_grid(n, h)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, 1.0) + 0.05 * g.coords[:, 0] ** 2)
+    ex, vx = one_d_levels(n, h, np.sqrt(1.1))   # V_x = 1.1 x^2 / 2
+    e1, v1 = one_d_levels(n, h, 1.0)
+    idx = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (2, 0, 0), (1, 1, 0)]
+    cols = [np.einsum("i,j,k->ijk", vx[:, a], v1[:, b], v1[:, c]).ravel() for a, b, c in idx]
+    psi = np.stack(cols, axis=1) / np.sqrt(g.dV)
+    Q, _ = np.linalg.qr(np.random.default_rng(4).standard_normal((5, 5)))
+    eps, phi, hphi, _ = ol.subspace_diag(H.apply, psi @ Q, g.dV)
+    expect = np.sort([ex[a] + e1[b] + e1[c] for a, b, c in idx])
+    assert np.abs(eps - expect).max() < 1e-11
+    Hphi = H.apply(phi)
+    assert np.abs(Hphi - phi * eps).max() < 1e-9 * np.abs(Hphi).max()
+    assert np.abs(hphi - Hphi).max() < 1e-9 * np.abs(Hphi).max()
 
 
 def test_tiny_molecule_dense_vs_block_cg():
@@ -380,6 +432,12 @@ def test_bf16_round_matches_library():
     x = np.random.default_rng(2).standard_normal(10000).astype(np.float32) * 100
     ref = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
     assert np.array_equal(op.bf16_round(x), ref)
+    # exact ties (low 16 bits 0x8000) round to the even neighbour
+    hi = np.array([0x3F80, 0x3F81, 0xBF80, 0xBF81, 0x4049, 0x404A, 0x0001, 0x7F7E], dtype=np.uint32)
+    for low in (0x8000, 0x7FFF, 0x8001):
+        t = ((hi << 16) | low).view(np.float32)
+        ref = torch.from_numpy(t.copy()).to(torch.bfloat16).float().numpy()
+        assert np.array_equal(op.bf16_round(t), ref), hex(low)
 
 
 def test_adam_first_step_is_signed_lr():
