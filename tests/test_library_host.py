@@ -107,3 +107,45 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     unbound = [n for n in names if n not in _lib.exported_names()]
     assert not unbound, unbound
+
+
+# point counts of the seeded molecules (union of 5 Bohr spheres), written
+# by the oracle's grid builder; the benchmark's throughput figures refer to
+# these sizes
+FULL_SIZE_NPTS = {wl.MOL20.name: 103331, wl.MOL100.name: 654520, wl.MOL300.name: 1821562}
+
+
+@pytest.mark.parametrize("w", [wl.MOL20, wl.MOL100, wl.MOL300], ids=lambda w: w.name)
+def test_full_size_grids_bit_exact(w):
+    spec = w.system
+    atoms = wl.atom_positions(spec)
+    lg = api.Grid.spheres(atoms, spec.radius, spec.h)
+    ref = og.sphere_union_grid(atoms, spec.radius, spec.h)
+    assert lg.npts == ref.npts == FULL_SIZE_NPTS[w.name]
+    ijk = lg.ijk()
+    assert np.array_equal(ijk[np.lexsort((ijk[:, 2], ijk[:, 1], ijk[:, 0]))], ref.ijk)
+    mp = lg.point_map()
+    _, origin, _, _ = lg.info()
+    rel = ijk - np.array(origin)
+    assert np.array_equal(mp[rel[:, 0], rel[:, 1], rel[:, 2]], np.arange(lg.npts))
+    assert np.sum(mp >= 0) == lg.npts
+
+
+def test_full_size_projector_lists_mol100():
+    # the 100-atom molecule at full size: every projector sphere list is the
+    # oracle's point set, coefficients to FP64 rounding
+    spec = wl.MOL100.system
+    atoms = wl.atom_positions(spec)
+    E = wl.kb_couplings(spec)
+    lg = api.Grid.spheres(atoms, spec.radius, spec.h)
+    ref = og.sphere_union_grid(atoms, spec.radius, spec.h)
+    pr_ref = oh.make_projectors(ref, atoms, E, spec.r_c, spec.r_cut)
+    off, idx, gam = api.Projectors(lg, atoms, E, spec.r_c, spec.r_cut).tables()
+    assert off[-1] == pr_ref.sph_off[-1]
+    to_ora = lib_to_oracle_index(ref, lg.ijk())
+    for A in range(spec.n_atoms):
+        lib_pts = to_ora[idx[off[A]:off[A + 1]]]
+        order = np.argsort(lib_pts)
+        assert np.array_equal(lib_pts[order], pr_ref.points(A))
+        g_ora = pr_ref.gamma(A).T
+        assert np.abs(gam[off[A]:off[A + 1]][order] - g_ora).max() < 1e-13 * np.abs(g_ora).max()
