@@ -183,6 +183,14 @@ MUTANTS = [
            "return float(np.sum(d * d) / n), 2.0 * d / n",
            "return float(np.sum(d * d) / n), d / n",
            "net_gradients"),
+    Mutant("learned_output_not_rescaled", "precond.py",
+           "out[grid.map[mask], s] = rms * y[0][mask]",
+           "out[grid.map[mask], s] = y[0][mask]",
+           "linear_stencils"),
+    Mutant("learned_input_unmasked_layer", "precond.py",
+           "a1 = np.maximum(z1, 0.0) * m",
+           "a1 = np.maximum(z1, 0.0)",
+           "linear_stencils or net_gradients"),
     Mutant("bf16_ties_away", "precond.py",
            "u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000",
            "u = (u + 0x8000) & 0xFFFF0000",

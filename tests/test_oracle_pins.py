@@ -427,6 +427,47 @@ def test_net_gradients_finite_difference():
             assert abs(fd - grads[li][idx]) <= 1e-7 * max(1.0, abs(fd)) + 1e-9
 
 
+def linear_stencil_net(K, channels=8):
+    """Weights for which the bias-free ReLU net computes the linear stencil K
+    (3x3x3 cross-correlation): channel 0 carries relu(x), channel 1
+    relu(-x), and relu(x) - relu(-x) = x."""
+    w0 = np.zeros((channels, 1, 3, 3, 3))
+    w1 = np.zeros((channels, channels, 3, 3, 3))
+    w2 = np.zeros((1, channels, 3, 3, 3))
+    w0[0, 0, 1, 1, 1], w0[1, 0, 1, 1, 1] = 1.0, -1.0
+    w1[0, 0, 1, 1, 1] = w1[1, 1, 1, 1, 1] = 1.0
+    w2[0, 0], w2[0, 1] = K, -K
+    return [w0, w1, w2]
+
+
+def test_learned_net_reproduces_linear_stencils():
+    # on a sphere-union grid (points off the grid are zero): the filter
+    # kernel gives the plain filter preconditioner, a one-point kernel gives
+    # the neighbour at that offset from the grid's own neighbour table
+    g, _, _, _ = small_molecule()
+    R = wl.random_block(g.npts, 3, 12)
+    a = 0.5
+    Kf = np.zeros((3, 3, 3))
+    Kf[1, 1, 1] = a
+    for d in range(3):
+        for s in (0, 2):
+            idx = [1, 1, 1]
+            idx[d] = s
+            Kf[tuple(idx)] = (1 - a) / 6
+    ref = eigensolver.FilterPreconditioner(g, a)(R)
+    assert np.abs(op.apply_learned(g, R, linear_stencil_net(Kf)) - ref).max() < 1e-14 * np.abs(ref).max()
+    nbr = g.neighbours(1)                      # [np, 3, 2]: offsets -1, +1 per axis
+    for axis in range(3):
+        for t, off in enumerate((-1, 1)):
+            Ks = np.zeros((3, 3, 3))
+            idx = [1, 1, 1]
+            idx[axis] = 1 + off
+            Ks[tuple(idx)] = 1.0
+            q = nbr[:, axis, t]
+            want = np.where((q >= 0)[:, None], R[np.maximum(q, 0)], 0.0)
+            assert np.abs(op.apply_learned(g, R, linear_stencil_net(Ks)) - want).max() < 1e-14
+
+
 def test_bf16_round_matches_library():
     torch = pytest.importorskip("torch")
     x = np.random.default_rng(2).standard_normal(10000).astype(np.float32) * 100
