@@ -62,3 +62,15 @@ def test_omp_threads(monkeypatch):
     assert bench.omp_threads() == 3
     monkeypatch.delenv("OMP_NUM_THREADS")
     assert bench.omp_threads() == len(os.sched_getaffinity(0))
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    # under torchrun only rank 0 times the oracle and prints the line
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                          "--gpus", "2", "--steps", "1", "--warmup", "0"],
+                         cwd=bench.ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert not [l for l in out.stdout.splitlines() if l.startswith("{")]
