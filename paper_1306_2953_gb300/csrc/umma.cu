@@ -112,6 +112,7 @@ struct UmmaArgs {
     int64_t lds;
     float *Y;
     int64_t ldy;
+    int yvec;             // mode 1: Y rows 16-byte aligned (Y and ldy multiples of 4 floats)
     int *err;
 };
 
@@ -222,6 +223,23 @@ __global__ void __launch_bounds__(UM_NT, 1) k_umma_tn(const __grid_constant__ CU
                     for (int j = 0; j < 32; ++j) {
                         const int n = n0 + c0 + j;
                         if (n < args.N) atomicAdd(srow + n, args.alpha * (double)__uint_as_float(r[j]));
+                    }
+                } else if (args.yvec && n0 + c0 + 32 <= args.N) {
+                    // the thread's 32 columns are 128 contiguous bytes of its row
+                    float4 *y4 = reinterpret_cast<float4 *>(args.Y + (int64_t)m * args.ldy + n0 + c0);
+                    const float al = (float)args.alpha, be = (float)args.beta;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float4 v = make_float4(al * __uint_as_float(r[4 * j]), al * __uint_as_float(r[4 * j + 1]),
+                                               al * __uint_as_float(r[4 * j + 2]), al * __uint_as_float(r[4 * j + 3]));
+                        if (args.beta != 0.0) {
+                            const float4 o = y4[j];
+                            v.x = v.x + be * o.x;
+                            v.y = v.y + be * o.y;
+                            v.z = v.z + be * o.z;
+                            v.w = v.w + be * o.w;
+                        }
+                        y4[j] = v;
                     }
                 } else {
                     float *yrow = args.Y + (int64_t)m * args.ldy;
@@ -456,6 +474,7 @@ int umma_rowmul(const float *X, int64_t ldx, int n, const double *C, int64_t ldc
     a.beta = beta;
     a.Y = Y;
     a.ldy = ldy;
+    a.yvec = ((uintptr_t)Y % 16 == 0) && (ldy % 4 == 0);
     a.err = err;
     return BN == 64 ? launch<64>(ta, tbm, a, 1, st) : launch<128>(ta, tbm, a, 1, st);
 }
