@@ -272,6 +272,9 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
         t0 = time.perf_counter()
         S = api.Solver(H, torch.from_numpy(psi0).to(dt).cuda(), workload.block, 1e-4, precond=pc)
         train_s, losses = 0.0, None
+        if mode.endswith("_cg"):
+            # five CG iterations on (-1/2 Lap + 2) W = R (kept alive by S)
+            S.set_precond_cg(api.Hamiltonian(g, np.full(g.npts, 2.0)), 5)
         if pc == _lib.RS_PRECOND_LEARNED:
             t1 = time.perf_counter()
             w, losses = train_learned(H, g, S)
@@ -573,7 +576,7 @@ def main():
                                 "sample": f"FP64 oracle H psi on one block of {NB} states of {workload.name} "
                                           f"({dt:.2f} s per block)"}
     if rank == 0 and world == 1 and args.eigensolve != "none":
-        line["eigensolve"] = [eigensolve_bench(wl.WORKLOADS[n], ["mixed_learned", "mixed_filter", "f64_filter"])
+        line["eigensolve"] = [eigensolve_bench(wl.WORKLOADS[n], ["mixed_learned", "mixed_cg", "mixed_filter", "f64_filter"])
                               for n in args.eigensolve.split(",")]
     if rank == 0:
         print(json.dumps(line))

@@ -380,6 +380,16 @@ int rs_solver_set_precond_weights(rs_solver *s, const float *w_dev);
  * Errors: RS_EINVAL. */
 int rs_solver_set_precond(rs_solver *s, int precond);
 
+/* Replaces the solver's preconditioner, for later sweeps, by n_iter
+ * conjugate-gradient iterations from W = 0 on (-1/2 Lap + sigma) W = R, one
+ * system per residual column: the operator the learned network is trained
+ * to imitate, applied directly.  Not in the paper.  shifted is a Hamiltonian
+ * on the solver's grid built with V = sigma everywhere and no projectors;
+ * it stays owned by the caller and must outlive the solver or the next
+ * preconditioner change.  n_iter in 1 .. 200.  Blocking.  Errors: RS_EINVAL
+ * (null argument, n_iter out of range, a grid of another size), RS_ENOMEM. */
+int rs_solver_set_precond_cg(rs_solver *s, rs_ham *shifted, int n_iter);
+
 int rs_solver_destroy(rs_solver *s);
 
 #ifdef __cplusplus

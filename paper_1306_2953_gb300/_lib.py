@@ -85,6 +85,7 @@ SIGNATURES = {
     "rs_solver_rayleigh_ritz_f64": (None, [P, P, P]),
     "rs_solver_set_precond_weights": (None, [P, P]),
     "rs_solver_set_precond": (None, [P, I32]),
+    "rs_solver_set_precond_cg": (None, [P, P, I32]),
     "rs_cg_workspace_bytes": (I64, [I64, I32, I32]),
     "rs_shifted_poisson_cg": (None, [P, P, P, I64, I32, I32, I32, P, P]),
     "rs_precond_apply": (None, [P, P, P, I64, P, I64, I32, P]),

@@ -266,6 +266,13 @@ class Solver:
         """rs_solver_set_precond: switch the preconditioner for later sweeps."""
         call("rs_solver_set_precond", self._h, int(kind))
 
+    def set_precond_cg(self, shifted: "Hamiltonian", n_iter: int):
+        """rs_solver_set_precond_cg: n_iter CG iterations on the shifted
+        Poisson operator ``shifted`` (V = sigma, no projectors) as the
+        preconditioner of later sweeps; ``shifted`` must outlive the solver."""
+        call("rs_solver_set_precond_cg", self._h, shifted._h, int(n_iter))
+        self._shifted = shifted
+
     def set_precond_weights(self, w):
         """Learned-preconditioner weights: FP32 device tensor of 2160 values."""
         call("rs_solver_set_precond_weights", self._h, _c(w.data_ptr()))

@@ -1,6 +1,8 @@
 // Preconditioners: none, the face-neighbour smoothing filter (the plain
 // method's preconditioner; Sec. III cites a filter of Saad et al. without
-// giving its form), and the learned convolutional network.
+// giving its form), the learned convolutional network, and a few conjugate-
+// gradient iterations on the shifted Poisson operator that the network is
+// trained to imitate.
 #include <new>
 
 #include "device.h"
@@ -60,7 +62,44 @@ class Learned : public Precond {
     bool ready = false;
 };
 
+// A few CG iterations on (-1/2 Lap + sigma) W = R, into a scratch block
+// [npts][nb] and then into W (whose leading dimension may differ).
+class ShiftedCG : public Precond {
+   public:
+    int init(rs_ham *hs, int iters, int64_t n, int b, int dtype) {
+        shifted = hs;
+        n_iter = iters;
+        npts = n;
+        nb = b;
+        es = dtype == RS_F64 ? 8 : 4;
+        RS_TRY(x.alloc((size_t)npts * nb * es));
+        return work.alloc((size_t)rs_cg_workspace_bytes(npts, nb, dtype));
+    }
+    int apply(const rs_ham *, const void *R, int64_t ldr, void *W, int64_t ldw, int ncols, int dtype,
+              cudaStream_t st) override {
+        if (ldr != nb || ncols != nb) return fail(RS_EINVAL, "CG preconditioner: residual block must be [npts][nb]");
+        RS_TRY(rs_shifted_poisson_cg(shifted, R, x.p, nb, nb, n_iter, dtype, work.p, st));
+        RS_CUDA(cudaMemcpy2DAsync(W, (size_t)ldw * es, x.p, (size_t)nb * es, (size_t)nb * es, (size_t)npts,
+                                  cudaMemcpyDeviceToDevice, st));
+        return RS_OK;
+    }
+    rs_ham *shifted = nullptr;
+    int n_iter = 0, nb = 1, es = 4;
+    int64_t npts = 0;
+    DevBuf x, work;
+};
+
 }  // namespace
+
+Precond *Precond::create_cg(rs_ham *shifted, int n_iter, int64_t npts, int nb, int dtype) {
+    ShiftedCG *p = new (std::nothrow) ShiftedCG();
+    if (!p) return nullptr;
+    if (p->init(shifted, n_iter, npts, nb, dtype) != RS_OK) {
+        delete p;
+        return nullptr;
+    }
+    return p;
+}
 
 Precond *Precond::create(int kind, double filter_alpha, int64_t npts, int nb, int dtype) {
     switch (kind) {

@@ -17,6 +17,8 @@ class Precond {
                       cudaStream_t st) = 0;
     virtual int set_weights(const float *w_dev, cudaStream_t st);
     static Precond *create(int kind, double filter_alpha, int64_t npts, int nb, int dtype);
+    // n_iter CG iterations on the caller's shifted Hamiltonian (V = sigma, no projectors)
+    static Precond *create_cg(rs_ham *shifted, int n_iter, int64_t npts, int nb, int dtype);
 };
 
 }  // namespace rs

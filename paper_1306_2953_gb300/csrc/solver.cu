@@ -507,6 +507,18 @@ extern "C" int rs_solver_set_precond(rs_solver *S, int precond) {
     return RS_OK;
 }
 
+extern "C" int rs_solver_set_precond_cg(rs_solver *S, rs_ham *shifted, int n_iter) {
+    if (!S || !shifted) return fail(RS_EINVAL, "rs_solver_set_precond_cg: null argument");
+    if (n_iter < 1 || n_iter > 200) return fail(RS_EINVAL, "rs_solver_set_precond_cg: n_iter must be in 1 .. 200");
+    if (ham_npts(shifted) != S->npts) return fail(RS_EINVAL, "rs_solver_set_precond_cg: grid size differs");
+    Precond *p = Precond::create_cg(shifted, n_iter, S->npts, S->cfg.nb, S->cfg.dtype);
+    if (!p) return fail(RS_ENOMEM, "rs_solver_set_precond_cg: allocation failed");
+    RS_CUDA(cudaDeviceSynchronize());   // no sweep still uses the old one
+    delete S->pc;
+    S->pc = p;
+    return RS_OK;
+}
+
 extern "C" int rs_solver_destroy(rs_solver *S) {
     delete S;
     return RS_OK;
