@@ -15,6 +15,8 @@ collective on the data path); value = work of all ranks / max time.
 from __future__ import annotations
 
 import argparse
+import contextlib
+import ctypes
 import json
 import os
 import statistics
@@ -117,6 +119,22 @@ def omp_threads() -> int:
         return os.cpu_count() or 1
 
 
+@contextlib.contextmanager
+def oracle_threads(n: int):
+    """Runs the oracle's OpenMP loops on n threads inside the block (the
+    team size of libgomp, which the oracle's library links), restoring the
+    previous size afterwards."""
+    from oracle import _native
+    L = _native.lib()
+    L.omp_get_max_threads.restype = ctypes.c_int
+    prev = L.omp_get_max_threads()
+    L.omp_set_num_threads(ctypes.c_int(n))
+    try:
+        yield
+    finally:
+        L.omp_set_num_threads(ctypes.c_int(prev))
+
+
 def cpu_baseline(workload, nb_sample: int, budget_s: float = 20.0):
     """The FP64 oracle's H psi (plain C loops, OpenMP on all host cores) on a
     bounded sample: one block of nb_sample states of the same molecule."""
@@ -137,7 +155,19 @@ def cpu_baseline(workload, nb_sample: int, budget_s: float = 20.0):
             break
     dt = (time.perf_counter() - t0) / n
     cores = omp_threads()
-    return g, dt, cores
+    # the same block on one thread: a few applications, a few seconds
+    dt1 = None
+    try:
+        with oracle_threads(1):
+            t0 = time.perf_counter()
+            n1 = 0
+            while n1 < 3 and (n1 == 0 or time.perf_counter() - t0 < budget_s / 2):
+                H.apply(psi)
+                n1 += 1
+            dt1 = (time.perf_counter() - t0) / n1
+    except (OSError, AttributeError):
+        dt1 = None
+    return g, dt, cores, dt1
 
 
 def algorithmic_bytes_f32(npts, n_entries, n_atoms, nst, nb=NB):
@@ -570,11 +600,14 @@ def main():
                     "max_rel_diff_vs_device_result": e2e_err},
             "gpu_launches": int(2 * (nst // NB) * args.steps), "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gcpu, dt, cores = cpu_baseline(workload, NB)
+        gcpu, dt, cores, dt1 = cpu_baseline(workload, NB)
         by = bytes_per_apply  # the same FP32 block bytes, computed by the oracle in FP64
         line["cpu_baseline"] = {"value": by / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
                                 "sample": f"FP64 oracle H psi on one block of {NB} states of {workload.name} "
                                           f"({dt:.2f} s per block)"}
+        if dt1 is not None:
+            line["cpu_baseline"]["single_thread"] = {"value": by / dt1 / 1e9, "unit": "GB/s", "cores": 1,
+                                                     "seconds_per_block": dt1}
     if rank == 0 and world == 1 and args.eigensolve != "none":
         line["eigensolve"] = [eigensolve_bench(wl.WORKLOADS[n], ["mixed_learned", "mixed_cg", "mixed_filter", "f64_filter"])
                               for n in args.eigensolve.split(",")]

@@ -74,3 +74,23 @@ def test_reference_arm_other_ranks_exit_quietly():
                          cwd=bench.ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [l for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_oracle_threads_sets_and_restores_team_size():
+    import ctypes
+    from oracle import _native
+    L = _native.lib()
+    L.omp_get_max_threads.restype = ctypes.c_int
+    before = L.omp_get_max_threads()
+    with bench.oracle_threads(1):
+        assert L.omp_get_max_threads() == 1
+    assert L.omp_get_max_threads() == before
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    # small budget on the 20-atom molecule: both timings are positive and the
+    # one-thread block is not faster than the all-core one by more than noise
+    g, dt, cores, dt1 = bench.cpu_baseline(wl.MOL20, 8, budget_s=1.0)
+    assert dt > 0 and dt1 is not None and dt1 > 0 and cores >= 1
+    if cores > 1:
+        assert dt1 > 0.8 * dt
