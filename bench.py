@@ -119,6 +119,25 @@ def omp_threads() -> int:
         return os.cpu_count() or 1
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name on x86; implementer
+    and part codes on Arm, which names no model there)."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    if fields.get("CPU implementer"):
+        return f"{platform.machine()} (implementer {fields['CPU implementer']}, part {fields.get('CPU part', '?')})"
+    return platform.machine() or "unknown"
+
+
 @contextlib.contextmanager
 def oracle_threads(n: int):
     """Runs the oracle's OpenMP loops on n threads inside the block (the
@@ -603,6 +622,7 @@ def main():
         gcpu, dt, cores, dt1 = cpu_baseline(workload, NB)
         by = bytes_per_apply  # the same FP32 block bytes, computed by the oracle in FP64
         line["cpu_baseline"] = {"value": by / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                                "cpu": cpu_model(),
                                 "sample": f"FP64 oracle H psi on one block of {NB} states of {workload.name} "
                                           f"({dt:.2f} s per block)"}
         if dt1 is not None:

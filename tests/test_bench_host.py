@@ -94,3 +94,8 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     assert dt > 0 and dt1 is not None and dt1 > 0 and cores >= 1
     if cores > 1:
         assert dt1 > 0.8 * dt
+
+
+def test_cpu_model_is_named():
+    m = bench.cpu_model()
+    assert isinstance(m, str) and m
