@@ -224,7 +224,7 @@ def run_reference(args, workload):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload.name, "npts": g.npts, "states_per_step": nb, "block": nb},
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"FP64 oracle H psi on one block of {nb} states of {workload.name} per step"},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
