@@ -190,10 +190,12 @@ def cpu_baseline(workload, nb_sample: int, budget_s: float = 20.0):
 
 
 def algorithmic_bytes_f32(npts, n_entries, n_atoms, nst, nb=NB):
-    """Same byte model as rs_ham_apply_bytes for FP32, for nst states."""
+    """Same byte model as rs_ham_apply_bytes for FP32, for nst states: psi
+    read once, H psi written once, V and the point map, one copy of the
+    projector tables and the coefficients."""
     s = 4
-    per_block = (npts * nb * 2 * s + npts * s + npts * 4 + n_entries * (4 + 4 * s) * 2 + (npts + 1) * 4
-                 + n_atoms * 4 * nb * s * 2 + (n_atoms + 1) * 4)
+    per_block = (npts * nb * 2 * s + npts * s + npts * 4 + n_entries * (4 + 4 * s) + (npts + 1) * 4
+                 + n_atoms * 4 * nb * s)
     return per_block * (nst // nb)
 
 
@@ -277,32 +279,27 @@ def build_any(workload):
     return build_system(workload)
 
 
-def train_learned(H, g, solver, n_res=40, n_tiles=10000, epochs=5, seed=11):
-    """Learned-preconditioner weights from the method's own residuals: Ritz
-    residuals of the current orbitals, their 200-iteration shifted-Poisson CG
-    solutions, and Adam on tiles cut from the pairs."""
+def initial_weights(seed=11):
+    """The seeded starting weights of the network (FP32 [2160], device)."""
     import torch
-    from paper_1306_2953_gb300 import api
-    Hs = api.Hamiltonian(g, np.full(g.npts, 1.0))
-    ncols = 1 << (max(n_res, 1) - 1).bit_length()     # power of two for the block CG
-    R = solver.residual(0, min(ncols, solver.nst)).float().contiguous()
-    X = torch.empty_like(R)
-    for b in range(0, R.shape[1], 32):
-        X[:, b:b + 32] = api.shifted_poisson_cg(Hs, R[:, b:b + 32].contiguous(), 200)
-    # the eigensolver uses only the direction of K r, so each target column is
-    # scaled to unit rms (the network's input is r / rms(r)): the loss then
-    # measures the direction, not the ~1/50 magnitude of the inverse operator
-    X = X / X.pow(2).mean(dim=0, keepdim=True).sqrt().clamp_min(1e-30)
-    w = torch.from_numpy(np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel()
-                                         for a in wl.conv_init(seed)]).astype(np.float32)).cuda()
-    losses = api.precond_train(Hs, R[:, :n_res].contiguous(), X[:, :n_res].contiguous(), w, n_tiles=n_tiles,
-                               epochs=epochs, batch=64, seed=seed)
-    return w, losses
+    return torch.from_numpy(np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel()
+                                            for a in wl.conv_init(seed)]).astype(np.float32)).cuda()
+
+
+# the solver's schedules (rs_solver_cfg): the learned preconditioner gives way
+# to the filter after 3 sweeps without a 10 % drop of the largest wanted
+# residual; FP32 solvers take the closing FP64 Rayleigh-Ritz every 10 sweeps
+# once that residual is <= 3e-3 and at every sweep once it is <= 1e-4
+SCHEDULE = {"stall_sweeps": 3, "stall_ratio": 0.9, "rr64_every": 10, "rr64_below": 3e-3, "rr64_always": 1e-4}
+LEARN = {"n_res": 40, "cg_iters": 200, "sigma": 1.0, "n_tiles": 10000, "epochs": 5, "batch": 64, "seed": 11}
 
 
 def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
     """Seconds until every judged eigenvalue is within tol Ha of the oracle's
-    reference (tests/golden), for each precision / preconditioner mode."""
+    reference (tests/golden), for each precision / preconditioner mode.  Each
+    mode is a sequence of library calls: solver creation, (learned mode)
+    rs_precond_train, then rs_eigensolver_step until the eigenvalues it
+    reports -- from the closing FP64 Rayleigh-Ritz in FP32 mode -- match."""
     import torch
     from paper_1306_2953_gb300 import api, _lib
     gold = load_golden(workload.name)
@@ -312,62 +309,37 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
     judged = len(ref)
     g, H = build_any(workload)
     out = {"workload": workload.name, "npts": g.npts, "states": workload.n_states, "judged": judged,
-           "tolerance_ha": tol, "reference": "oracle block CG (tests/golden)", "modes": {}}
+           "tolerance_ha": tol, "reference": "oracle block CG (tests/golden)", "schedule": SCHEDULE, "modes": {}}
     psi0 = wl.random_block(g.npts, workload.n_states, workload.seed)
+    w0 = initial_weights(LEARN["seed"])
     for mode in modes:
         dt = torch.float64 if mode.startswith("f64") else torch.float32
         pc = _lib.RS_PRECOND_LEARNED if mode.endswith("learned") else _lib.RS_PRECOND_FILTER
+        psi0_d = torch.from_numpy(psi0).to(dt).cuda()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S = api.Solver(H, torch.from_numpy(psi0).to(dt).cuda(), workload.block, 1e-4, precond=pc)
-        train_s, losses = 0.0, None
+        S = api.Solver(H, psi0_d, workload.block, 1e-4, precond=pc, n_wanted=judged, **SCHEDULE)
+        losses = None
         if mode.endswith("_cg"):
             # five CG iterations on (-1/2 Lap + 2) W = R (kept alive by S)
             S.set_precond_cg(api.Hamiltonian(g, np.full(g.npts, 2.0)), 5)
         if pc == _lib.RS_PRECOND_LEARNED:
-            t1 = time.perf_counter()
-            w, losses = train_learned(H, g, S)
-            S.set_precond_weights(w)
-            torch.cuda.synchronize()
-            train_s = time.perf_counter() - t1
-        sweeps, err = 0, float("inf")
-        best, stall, fallback_at = float("inf"), 0, None
+            losses = S.train_precond(g, w0, **LEARN)
+        err = float("inf")
         while True:
-            eps, res, _ = S.step()
-            sweeps += 1
-            r = res.cpu().numpy()[:judged]
-            if pc == _lib.RS_PRECOND_LEARNED and fallback_at is None:
-                # the plain filter takes over once the learned preconditioner
-                # stops reducing the largest residual (3 sweeps below 10 %)
-                rmax = float(r.max())
-                if rmax < 0.9 * best:
-                    best, stall = rmax, 0
-                else:
-                    stall += 1
-                if stall >= 3:
-                    S.set_precond(_lib.RS_PRECOND_FILTER)
-                    fallback_at = sweeps
-            if dt == torch.float32:
-                # FP32 mode: the eigenvalues come from an FP64 Rayleigh-Ritz of
-                # the subspace, taken every 10 sweeps once the residuals are
-                # small and at every sweep below 1e-4 (its cost is timed)
-                rmax = float(r.max())
-                if rmax <= 1e-4 or (rmax <= 3e-3 and sweeps % 10 == 0):
-                    eps = S.rayleigh_ritz_f64()
-                else:
-                    eps = None
-            if eps is None:
-                err = float("inf")
-            else:
-                err = float(np.abs(eps.cpu().numpy()[:judged] - ref).max())
+            eps, _, _ = S.step()
+            st = S.stats()
+            err = float(np.abs(eps.cpu().numpy()[:judged] - ref).max()) if st["eps_f64"] else float("inf")
             el = time.perf_counter() - t0
             if err <= tol or el > max_seconds:
                 break
-        out["modes"][mode] = {"seconds": el, "train_seconds": train_s, "sweeps": sweeps, "max_error_ha": err,
-                              "converged": err <= tol, "train_losses": losses}
+        out["modes"][mode] = {"seconds": el, "sweeps": st["sweeps"], "max_error_ha": err, "converged": err <= tol,
+                              "train_seconds": st["train_target_seconds"] + st["train_fit_seconds"],
+                              "train_target_seconds": st["train_target_seconds"],
+                              "train_fit_seconds": st["train_fit_seconds"], "train_losses": losses}
         if pc == _lib.RS_PRECOND_LEARNED:
-            out["modes"][mode]["filter_fallback_after_sweep"] = fallback_at
-        del S
+            out["modes"][mode]["filter_fallback_after_sweep"] = st["fallback_sweep"] or None
+        del S, psi0_d
     return out
 
 
@@ -548,6 +520,8 @@ def main():
     if world > 1:
         dist.barrier()
     _lib.call("rs_ham_timing", H._h, 0)
+    if H.status() != 0:
+        raise RuntimeError("an H psi pipeline wait gave up during the timed region: the results are incomplete")
     ms = e0.elapsed_time(e1)
     pms, sms, ncalls = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
     _lib.call("rs_ham_timing_read", H._h, ctypes.byref(pms), ctypes.byref(sms), ctypes.byref(ncalls))
@@ -605,6 +579,9 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload.name, "npts": npts, "states": nst, "block": NB,
                        "psi_bytes": psi.numel() * 4,
+                       "bytes_model": "per 32-state block: psi read once and H psi written once (2 x 4 B per "
+                                      "point-state), V and the point map (8 B per point), one copy of the projector "
+                                      "tables (20 B per sphere entry), projection coefficients",
                        "l2": f"inputs (psi, {psi.numel() * 4 / 1e9:.2f} GB) larger than L2 (129 MB)",
                        "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "kernel": "k_hpsi_ring (fused stencil + V + nonlocal gather)",

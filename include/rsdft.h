@@ -17,7 +17,7 @@
  *  - Orbital blocks are row-major [npts][ld] arrays: the value of state s at
  *    grid point p is at element p*ld + s; ld >= the number of states used.
  *    Grid points are in the library's order (bricks of 4x4x4 lattice points,
- *    Sec. V.A "small parallelepipedic grids"); rs_grid_ijk() gives each
+ *    the small-box blocking of Sec. V.A); rs_grid_ijk() gives each
  *    point's integer lattice coordinates.
  *  - dtype is RS_F64 (double) or RS_F32 (float).
  *  - Pointers named *_dev are device pointers on the current CUDA device and
@@ -46,11 +46,15 @@ enum {
     RS_ECUDA = -3,    /* a CUDA runtime call failed; no GPU; or the kernel image is missing */
     RS_ENOTSPD = -4,  /* overlap matrix not positive definite (Cholesky failed) */
     RS_ENOCONV = -5,  /* an iteration cap was hit */
-    RS_ENAN = -6      /* a non-finite value was detected */
+    RS_ENAN = -6,     /* a non-finite value was detected */
+    RS_ETIMEOUT = -7  /* a bounded device-side wait gave up; that call's result is incomplete */
 };
 
 enum { RS_F64 = 0, RS_F32 = 1 };
-enum { RS_PRECOND_NONE = 0, RS_PRECOND_FILTER = 1, RS_PRECOND_LEARNED = 2 };
+/* Preconditioners: none, the smoothing filter (Sec. III), the learned network,
+ * and a few CG iterations on the shifted Poisson operator (RS_PRECOND_CG is
+ * set with rs_solver_set_precond_cg, not in rs_solver_cfg). */
+enum { RS_PRECOND_NONE = 0, RS_PRECOND_FILTER = 1, RS_PRECOND_LEARNED = 2, RS_PRECOND_CG = 3 };
 
 typedef struct rs_grid rs_grid;
 typedef struct rs_proj rs_proj;
@@ -159,8 +163,23 @@ int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi, void *hps
  * device word after the work queued before it.  Errors: RS_EINVAL, RS_ECUDA. */
 int rs_ham_status(rs_ham *h, int *flags);
 
-/* Algorithmic bytes one rs_ham_apply_block call moves (psi read once, hpsi
- * written once, V, the point map and the projector tables), used for GB/s. */
+/* Clears the status word read by rs_ham_status (blocking). */
+int rs_ham_reset_status(rs_ham *h);
+
+/* Failure-detection test hook (no counterpart in the paper): the number of
+ * bounded barrier tests (each suspends the waiting thread for at most 20 us)
+ * after which a pipeline wait of the FP32 32-state H psi kernel gives up,
+ * sets the status word and leaves the kernel.  tests < 0 restores the
+ * default (100000, about two seconds); 0 makes every wait give up at once,
+ * so a call returns promptly with an incomplete hpsi.  Host-only; takes
+ * effect from the next call. */
+int rs_ham_set_wait_limit(rs_ham *h, int tests);
+
+/* Algorithmic bytes one rs_ham_apply_block call moves, used for GB/s: psi
+ * read once, hpsi written once, V and the point map, one copy of the
+ * projector tables and the projection coefficients.  The projection pass's
+ * second read of the covered psi rows (L2-resident within a block) and of
+ * its own atom-major copy of the tables are not counted. */
 int64_t rs_ham_apply_bytes(const rs_ham *h, int nb, int dtype);
 
 /* Per-launch timing of rs_ham_apply_block (a native profiling aid): while
@@ -224,9 +243,9 @@ int rs_orthonormalize(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int 
 
 /* Allocation-free variant of rs_orthonormalize (no counterpart in the paper:
  * it exists for callers of this library that cannot allocate device memory
- * when they need the operation -- code being captured into a CUDA graph that
- * must not contain allocation nodes, plugins whose host framework owns every
- * device buffer, or loops that forbid cudaMalloc after start-up).
+ * when they need the operation -- plugins whose host framework owns every
+ * device buffer and hands out no workspace, or loops that forbid cudaMalloc
+ * after start-up because an allocation can block or fail mid-run).
  * Same operation and arguments as rs_orthonormalize minus the workspace and
  * the U^-1 output; the scratch lives in one fixed __device__ array inside
  * this library, sized for nst <= 256 states (about 2 MB, held by every GPU
@@ -235,16 +254,18 @@ int rs_orthonormalize(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int 
  *  - The call allocates nothing (no cudaMalloc / cudaFree, no allocating
  *    library routine).
  *  - The first call on each device looks up the array's device address on
- *    that device (cudaGetSymbolAddress); make that first call outside any
- *    stream capture.
+ *    that device (cudaGetSymbolAddress).
+ *  - The call is blocking: it reads the factorisation status back to the
+ *    host and synchronises `stream` before it returns, so it must not be
+ *    issued on a stream that is being captured.
  *  - All calls share the one array: calls that overlap on the GPU (from
  *    different host threads or streams) race and must be serialised by the
  *    caller.  The call writes every scratch word it reads before reading it.
- * Blocking.  Errors: RS_EINVAL, RS_ENOTSPD (Psi left unchanged), RS_ECUDA. */
+ * Errors: RS_EINVAL, RS_ENOTSPD (Psi left unchanged), RS_ECUDA. */
 int rs_orthonormalize_noalloc(const rs_grid *g, void *Psi_dev, int64_t ld, int nst, int dtype, void *stream);
 
-/* Dense symmetric eigensolver of the Rayleigh-Ritz step (Sec. VI: "the
- * subspace Hamiltonian is diagonalised", there on the CPU with LAPACK):
+/* Dense symmetric eigensolver of the Rayleigh-Ritz step (Sec. VI, Eqs. 7-8,
+ * where the paper diagonalises the small matrix on the CPU with LAPACK):
  * A_dev = V diag(w) V^T, eigenvalues ascending, A_dev device double [n][n]
  * (read only), w_dev [n], V_dev [n][n] (columns are eigenvectors).
  *   refine > 0: FP32 cyclic Jacobi, `refine` FP64 refinement steps
@@ -277,9 +298,25 @@ typedef struct {
     int nst;              /* states (a multiple of nb) */
     int nb;               /* block size: power of two, 1..64 */
     int dtype;            /* RS_F64 or RS_F32 */
-    int precond;          /* RS_PRECOND_* */
+    int precond;          /* RS_PRECOND_NONE, _FILTER or _LEARNED */
     double tol;           /* residual-norm threshold per state */
     double filter_alpha;  /* filter weight alpha (0.5) */
+    /* The schedules below look at the largest residual norm r of the lowest
+     * n_wanted states after each sweep (0 = all nst; the top block is
+     * usually a convergence buffer whose states are not wanted). */
+    int n_wanted;
+    /* Learned-preconditioner fallback: once stall_sweeps sweeps in a row
+     * leave r above stall_ratio times its best value so far, the solver
+     * switches to the plain filter for good (0 = never; e.g. 3 and 0.9). */
+    int stall_sweeps;
+    double stall_ratio;
+    /* RS_F32 solvers: the eigenvalues a step reports come from the closing
+     * FP64 Rayleigh-Ritz (rs_solver_rayleigh_ritz_f64, timed inside the step)
+     * at every sweep with r <= rr64_always, and every rr64_every sweeps once
+     * r <= rr64_below (rr64_every = 0: never; e.g. 10, 3e-3, 1e-4). */
+    int rr64_every;
+    double rr64_below;
+    double rr64_always;
 } rs_solver_cfg;
 
 /* Creates a solver and allocates its device workspace (blocking).
@@ -287,10 +324,30 @@ typedef struct {
  * orthonormalised and subspace-diagonalised. */
 int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void *Psi0_dev, void *stream, rs_solver **out);
 
-/* One sweep over all blocks (see above).  eps_dev / resnorm_dev: device
- * double [nst] (may be NULL); n_converged: host, states with residual norm
- * <= tol (may be NULL).  Blocking (reads the convergence count). */
+/* One sweep over all blocks (see above), then the schedules of
+ * rs_solver_cfg.  eps_dev / resnorm_dev: device double [nst] (may be NULL);
+ * eps_dev receives the sweep's Ritz values, or the FP64 Rayleigh-Ritz
+ * eigenvalues when the schedule took that step (rs_solver_stats says which);
+ * resnorm_dev the residual norms the sweep measured.  n_converged: host,
+ * states with residual norm <= tol (may be NULL).  Blocking (reads the
+ * residuals).  Errors: RS_ENAN (a non-finite residual), RS_ETIMEOUT (a
+ * bounded wait of an H psi or tensor-core kernel gave up: the sweep's
+ * result is incomplete), RS_ECUDA. */
 int rs_eigensolver_step(rs_solver *s, double *eps_dev, double *resnorm_dev, int *n_converged, void *stream);
+
+typedef struct {
+    int sweeps;                   /* sweeps taken */
+    int eps_f64;                  /* 1 when the last step's eigenvalues came from an FP64 Rayleigh-Ritz
+                                   * (always 1 for RS_F64 solvers) */
+    int precond;                  /* RS_PRECOND_* in use now */
+    int fallback_sweep;           /* sweep after which the learned preconditioner gave way to the filter (0: not) */
+    double max_residual;          /* largest residual norm of the wanted states in the last sweep */
+    double train_target_seconds;  /* last rs_precond_train: residuals and CG targets (wall clock) */
+    double train_fit_seconds;     /* last rs_precond_train: tile cutting and Adam steps (wall clock) */
+} rs_solver_stats_t;
+
+/* Host-side statistics of the solver (no device work). */
+int rs_solver_stats(rs_solver *s, rs_solver_stats_t *out);
 
 /* ------------------------------------------------ learned preconditioner --
  * Not in the paper (its preconditioner is the filter of Sec. III).  The
@@ -344,8 +401,48 @@ typedef struct {
  * solutions), inputs and targets scaled by the residual's rms.  w_dev holds
  * the initial FP32 master weights and receives the trained ones; loss_host
  * (may be NULL) receives the mean loss of every epoch.  Blocking. */
-int rs_precond_train(rs_ham *h, const rs_grid *g, const float *R_dev, const float *X_dev, int64_t ld, int ncols,
-                     const rs_train_cfg *cfg, float *w_dev, float *loss_host, void *stream);
+int rs_precond_train_pairs(rs_ham *h, const rs_grid *g, const float *R_dev, const float *X_dev, int64_t ld, int ncols,
+                           const rs_train_cfg *cfg, float *w_dev, float *loss_host, void *stream);
+
+/* Adam on caller-provided dense tiles (the training kernels alone):
+ * x_dev, target_dev FP32 [ntiles][D^3], mask_dev [ntiles][D^3] and valid_dev
+ * [D^3] bytes as in rs_convnet_tiles.  `epochs` passes over the tiles in
+ * order, one Adam step (beta = 0.9, 0.999; eps = 1e-8; moments zero at the
+ * start) per batch of `batch` consecutive tiles, a last partial batch
+ * dropped; each step's loss is the mean over the batch's valid grid points.
+ * w_dev: initial FP32 weights, receives the trained ones.  Blocking. */
+int rs_precond_train_tiles(float *w_dev, const float *x_dev, const uint8_t *mask_dev, const float *target_dev,
+                           const uint8_t *valid_dev, int ntiles, int D, int batch, int epochs, float lr,
+                           float *loss_host, void *stream);
+
+typedef struct {
+    int n_res;          /* residual columns: the Ritz residuals of the lowest n_res states (<= 256) */
+    int cg_iters;       /* CG iterations of the targets (200) */
+    double sigma;       /* shift of the target operator -1/2 Lap + sigma (1 Ha) */
+    rs_train_cfg train; /* tiles and Adam */
+} rs_learn_cfg;
+
+/* The learned mode of an RS_F32 solver created with RS_PRECOND_LEARNED, in
+ * one call: the Ritz residuals of its lowest n_res states, their targets
+ * (cg_iters CG iterations on (-1/2 Lap + sigma) X = R from X = 0, on a
+ * Hamiltonian of grid g with V = sigma and no projectors), each target
+ * column scaled to unit rms, training on tiles of the pairs
+ * (rs_precond_train_pairs), and the trained weights set as the solver's.
+ * w_init_dev: FP32 [2160] starting weights (not modified), or NULL to
+ * continue from the solver's current weights (for training again on the
+ * residuals of a later sweep).  loss_host: train.epochs floats or NULL.
+ * Blocking.  Errors: RS_EINVAL (solver not learned / not FP32, sizes, no
+ * weights to start from), RS_ENOMEM. */
+int rs_precond_train(rs_solver *s, const rs_grid *g, const rs_learn_cfg *cfg, const float *w_init_dev,
+                     float *loss_host, void *stream);
+
+/* The solver's learned weights to / from a file: the 4 bytes "RSNN", then
+ * little-endian uint32 version (1), uint32 count (2160), the FP32 weights,
+ * and the uint32 FNV-1a hash of the weight bytes.  Load needs a solver whose
+ * preconditioner is the learned one and rejects files that do not match
+ * (RS_EINVAL) or hold non-finite weights (RS_ENAN).  Blocking. */
+int rs_precond_save(rs_solver *s, const char *path);
+int rs_precond_load(rs_solver *s, const char *path);
 
 /* FP64 Rayleigh-Ritz of the solver's current subspace (Sec. VI, Eq. 7): the
  * FP32 orbitals of an RS_F32 solver are widened to FP64, H is applied in
@@ -370,11 +467,12 @@ int rs_solver_psi(rs_solver *s, void **psi_dev);
 
 /* Weights of the learned preconditioner (RS_PRECOND_LEARNED, FP32 F32-mode
  * solvers only): w_dev is the 2160-value FP32 array described above (copied).
- * Until weights are set the learned preconditioner refuses to run. */
+ * Until weights are set the learned preconditioner refuses to run.
+ * Errors: RS_EINVAL when the solver's preconditioner is not the learned one. */
 int rs_solver_set_precond_weights(rs_solver *s, const float *w_dev);
 
 /* Replaces the solver's preconditioner (RS_PRECOND_NONE / FILTER / LEARNED;
- * a new learned preconditioner needs its weights set again) for the sweeps
+ * a learned one takes the weights last set or trained, if any) for the sweeps
  * that follow, e.g. the plain filter as the fallback once the learned one
  * stops reducing the residuals.  Blocking (waits for queued sweeps).
  * Errors: RS_EINVAL. */

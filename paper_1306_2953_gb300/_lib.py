@@ -13,11 +13,11 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsdft.so")
 
-RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENOTSPD, RS_ENOCONV, RS_ENAN = 0, -1, -2, -3, -4, -5, -6
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENOTSPD, RS_ENOCONV, RS_ENAN, RS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 RS_F64, RS_F32 = 0, 1
-RS_PRECOND_NONE, RS_PRECOND_FILTER, RS_PRECOND_LEARNED = 0, 1, 2
+RS_PRECOND_NONE, RS_PRECOND_FILTER, RS_PRECOND_LEARNED, RS_PRECOND_CG = 0, 1, 2, 3
 _NAMES = {RS_EINVAL: "RS_EINVAL", RS_ENOMEM: "RS_ENOMEM", RS_ECUDA: "RS_ECUDA", RS_ENOTSPD: "RS_ENOTSPD",
-          RS_ENOCONV: "RS_ENOCONV", RS_ENAN: "RS_ENAN"}
+          RS_ENOCONV: "RS_ENOCONV", RS_ENAN: "RS_ENAN", RS_ETIMEOUT: "RS_ETIMEOUT"}
 
 
 class RsError(RuntimeError):
@@ -38,7 +38,19 @@ class TrainCfg(ctypes.Structure):
 
 class SolverCfg(ctypes.Structure):
     _fields_ = [("nst", ctypes.c_int), ("nb", ctypes.c_int), ("dtype", ctypes.c_int), ("precond", ctypes.c_int),
-                ("tol", ctypes.c_double), ("filter_alpha", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("filter_alpha", ctypes.c_double), ("n_wanted", ctypes.c_int),
+                ("stall_sweeps", ctypes.c_int), ("stall_ratio", ctypes.c_double), ("rr64_every", ctypes.c_int),
+                ("rr64_below", ctypes.c_double), ("rr64_always", ctypes.c_double)]
+
+
+class SolverStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("eps_f64", ctypes.c_int), ("precond", ctypes.c_int),
+                ("fallback_sweep", ctypes.c_int), ("max_residual", ctypes.c_double),
+                ("train_target_seconds", ctypes.c_double), ("train_fit_seconds", ctypes.c_double)]
+
+
+class LearnCfg(ctypes.Structure):
+    _fields_ = [("n_res", ctypes.c_int), ("cg_iters", ctypes.c_int), ("sigma", ctypes.c_double), ("train", TrainCfg)]
 
 
 P = ctypes.c_void_p
@@ -65,6 +77,8 @@ SIGNATURES = {
     "rs_ham_apply_block": (None, [P, P, I64, P, I64, I32, I32, P]),
     "rs_ham_apply_bytes": (I64, [P, I32, I32]),
     "rs_ham_status": (None, [P, P]),
+    "rs_ham_reset_status": (None, [P]),
+    "rs_ham_set_wait_limit": (None, [P, I32]),
     "rs_ham_timing": (None, [P, I32]),
     "rs_ham_timing_read": (None, [P, P, P, P]),
     "rs_ham_launch_bytes": (None, [P, I32, I32, P, P]),
@@ -80,6 +94,7 @@ SIGNATURES = {
     "rs_subspace_diag": (None, [P, P, P, I64, I32, I32, I32, P, P, P, P]),
     "rs_solver_create": (None, [P, ctypes.POINTER(SolverCfg), P, P, PP]),
     "rs_eigensolver_step": (None, [P, P, P, P, P]),
+    "rs_solver_stats": (None, [P, ctypes.POINTER(SolverStats)]),
     "rs_solver_psi": (None, [P, PP]),
     "rs_solver_residual": (None, [P, I32, I32, P, I64, P]),
     "rs_solver_rayleigh_ritz_f64": (None, [P, P, P]),
@@ -90,7 +105,11 @@ SIGNATURES = {
     "rs_shifted_poisson_cg": (None, [P, P, P, I64, I32, I32, I32, P, P]),
     "rs_precond_apply": (None, [P, P, P, I64, P, I64, I32, P]),
     "rs_convnet_tiles": (None, [P, P, P, P, P, I32, I32, P, P, P, P]),
-    "rs_precond_train": (None, [P, P, P, P, I64, I32, ctypes.POINTER(TrainCfg), P, P, P]),
+    "rs_precond_train_pairs": (None, [P, P, P, P, I64, I32, ctypes.POINTER(TrainCfg), P, P, P]),
+    "rs_precond_train_tiles": (None, [P, P, P, P, P, I32, I32, I32, I32, ctypes.c_float, P, P]),
+    "rs_precond_train": (None, [P, P, ctypes.POINTER(LearnCfg), P, P, P]),
+    "rs_precond_save": (None, [P, ctypes.c_char_p]),
+    "rs_precond_load": (None, [P, ctypes.c_char_p]),
     "rs_solver_destroy": (None, [P]),
 }
 

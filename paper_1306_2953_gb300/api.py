@@ -179,6 +179,15 @@ class Hamiltonian:
         call("rs_ham_status", self._h, ctypes.byref(f))
         return int(f.value)
 
+    def reset_status(self):
+        """rs_ham_reset_status: clears the status word (blocking)."""
+        call("rs_ham_reset_status", self._h)
+
+    def set_wait_limit(self, tests: int):
+        """rs_ham_set_wait_limit (failure-detection test hook): barrier tests
+        before a pipeline wait gives up; < 0 restores the default."""
+        call("rs_ham_set_wait_limit", self._h, int(tests))
+
     def close(self):
         if self._h:
             _lib.lib().rs_ham_destroy(self._h)
@@ -234,8 +243,11 @@ class Solver:
     """Block CG (LOBPCG) eigensolver (rs_solver_*)."""
 
     def __init__(self, ham: Hamiltonian, Psi0, nb: int, tol: float, precond: int = _lib.RS_PRECOND_FILTER,
-                 filter_alpha: float = 0.5, stream=None):
-        cfg = _lib.SolverCfg(Psi0.shape[1], nb, dtype_code(Psi0), precond, float(tol), float(filter_alpha))
+                 filter_alpha: float = 0.5, n_wanted: int = 0, stall_sweeps: int = 0, stall_ratio: float = 0.9,
+                 rr64_every: int = 0, rr64_below: float = 0.0, rr64_always: float = 0.0, stream=None):
+        cfg = _lib.SolverCfg(Psi0.shape[1], nb, dtype_code(Psi0), precond, float(tol), float(filter_alpha),
+                             int(n_wanted), int(stall_sweeps), float(stall_ratio), int(rr64_every), float(rr64_below),
+                             float(rr64_always))
         assert Psi0.is_contiguous()
         out = ctypes.c_void_p()
         call("rs_solver_create", ham._h, ctypes.byref(cfg), _c(Psi0.data_ptr()), _stream(stream), ctypes.byref(out))
@@ -254,6 +266,29 @@ class Solver:
         call("rs_eigensolver_step", self._h, _c(eps.data_ptr()), _c(res.data_ptr()), ctypes.byref(nconv),
              _stream(stream))
         return eps, res, nconv.value
+
+    def stats(self) -> dict:
+        """rs_solver_stats as a dict."""
+        st = _lib.SolverStats()
+        call("rs_solver_stats", self._h, ctypes.byref(st))
+        return {k: getattr(st, k) for k, _ in _lib.SolverStats._fields_}
+
+    def train_precond(self, grid: Grid, w_init=None, n_res: int = 40, cg_iters: int = 200, sigma: float = 1.0,
+                      n_tiles: int = 10000, epochs: int = 5, batch: int = 64, lr: float = 1e-3, seed: int = 11,
+                      tile: int = 16, stream=None):
+        """rs_precond_train: residuals, CG targets, training and the weights,
+        all in the library; returns the per-epoch mean losses."""
+        cfg = _lib.LearnCfg(n_res, cg_iters, float(sigma), _lib.TrainCfg(n_tiles, tile, epochs, batch, lr, seed))
+        losses = (ctypes.c_float * max(epochs, 1))()
+        call("rs_precond_train", self._h, grid._h, ctypes.byref(cfg),
+             _c(w_init.data_ptr()) if w_init is not None else None, losses, _stream(stream))
+        return list(losses)[:epochs]
+
+    def save_precond(self, path: str):
+        call("rs_precond_save", self._h, str(path).encode())
+
+    def load_precond(self, path: str):
+        call("rs_precond_load", self._h, str(path).encode())
 
     def psi(self):
         """The solver's orbitals as a torch tensor view [npts, nst] (no copy)."""
@@ -362,8 +397,17 @@ def precond_train(ham: Hamiltonian, R, X, w, n_tiles: int, epochs: int, batch: i
     of (R, X) column pairs; returns the per-epoch mean losses."""
     cfg = _lib.TrainCfg(n_tiles, tile, epochs, batch, lr, seed)
     losses = (ctypes.c_float * max(epochs, 1))()
-    call("rs_precond_train", ham._h, ham.grid._h, _c(R.data_ptr()), _c(X.data_ptr()), R.stride(0), R.shape[1],
+    call("rs_precond_train_pairs", ham._h, ham.grid._h, _c(R.data_ptr()), _c(X.data_ptr()), R.stride(0), R.shape[1],
          ctypes.byref(cfg), _c(w.data_ptr()), losses, _stream(stream))
+    return list(losses)[:epochs]
+
+
+def precond_train_tiles(w, x, mask, target, valid, batch: int, epochs: int, lr: float = 1e-3, stream=None):
+    """Adam on dense tiles [ntiles, D, D, D] (rs_precond_train_tiles); w (FP32
+    [2160]) is updated in place; returns the per-epoch mean losses."""
+    losses = (ctypes.c_float * max(epochs, 1))()
+    call("rs_precond_train_tiles", _c(w.data_ptr()), _c(x.data_ptr()), _c(mask.data_ptr()), _c(target.data_ptr()),
+         _c(valid.data_ptr()), x.shape[0], x.shape[1], batch, epochs, float(lr), losses, _stream(stream))
     return list(losses)[:epochs]
 
 

@@ -27,6 +27,12 @@ namespace rs {
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Raises the dynamic shared-memory limit of kernel `fn` on the current
+// device to at least `bytes`.  The attribute belongs to a (function, device)
+// pair, so the grant is remembered per pair and later calls with a size
+// already granted cost one table lookup.
+int smem_optin(const void *fn, size_t bytes);
+
 // Device buffer owned by a handle.
 struct DevBuf {
     void *p = nullptr;

@@ -682,11 +682,7 @@ template <typename T, int SG, int TX, int TY>
 static int launch_stencil(rs_ham *H, const HamDev<T> &d, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, int nb,
                           cudaStream_t st) {
     using C = StencilCfg<T, SG, TX, TY>;
-    static bool attr_done = false;  // per instantiation; set once per process
-    if (!attr_done) {
-        RS_CUDA(cudaFuncSetAttribute(k_stencil<T, SG, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
-        attr_done = true;
-    }
+    RS_TRY(smem_optin((const void *)k_stencil<T, SG, TX, TY>, C::SMEM));
     const WorkList *wl = H->work.at({TX, TY});
     if (wl->count == 0) return RS_OK;
     dim3 grid((unsigned)wl->count, (unsigned)(nb / SG));
@@ -776,9 +772,13 @@ extern "C" int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi
 }
 
 extern "C" int64_t rs_ham_apply_bytes(const rs_ham *h, int nb, int dtype) {
-    int64_t a = 0, b = 0;
-    if (rs_ham_launch_bytes(h, nb, dtype, &a, &b) != RS_OK) return -1;
-    return a + b;
+    // psi read once, hpsi written once, V and the point map, one copy of the
+    // projector tables and the coefficients: the bytes of the fused launch
+    // (the projection pass re-reads rows that stay in L2 and its own copy of
+    // the tables, which are not counted again)
+    int64_t b = 0;
+    if (rs_ham_launch_bytes(h, nb, dtype, nullptr, &b) != RS_OK) return -1;
+    return b;
 }
 
 extern "C" int rs_ham_launch_bytes(const rs_ham *h, int nb, int dtype, int64_t *project_bytes, int64_t *stencil_bytes) {
@@ -797,6 +797,21 @@ extern "C" int rs_ham_status(rs_ham *h, int *flags) {
     *flags = f;
     return RS_OK;
 }
+
+extern "C" int rs_ham_reset_status(rs_ham *h) {
+    if (!h) return fail(RS_EINVAL, "rs_ham_reset_status: null handle");
+    return ring_reset_status(h->ring);
+}
+
+extern "C" int rs_ham_set_wait_limit(rs_ham *h, int tests) {
+    if (!h) return fail(RS_EINVAL, "rs_ham_set_wait_limit: null handle");
+    ring_set_wait_limit(h->ring, tests);
+    return RS_OK;
+}
+
+namespace rs {
+int *ham_status_word(rs_ham *h) { return ring_status_word(h->ring); }
+}  // namespace rs
 
 extern "C" int rs_ham_timing(rs_ham *h, int enable) {
     if (!h) return fail(RS_EINVAL, "rs_ham_timing: null handle");

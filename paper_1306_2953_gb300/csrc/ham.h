@@ -14,6 +14,9 @@ double ham_dV(const rs_ham *h);
 const int32_t *ham_map(const rs_ham *h);   // device point map [d0][d1][d2]
 const int32_t *ham_loc(const rs_ham *h);   // device linear map index of every point
 int ham_dim(const rs_ham *h, int axis);
+// Device status word of the H psi kernel's bounded waits (nullptr when the
+// handle has no such kernel): nonzero once a wait gave up.
+int *ham_status_word(rs_ham *h);
 struct DevBuf;
 // Device scratch owned by h, grown to at least `bytes` (nullptr on failure).
 DevBuf *ham_scratch(rs_ham *h, size_t bytes);

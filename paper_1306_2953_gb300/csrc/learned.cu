@@ -254,13 +254,8 @@ __global__ void k_tile_bwd_weight(const float *__restrict__ gout, const float *_
 template <int CIN, int COUT> int tile_bwd_weight(const float *gout, const float *in, int ntiles, int D, float *dW,
                                                  cudaStream_t st) {
     const size_t sm = sizeof(float) * (size_t)(COUT * WB_PLANES + CIN * (WB_PLANES + 2)) * D * D;
-    static bool attr = false;
-    if (!attr) {
-        RS_CUDA(cudaFuncSetAttribute(k_tile_bwd_weight<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     200 * 1024));
-        attr = true;
-    }
     if (sm > 200 * 1024) return fail(RS_EINVAL, "tile_bwd_weight: tile too large");
+    RS_TRY(smem_optin((const void *)k_tile_bwd_weight<CIN, COUT>, sm));
     const int threads = ((CIN * 27 + 31) / 32) * 32;
     k_tile_bwd_weight<CIN, COUT><<<dim3((unsigned)ntiles, (unsigned)((D + WB_PLANES - 1) / WB_PLANES)), threads, sm, st>>>(
         gout, in, ntiles, D, dW);
@@ -541,13 +536,78 @@ static uint64_t splitmix64(uint64_t &s) {
     return z ^ (z >> 31);
 }
 
-extern "C" int rs_precond_train(rs_ham *h, const rs_grid *g, const float *R_dev, const float *X_dev, int64_t ld,
-                                int ncols, const rs_train_cfg *cfg, float *w_dev, float *loss_host, void *stream) {
-    if (!h || !g || !R_dev || !X_dev || !cfg || !w_dev) return fail(RS_EINVAL, "rs_precond_train: null argument");
-    const rs_train_cfg c = *cfg;
-    if (ncols < 1 || ncols > 256 || ld < ncols || c.n_tiles < 1 || c.batch < 1 || c.epochs < 0 || c.tile < 1)
-        return fail(RS_EINVAL, "rs_precond_train: bad sizes");
-    cudaStream_t st = (cudaStream_t)stream;
+namespace rs {
+
+// Adam on dense tiles already cut: `epochs` passes over the tiles in order,
+// one step per batch of `batch` consecutive tiles (a last partial batch is
+// dropped), moments zero at the start.  loss_host[ep] (may be NULL) gets the
+// mean batch loss of epoch ep.  Blocking.
+int train_tiles_impl(float *w_dev, const float *xin, const float *tgt, const uint8_t *msk, const uint8_t *dvalid,
+                     int ntiles, int D, int batch, int epochs, float lr, float *loss_host, cudaStream_t st) {
+    const int D3 = D * D * D;
+    const int64_t ntot = (int64_t)ntiles * D3;
+    const int B = std::min(batch, ntiles);
+    DevBuf ws, grad, m, v, dl;
+    RS_TRY(ws.alloc(TileBufs::floats(B, D) * sizeof(float)));
+    RS_TRY(grad.alloc(sizeof(float) * W_TOTAL));
+    RS_TRY(m.alloc(sizeof(float) * W_TOTAL));
+    RS_TRY(v.alloc(sizeof(float) * W_TOTAL));
+    RS_TRY(dl.alloc(sizeof(double)));
+    RS_CUDA(cudaMemsetAsync(m.p, 0, sizeof(float) * W_TOTAL, st));
+    RS_CUDA(cudaMemsetAsync(v.p, 0, sizeof(float) * W_TOTAL, st));
+    // number of valid points (interior grid points) of every tile, for the mean
+    std::vector<int> tvalid((size_t)ntiles, 0);
+    {
+        std::vector<uint8_t> hm((size_t)ntot), valid((size_t)D3);
+        RS_CUDA(cudaMemcpyAsync(hm.data(), msk, hm.size(), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaMemcpyAsync(valid.data(), dvalid, valid.size(), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> vidx;
+        for (int e = 0; e < D3; ++e)
+            if (valid[e]) vidx.push_back(e);
+        for (int n = 0; n < ntiles; ++n) {
+            const uint8_t *tm = hm.data() + (size_t)n * D3;
+            int cnt = 0;
+            for (int e : vidx) cnt += tm[e] != 0;
+            tvalid[n] = cnt;
+        }
+    }
+    TileBufs b(ws.as<float>(), B, D);
+    int step = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        RS_CUDA(cudaMemsetAsync(dl.p, 0, sizeof(double), st));
+        int nbatches = 0;
+        for (int t0 = 0; t0 + B <= ntiles; t0 += B, ++nbatches) {
+            int nvalid = 0;
+            for (int n = t0; n < t0 + B; ++n) nvalid += tvalid[n];
+            const float *x0 = xin + (int64_t)t0 * D3;
+            const uint8_t *mk = msk + (int64_t)t0 * D3;
+            k_round_weights<<<9, 256, 0, st>>>(w_dev, b.wq, W_TOTAL);
+            RS_LAUNCH_CHECK();
+            RS_TRY(tile_forward(b.wq, x0, mk, B, D, b, st));
+            const int64_t n = (int64_t)B * D3;
+            k_tile_loss<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b.y, tgt + (int64_t)t0 * D3, mk, dvalid, B, D,
+                                                                    1.0 / std::max(nvalid, 1), b.g3, dl.as<double>());
+            RS_CUDA(cudaMemsetAsync(grad.p, 0, sizeof(float) * W_TOTAL, st));
+            RS_TRY(tile_backward(b.wq, x0, mk, B, D, b, grad.as<float>(), st));
+            ++step;
+            k_adam<<<(W_TOTAL + 255) / 256, 256, 0, st>>>(w_dev, grad.as<float>(), m.as<float>(), v.as<float>(), W_TOTAL,
+                                                          lr, 0.9f, 0.999f, 1e-8f, step);
+            RS_LAUNCH_CHECK();
+        }
+        double tot = 0;
+        RS_CUDA(cudaMemcpyAsync(&tot, dl.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+        if (loss_host) loss_host[ep] = (float)(tot / std::max(nbatches, 1));
+    }
+    RS_CUDA(cudaStreamSynchronize(st));
+    return RS_OK;
+}
+
+// Cuts c.n_tiles tiles around random grid points of the column pairs (R, X),
+// inputs and targets scaled by the residual column's rms, and trains on them.
+int train_pairs_impl(const rs_ham *h, const rs_grid *g, const float *R_dev, const float *X_dev, int64_t ld, int ncols,
+                     const rs_train_cfg &c, float *w_dev, float *loss_host, cudaStream_t st) {
     const int D = c.tile + 6, D3 = D * D * D;
     const int64_t np = g->npts;
     // tile positions: a random grid point of a random column at the tile centre
@@ -563,7 +623,7 @@ extern "C" int rs_precond_train(rs_ham *h, const rs_grid *g, const float *R_dev,
     for (int i = 3; i < D - 3; ++i)
         for (int j = 3; j < D - 3; ++j)
             for (int k = 3; k < D - 3; ++k) valid[((size_t)i * D + j) * D + k] = 1;
-    DevBuf dorg, dvalid, xin, tgt, msk, ss, rms, ws, grad, m, v, dl;
+    DevBuf dorg, dvalid, xin, tgt, msk, ss, rms;
     RS_TRY(dorg.upload(org.data(), org.size() * sizeof(int4)));
     RS_TRY(dvalid.upload(valid.data(), valid.size()));
     RS_TRY(xin.alloc((size_t)c.n_tiles * D3 * sizeof(float)));
@@ -579,57 +639,30 @@ extern "C" int rs_precond_train(rs_ham *h, const rs_grid *g, const float *R_dev,
         ham_map(h), g->dims[0], g->dims[1], g->dims[2], R_dev, X_dev, ld, rms.as<double>(), dorg.as<int4>(), c.n_tiles,
         D, xin.as<float>(), tgt.as<float>(), msk.as<uint8_t>());
     RS_LAUNCH_CHECK();
-    const int B = std::min(c.batch, c.n_tiles);
-    RS_TRY(ws.alloc(TileBufs::floats(B, D) * sizeof(float)));
-    RS_TRY(grad.alloc(sizeof(float) * W_TOTAL));
-    RS_TRY(m.alloc(sizeof(float) * W_TOTAL));
-    RS_TRY(v.alloc(sizeof(float) * W_TOTAL));
-    RS_TRY(dl.alloc(sizeof(double)));
-    RS_CUDA(cudaMemsetAsync(m.p, 0, sizeof(float) * W_TOTAL, st));
-    RS_CUDA(cudaMemsetAsync(v.p, 0, sizeof(float) * W_TOTAL, st));
-    // number of valid points (interior grid points) of every tile, for the mean
-    std::vector<int> tvalid((size_t)c.n_tiles, 0);
-    {
-        std::vector<uint8_t> hm((size_t)ntot);
-        RS_CUDA(cudaMemcpyAsync(hm.data(), msk.p, hm.size(), cudaMemcpyDeviceToHost, st));
-        RS_CUDA(cudaStreamSynchronize(st));
-        for (int n = 0; n < c.n_tiles; ++n) {
-            const uint8_t *tm = hm.data() + (size_t)n * D3;
-            int cnt = 0;
-            for (int e = 0; e < D3; ++e) cnt += tm[e] && valid[e];
-            tvalid[n] = cnt;
-        }
-    }
-    TileBufs b(ws.as<float>(), B, D);
-    int step = 0;
-    for (int ep = 0; ep < c.epochs; ++ep) {
-        RS_CUDA(cudaMemsetAsync(dl.p, 0, sizeof(double), st));
-        int nbatches = 0;
-        for (int t0 = 0; t0 + B <= c.n_tiles; t0 += B, ++nbatches) {
-            int nvalid = 0;
-            for (int n = t0; n < t0 + B; ++n) nvalid += tvalid[n];
-            const float *x0 = xin.as<float>() + (int64_t)t0 * D3;
-            const uint8_t *mk = msk.as<uint8_t>() + (int64_t)t0 * D3;
-            k_round_weights<<<9, 256, 0, st>>>(w_dev, b.wq, W_TOTAL);
-            RS_LAUNCH_CHECK();
-            RS_TRY(tile_forward(b.wq, x0, mk, B, D, b, st));
-            const int64_t n = (int64_t)B * D3;
-            k_tile_loss<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b.y, tgt.as<float>() + (int64_t)t0 * D3, mk,
-                                                                    dvalid.as<uint8_t>(), B, D,
-                                                                    1.0 / std::max(nvalid, 1), b.g3, dl.as<double>());
-            RS_CUDA(cudaMemsetAsync(grad.p, 0, sizeof(float) * W_TOTAL, st));
-            RS_TRY(tile_backward(b.wq, x0, mk, B, D, b, grad.as<float>(), st));
-            ++step;
-            k_adam<<<(W_TOTAL + 255) / 256, 256, 0, st>>>(w_dev, grad.as<float>(), m.as<float>(), v.as<float>(), W_TOTAL,
-                                                          c.lr, 0.9f, 0.999f, 1e-8f, step);
-            RS_LAUNCH_CHECK();
-        }
-        double tot = 0;
-        RS_CUDA(cudaMemcpyAsync(&tot, dl.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-        RS_CUDA(cudaStreamSynchronize(st));
-        if (loss_host) loss_host[ep] = (float)(tot / std::max(nbatches, 1));
-    }
-    return RS_OK;
+    return train_tiles_impl(w_dev, xin.as<float>(), tgt.as<float>(), msk.as<uint8_t>(), dvalid.as<uint8_t>(), c.n_tiles,
+                            D, c.batch, c.epochs, c.lr, loss_host, st);
+}
+
+}  // namespace rs
+
+extern "C" int rs_precond_train_pairs(rs_ham *h, const rs_grid *g, const float *R_dev, const float *X_dev, int64_t ld,
+                                      int ncols, const rs_train_cfg *cfg, float *w_dev, float *loss_host, void *stream) {
+    if (!h || !g || !R_dev || !X_dev || !cfg || !w_dev) return fail(RS_EINVAL, "rs_precond_train_pairs: null argument");
+    const rs_train_cfg c = *cfg;
+    if (ncols < 1 || ncols > 256 || ld < ncols || c.n_tiles < 1 || c.batch < 1 || c.epochs < 0 || c.tile < 1)
+        return fail(RS_EINVAL, "rs_precond_train_pairs: bad sizes");
+    if (ham_npts(h) != g->npts) return fail(RS_EINVAL, "rs_precond_train_pairs: grid and Hamiltonian differ");
+    return train_pairs_impl(h, g, R_dev, X_dev, ld, ncols, c, w_dev, loss_host, (cudaStream_t)stream);
+}
+
+extern "C" int rs_precond_train_tiles(float *w_dev, const float *x_dev, const uint8_t *mask_dev, const float *target_dev,
+                                      const uint8_t *valid_dev, int ntiles, int D, int batch, int epochs, float lr,
+                                      float *loss_host, void *stream) {
+    if (!w_dev || !x_dev || !mask_dev || !target_dev || !valid_dev) return fail(RS_EINVAL, "rs_precond_train_tiles: null argument");
+    if (ntiles < 1 || D < 3 || D > 64 || batch < 1 || epochs < 0 || !(lr > 0))
+        return fail(RS_EINVAL, "rs_precond_train_tiles: bad sizes");
+    return train_tiles_impl(w_dev, x_dev, target_dev, mask_dev, valid_dev, ntiles, D, batch, epochs, lr, loss_host,
+                            (cudaStream_t)stream);
 }
 
 // ----------------------------------------------------- solver plug-in ---

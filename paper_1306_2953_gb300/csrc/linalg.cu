@@ -187,7 +187,7 @@ int rowmul(const T *X, int64_t ldx, int n, const double *C, int64_t ldc, int m, 
            double alpha, double beta, cudaStream_t st) {
     const size_t smem = (size_t)R_ROWS * n * sizeof(T);
     if (smem > 200 * 1024) return fail(RS_EINVAL, "rowmul: n too large");
-    if (smem > 48 * 1024) RS_CUDA(cudaFuncSetAttribute(k_rowmul<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) RS_TRY(smem_optin((const void *)k_rowmul<T>, smem));
     const int64_t blocks = (npts + R_ROWS - 1) / R_ROWS;
     k_rowmul<T><<<(unsigned)blocks, R_NT, smem, st>>>(X, ldx, n, C, ldc, m, Y, ldy, npts, (T)alpha, (T)beta);
     RS_LAUNCH_CHECK();
@@ -316,12 +316,7 @@ int cholesky(double *A, int lda, int n, double rel, int *status_dev, cudaStream_
     if (n > CHOL_MAX) return fail(RS_EINVAL, "cholesky: n > %d", CHOL_MAX);
     if (n <= CHOL_SMEM_MAX) {
         const size_t sm = sizeof(double) * (size_t)n * n;
-        static bool attr = false;
-        if (!attr) {
-            RS_CUDA(cudaFuncSetAttribute(k_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * CHOL_SMEM_MAX * CHOL_SMEM_MAX)));
-            attr = true;
-        }
+        RS_TRY(smem_optin((const void *)k_chol<true>, sm));
         k_chol<true><<<1, 1024, sm, st>>>(A, lda, n, rel, status_dev);
     } else {
         k_chol<false><<<1, 1024, 0, st>>>(A, lda, n, rel, status_dev);
@@ -333,13 +328,7 @@ int cholesky(double *A, int lda, int n, double rel, int *status_dev, cudaStream_
 int tri_inv(const double *U, int ldu, int n, double *X, int ldx, cudaStream_t st) {
     constexpr int WPB = 8;   // columns (warps) per CTA
     const size_t sm = sizeof(double) * (size_t)WPB * n;
-    if (sm > 48 * 1024) {
-        static int attr = 0;
-        if ((int)sm > attr) {
-            RS_CUDA(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            attr = (int)sm;
-        }
-    }
+    if (sm > 48 * 1024) RS_TRY(smem_optin((const void *)k_trinv, sm));
     k_trinv<<<(n + WPB - 1) / WPB, 32 * WPB, sm, st>>>(U, ldu, n, X, ldx);
     RS_LAUNCH_CHECK();
     return RS_OK;
@@ -921,18 +910,10 @@ int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *
         int *perm = reinterpret_cast<int *>(rot + jacobi_log_elems(n, max_sweeps));
         const size_t fs = jacobi_full_smem(n, sizeof(T));
         if (sizeof(T) == 4 && fs <= JACOBI_PK_MAX_SMEM) {
-            static int fs_attr = 0;
-            if ((int)fs > fs_attr) {
-                RS_CUDA(cudaFuncSetAttribute(k_jacobi_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
-                fs_attr = (int)fs;
-            }
+            RS_TRY(smem_optin((const void *)k_jacobi_full<T>, fs));
             k_jacobi_full<T><<<1, 1024, fs, st>>>(A, lda, n, max_sweeps, tol, rot, w, perm, info);
         } else {
-            static int pk_attr = 0;   // largest dynamic shared memory granted so far (per instantiation)
-            if ((int)pk > pk_attr) {
-                RS_CUDA(cudaFuncSetAttribute(k_jacobi_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk));
-                pk_attr = (int)pk;
-            }
+            RS_TRY(smem_optin((const void *)k_jacobi_pk<T>, pk));
             k_jacobi_pk<T><<<1, 1024, pk, st>>>(A, lda, n, max_sweeps, tol, rot, w, perm, info);
         }
         RS_LAUNCH_CHECK();

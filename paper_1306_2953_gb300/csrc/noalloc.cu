@@ -2,13 +2,14 @@
 //
 // rs_orthonormalize needs a device workspace that the caller allocates.
 // Some callers cannot allocate device memory at the point where they need
-// the operation: code running inside a CUDA stream capture that must not
-// add allocation nodes, plugins handed pre-allocated buffers by a host
-// framework that owns all device memory, or real-time loops that forbid
-// cudaMalloc after start-up.  rs_orthonormalize_noalloc serves them: its
-// scratch (overlap matrix, Cholesky factor, inverse and status word) lives
-// in one file-scope __device__ array of fixed size that every GPU loading
-// this library holds until the process exits.
+// the operation: plugins handed pre-allocated buffers by a host framework
+// that owns all device memory, or real-time loops that forbid cudaMalloc
+// after start-up.  rs_orthonormalize_noalloc serves them: its scratch
+// (overlap matrix, Cholesky factor, inverse and status word) lives in one
+// file-scope __device__ array of fixed size that every GPU loading this
+// library holds until the process exits.  The call is blocking (it reads
+// the factorisation status back and synchronises its stream), so it is not
+// for a stream under capture.
 #include <mutex>
 
 #include "device.h"

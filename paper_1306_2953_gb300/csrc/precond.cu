@@ -24,6 +24,7 @@ class Identity : public Precond {
               cudaStream_t st) override {
         return ham_filter(h, R, ldr, W, ldw, nb, dtype, 1.0, st);
     }
+    int kind() const override { return RS_PRECOND_NONE; }
 };
 
 class Filter : public Precond {
@@ -33,6 +34,7 @@ class Filter : public Precond {
               cudaStream_t st) override {
         return ham_filter(h, R, ldr, W, ldw, nb, dtype, alpha, st);
     }
+    int kind() const override { return RS_PRECOND_FILTER; }
     double alpha;
 };
 
@@ -58,6 +60,7 @@ class Learned : public Precond {
         return learned_apply(h, (const float *)R, ldr, (float *)W, ldw, nb, wq.as<float>(), act.as<float>(),
                              dots.as<double>(), st);
     }
+    int kind() const override { return RS_PRECOND_LEARNED; }
     DevBuf w, wq, act, dots;
     bool ready = false;
 };
@@ -83,6 +86,7 @@ class ShiftedCG : public Precond {
                                   cudaMemcpyDeviceToDevice, st));
         return RS_OK;
     }
+    int kind() const override { return RS_PRECOND_CG; }
     rs_ham *shifted = nullptr;
     int n_iter = 0, nb = 1, es = 4;
     int64_t npts = 0;

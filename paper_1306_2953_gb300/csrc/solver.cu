@@ -18,12 +18,17 @@
 // Gram matrices, residual norms, Cholesky, Rayleigh-Ritz and eigenvalues are
 // FP64 (exact products with compensated accumulation, see linalg.cu).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
 #include <new>
 #include <vector>
 
 #include "device.h"
 #include "ham.h"
+#include "learned.h"
 #include "linalg.h"
 #include "precond.h"
 #include "umma.h"
@@ -149,6 +154,14 @@ struct rs_solver {
     UmmaSplitCache gs_t, gs_n;   // FP32 mode: splits of Psi[:, :(b+1) nb] within a block step
     std::vector<char> has_p;
     Precond *pc = nullptr;
+    // learned preconditioner: the FP32 weights last set or trained
+    DevBuf wlearn;
+    bool has_wlearn = false;
+    // schedules and statistics (rs_solver_stats)
+    int sweeps = 0, eps_f64 = 0, fallback_sweep = 0, stall = 0;
+    double best = std::numeric_limits<double>::infinity(), max_res = 0;
+    double train_target_s = 0, train_fit_s = 0;
+    DevBuf eps64;   // FP64 Rayleigh-Ritz eigenvalues when the caller passes no eps_dev
     // small FP64 buffers (inside `small`)
     double *dots = nullptr, *M = nullptr, *G = nullptr, *A = nullptr, *U = nullptr, *Ui = nullptr, *T1 = nullptr,
            *At = nullptr, *Yv = nullptr, *mu = nullptr, *C = nullptr;
@@ -226,7 +239,12 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
     RS_LAUNCH_CHECK();
     std::vector<double> res(nb);
     RS_CUDA(cudaMemcpyAsync(res.data(), resb, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    // a bounded wait of an earlier H psi launch that gave up leaves incomplete
+    // data behind: stop before it spreads into the residuals
+    int ringerr = 0;
+    if (int *rw = ham_status_word(S->h)) RS_CUDA(cudaMemcpyAsync(&ringerr, rw, sizeof(int), cudaMemcpyDeviceToHost, st));
     RS_CUDA(cudaStreamSynchronize(st));
+    if (ringerr) return fail(RS_ETIMEOUT, "eigensolver: an H psi pipeline wait timed out");
     bool conv = true;
     for (double r : res) {
         if (!std::isfinite(r)) return fail(RS_ENAN, "eigensolver: non-finite residual in block %d", b);
@@ -303,6 +321,54 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
 
 }  // namespace
 
+__global__ void k_widen(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = (double)a[e];
+}
+
+static int rayleigh_ritz_f64_impl(rs_solver *S, double *eps_dev, cudaStream_t st) {
+    const rs_solver_cfg &c = S->cfg;
+    const int n = c.nst;
+    if (c.dtype == RS_F64) {
+        RS_CUDA(cudaMemcpyAsync(eps_dev, S->eig.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+        return RS_OK;
+    }
+    const size_t nn = (size_t)n * n;
+    if (!S->psi64.p) {
+        RS_TRY(S->psi64.alloc(sizeof(double) * (size_t)S->npts * n));
+        RS_TRY(S->hpsi64.alloc(sizeof(double) * (size_t)S->npts * n));
+        RS_TRY(S->rr64.alloc(sizeof(double) * (4 * nn + 16) + eigh_work_bytes(n)));
+    }
+    double *Sm = S->rr64.as<double>(), *h = Sm + nn, *Ui = h + nn, *T = Ui + nn;
+    int *status = reinterpret_cast<int *>(T + nn);
+    void *ew = reinterpret_cast<void *>(T + nn + 16);
+    // FP64 copy of the FP32 orbitals, H applied in FP64
+    k_widen<<<1024, 256, 0, st>>>(S->psi.as<float>(), S->psi64.as<double>(), S->npts * n);
+    RS_LAUNCH_CHECK();
+    for (int b = 0; b < n; b += c.nb)
+        RS_TRY(rs_ham_apply_block(S->h, S->psi64.as<double>() + b, n, S->hpsi64.as<double>() + b, n, c.nb, RS_F64, st));
+    // generalized Rayleigh-Ritz h x = eps S x with S, h accumulated in FP64
+    // (the overlap of the FP32 orbitals is exact: products of FP32 values)
+    RS_TRY(gram<float>(S->psi.as<float>(), n, n, S->psi.as<float>(), n, n, S->npts, S->dV, Sm, n, st));
+    RS_TRY(gram<double>(S->psi64.as<double>(), n, n, S->hpsi64.as<double>(), n, n, S->npts, S->dV, h, n, st));
+    RS_TRY(symmetrize(Sm, n, n, st));
+    RS_TRY(symmetrize(h, n, n, st));
+    RS_TRY(cholesky(Sm, n, n, 1e-14, status, st));
+    RS_TRY(tri_inv(Sm, n, n, Ui, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, Ui, n, true, h, n, false, 0.0, T, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, T, n, false, Ui, n, false, 0.0, h, n, st));
+    RS_TRY(symmetrize(h, n, n, st));
+    RS_TRY(eigh(h, n, n, eps_dev, T, n, 2, status, ew, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    return RS_OK;
+}
+
+extern "C" int rs_solver_rayleigh_ritz_f64(rs_solver *S, double *eps_dev, void *stream) {
+    if (!S || !eps_dev) return fail(RS_EINVAL, "rs_solver_rayleigh_ritz_f64: null argument");
+    return rayleigh_ritz_f64_impl(S, eps_dev, (cudaStream_t)stream);
+}
+
 extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void *Psi0_dev, void *stream,
                                 rs_solver **out) {
     if (!h || !cfg || !Psi0_dev || !out) return fail(RS_EINVAL, "rs_solver_create: null argument");
@@ -312,6 +378,11 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
     if (c.dtype != RS_F64 && c.dtype != RS_F32) return fail(RS_EINVAL, "rs_solver_create: bad dtype");
     if (c.precond < RS_PRECOND_NONE || c.precond > RS_PRECOND_LEARNED) return fail(RS_EINVAL, "rs_solver_create: bad precond");
     if (!(c.tol > 0)) return fail(RS_EINVAL, "rs_solver_create: tol must be > 0");
+    if (c.n_wanted < 0 || c.n_wanted > c.nst) return fail(RS_EINVAL, "rs_solver_create: n_wanted must be in 0 .. nst");
+    if (c.stall_sweeps < 0 || (c.stall_sweeps > 0 && !(c.stall_ratio > 0 && c.stall_ratio <= 1)))
+        return fail(RS_EINVAL, "rs_solver_create: stall_sweeps must be >= 0 and stall_ratio in (0, 1]");
+    if (c.rr64_every < 0 || !(c.rr64_below >= 0) || !(c.rr64_always >= 0))
+        return fail(RS_EINVAL, "rs_solver_create: bad FP64 Rayleigh-Ritz schedule");
     *out = nullptr;
     rs_solver *S = new (std::nothrow) rs_solver;
     if (!S) return fail(RS_ENOMEM, "host allocation failed");
@@ -397,15 +468,65 @@ extern "C" int rs_eigensolver_step(rs_solver *S, double *eps_dev, double *resnor
     if (resnorm_dev) RS_CUDA(cudaMemcpyAsync(resnorm_dev, S->res.p, sizeof(double) * c.nst, cudaMemcpyDeviceToDevice, st));
     std::vector<double> res(c.nst);
     RS_CUDA(cudaMemcpyAsync(res.data(), S->res.p, sizeof(double) * c.nst, cudaMemcpyDeviceToHost, st));
-    int tcerr = 0;
+    // status words of the bounded device waits: the tensor-core pipeline and
+    // the H psi ring (a wait that gave up leaves that launch's result incomplete)
+    int tcerr = 0, ringerr = 0;
     if (S->tc.err) RS_CUDA(cudaMemcpyAsync(&tcerr, S->tc.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (int *rw = ham_status_word(S->h)) RS_CUDA(cudaMemcpyAsync(&ringerr, rw, sizeof(int), cudaMemcpyDeviceToHost, st));
     RS_CUDA(cudaStreamSynchronize(st));
-    if (tcerr) return fail(RS_ECUDA, "eigensolver: a tensor-core pipeline wait timed out");
+    if (tcerr) return fail(RS_ETIMEOUT, "eigensolver: a tensor-core pipeline wait timed out");
+    if (ringerr) return fail(RS_ETIMEOUT, "eigensolver: an H psi pipeline wait timed out");
+    ++S->sweeps;
+    const int nw = c.n_wanted > 0 ? c.n_wanted : c.nst;
+    double rmax = 0;
+    for (int k = 0; k < nw; ++k) rmax = std::max(rmax, res[k]);
+    S->max_res = rmax;
     if (n_converged) {
         int k = 0;
         for (double r : res) k += r <= c.tol;
         *n_converged = k;
     }
+    // the learned preconditioner gives way to the plain filter once it stops
+    // reducing the largest wanted residual (stall_sweeps sweeps in a row
+    // without a drop below stall_ratio times the best so far)
+    if (S->pc->kind() == RS_PRECOND_LEARNED && c.stall_sweeps > 0 && !S->fallback_sweep) {
+        if (rmax < c.stall_ratio * S->best) {
+            S->best = rmax;
+            S->stall = 0;
+        } else if (++S->stall >= c.stall_sweeps) {
+            Precond *p = Precond::create(RS_PRECOND_FILTER, c.filter_alpha, S->npts, c.nb, c.dtype);
+            if (!p) return fail(RS_ENOMEM, "eigensolver: filter fallback unavailable");
+            delete S->pc;   // the sweep above is complete (the stream was synchronised)
+            S->pc = p;
+            S->fallback_sweep = S->sweeps;
+        }
+    }
+    // FP32 solvers: eigenvalues from the closing FP64 Rayleigh-Ritz, taken at
+    // every sweep once the largest wanted residual is <= rr64_always and every
+    // rr64_every sweeps once it is <= rr64_below
+    S->eps_f64 = c.dtype == RS_F64;
+    if (c.dtype == RS_F32 && c.rr64_every > 0 &&
+        (rmax <= c.rr64_always || (rmax <= c.rr64_below && S->sweeps % c.rr64_every == 0))) {
+        double *out = eps_dev;
+        if (!out) {
+            if (!S->eps64.p) RS_TRY(S->eps64.alloc(sizeof(double) * c.nst));
+            out = S->eps64.as<double>();
+        }
+        RS_TRY(rayleigh_ritz_f64_impl(S, out, st));
+        S->eps_f64 = 1;
+    }
+    return RS_OK;
+}
+
+extern "C" int rs_solver_stats(rs_solver *S, rs_solver_stats_t *out) {
+    if (!S || !out) return fail(RS_EINVAL, "rs_solver_stats: null argument");
+    out->sweeps = S->sweeps;
+    out->eps_f64 = S->eps_f64;
+    out->precond = S->pc->kind();
+    out->fallback_sweep = S->fallback_sweep;
+    out->max_residual = S->max_res;
+    out->train_target_seconds = S->train_target_s;
+    out->train_fit_seconds = S->train_fit_s;
     return RS_OK;
 }
 
@@ -436,62 +557,160 @@ extern "C" int rs_solver_residual(rs_solver *S, int first, int ncols, void *R_de
     return RS_OK;
 }
 
-__global__ void k_widen(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        b[e] = (double)a[e];
-}
-
-extern "C" int rs_solver_rayleigh_ritz_f64(rs_solver *S, double *eps_dev, void *stream) {
-    if (!S || !eps_dev) return fail(RS_EINVAL, "rs_solver_rayleigh_ritz_f64: null argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    const rs_solver_cfg &c = S->cfg;
-    const int n = c.nst;
-    if (c.dtype == RS_F64) {
-        RS_CUDA(cudaMemcpyAsync(eps_dev, S->eig.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        RS_CUDA(cudaStreamSynchronize(st));
-        return RS_OK;
-    }
-    const size_t nn = (size_t)n * n;
-    if (!S->psi64.p) {
-        RS_TRY(S->psi64.alloc(sizeof(double) * (size_t)S->npts * n));
-        RS_TRY(S->hpsi64.alloc(sizeof(double) * (size_t)S->npts * n));
-        RS_TRY(S->rr64.alloc(sizeof(double) * (4 * nn + 16) + eigh_work_bytes(n)));
-    }
-    double *Sm = S->rr64.as<double>(), *h = Sm + nn, *Ui = h + nn, *T = Ui + nn;
-    int *status = reinterpret_cast<int *>(T + nn);
-    void *ew = reinterpret_cast<void *>(T + nn + 16);
-    // FP64 copy of the FP32 orbitals, H applied in FP64
-    k_widen<<<1024, 256, 0, st>>>(S->psi.as<float>(), S->psi64.as<double>(), S->npts * n);
-    RS_LAUNCH_CHECK();
-    for (int b = 0; b < n; b += c.nb)
-        RS_TRY(rs_ham_apply_block(S->h, S->psi64.as<double>() + b, n, S->hpsi64.as<double>() + b, n, c.nb, RS_F64, st));
-    // generalized Rayleigh-Ritz h x = eps S x with S, h accumulated in FP64
-    // (the overlap of the FP32 orbitals is exact: products of FP32 values)
-    RS_TRY(gram<float>(S->psi.as<float>(), n, n, S->psi.as<float>(), n, n, S->npts, S->dV, Sm, n, st));
-    RS_TRY(gram<double>(S->psi64.as<double>(), n, n, S->hpsi64.as<double>(), n, n, S->npts, S->dV, h, n, st));
-    RS_TRY(symmetrize(Sm, n, n, st));
-    RS_TRY(symmetrize(h, n, n, st));
-    RS_TRY(cholesky(Sm, n, n, 1e-14, status, st));
-    RS_TRY(tri_inv(Sm, n, n, Ui, n, st));
-    RS_TRY(gemm_small(n, n, n, 1.0, Ui, n, true, h, n, false, 0.0, T, n, st));
-    RS_TRY(gemm_small(n, n, n, 1.0, T, n, false, Ui, n, false, 0.0, h, n, st));
-    RS_TRY(symmetrize(h, n, n, st));
-    RS_TRY(eigh(h, n, n, eps_dev, T, n, 2, status, ew, st));
-    RS_CUDA(cudaStreamSynchronize(st));
-    return RS_OK;
-}
-
 extern "C" int rs_solver_psi(rs_solver *S, void **psi_dev) {
     if (!S || !psi_dev) return fail(RS_EINVAL, "rs_solver_psi: null argument");
     *psi_dev = S->psi.p;
     return RS_OK;
 }
 
+// Keeps a copy of the learned weights in the solver (saved by
+// rs_precond_save, reinstated when the learned preconditioner is selected
+// again) and hands them to the current preconditioner when it is the learned one.
+static int store_weights(rs_solver *S, const float *w_dev, cudaStream_t st) {
+    if (!S->wlearn.p) RS_TRY(S->wlearn.alloc(sizeof(float) * LEARNED_WEIGHTS));
+    if (w_dev != S->wlearn.as<float>())
+        RS_CUDA(cudaMemcpyAsync(S->wlearn.p, w_dev, sizeof(float) * LEARNED_WEIGHTS, cudaMemcpyDeviceToDevice, st));
+    S->has_wlearn = true;
+    if (S->pc->kind() == RS_PRECOND_LEARNED) RS_TRY(S->pc->set_weights(S->wlearn.as<float>(), st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    return RS_OK;
+}
+
 extern "C" int rs_solver_set_precond_weights(rs_solver *S, const float *w_dev) {
     if (!S || !w_dev) return fail(RS_EINVAL, "rs_solver_set_precond_weights: null argument");
-    RS_TRY(S->pc->set_weights(w_dev, nullptr));
-    RS_CUDA(cudaDeviceSynchronize());
+    if (S->pc->kind() != RS_PRECOND_LEARNED)
+        return fail(RS_EINVAL, "rs_solver_set_precond_weights: the solver's preconditioner is not the learned one");
+    RS_CUDA(cudaDeviceSynchronize());   // the caller's weights are written on any stream
+    return store_weights(S, w_dev, nullptr);
+}
+
+extern "C" int rs_precond_train(rs_solver *S, const rs_grid *g, const rs_learn_cfg *cfg, const float *w_init_dev,
+                                float *loss_host, void *stream) {
+    if (!S || !g || !cfg) return fail(RS_EINVAL, "rs_precond_train: null argument");
+    const rs_learn_cfg c = *cfg;
+    const rs_solver_cfg &sc = S->cfg;
+    if (sc.dtype != RS_F32) return fail(RS_EINVAL, "rs_precond_train: the learned preconditioner needs an RS_F32 solver");
+    if (S->pc->kind() != RS_PRECOND_LEARNED) return fail(RS_EINVAL, "rs_precond_train: the solver's preconditioner is not the learned one");
+    if (g->npts != S->npts) return fail(RS_EINVAL, "rs_precond_train: grid of another size");
+    if (c.n_res < 1 || c.n_res > sc.nst || c.n_res > 256 || c.cg_iters < 0 || c.cg_iters > 10000 || !(c.sigma > 0) ||
+        c.train.n_tiles < 1 || c.train.batch < 1 || c.train.epochs < 0 || c.train.tile < 1 || c.train.tile > 58 ||
+        !(c.train.lr > 0))
+        return fail(RS_EINVAL, "rs_precond_train: bad configuration");
+    if (!w_init_dev && !S->has_wlearn) return fail(RS_EINVAL, "rs_precond_train: no initial weights");
+    cudaStream_t st = (cudaStream_t)stream;
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    // the residual columns, padded to the CG block width (a power of two <= 64)
+    int w = 1;
+    while (w < std::min(c.n_res, 64)) w <<= 1;
+    const int chunks = (c.n_res + w - 1) / w, ld = chunks * w;
+    const int64_t np = S->npts;
+    DevBuf R, X, work, nrm;
+    RS_TRY(R.alloc(sizeof(float) * (size_t)np * ld));
+    RS_TRY(X.alloc(sizeof(float) * (size_t)np * ld));
+    RS_TRY(work.alloc((size_t)rs_cg_workspace_bytes(np, w, RS_F32)));
+    RS_TRY(nrm.alloc(sizeof(double) * 256));
+    const int ncols = std::min(ld, sc.nst);
+    RS_TRY(rs_solver_residual(S, 0, ncols, R.p, ld, st));
+    if (ncols < ld)
+        RS_CUDA(cudaMemset2DAsync(R.as<float>() + ncols, sizeof(float) * ld, 0, sizeof(float) * (ld - ncols), (size_t)np, st));
+    // targets: cg_iters conjugate-gradient iterations on (-1/2 Lap + sigma) X = R,
+    // the operator applied by a Hamiltonian on the same grid with V = sigma
+    {
+        std::vector<double> Vs((size_t)np, c.sigma);
+        rs_ham *hs = nullptr;
+        RS_TRY(rs_ham_create(g, Vs.data(), nullptr, 4, &hs));
+        int rc = RS_OK;
+        for (int k = 0; k < chunks && rc == RS_OK; ++k)
+            rc = rs_shifted_poisson_cg(hs, R.as<float>() + k * w, X.as<float>() + k * w, ld, w, c.cg_iters, RS_F32, work.p, st);
+        if (rc == RS_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(RS_ECUDA, "rs_precond_train: CG failed");
+        rs_ham_destroy(hs);
+        RS_TRY(rc);
+    }
+    // the eigensolver uses only the direction of K r: every target column is
+    // scaled to unit rms, like the network's input r / rms(r); unscaled
+    // targets (about 1/50 of the input) would let an output near zero that
+    // carries no direction minimise the loss
+    RS_TRY(coldots(RS_F32, X.p, ld, X.p, ld, c.n_res, np, nrm.as<double>(), st));
+    k_scale_cols<float><<<elem_blocks(np, c.n_res), 256, 0, st>>>(X.as<float>(), ld, c.n_res, np, nrm.as<double>(),
+                                                                  1.0 / (double)np);
+    RS_LAUNCH_CHECK();
+    RS_CUDA(cudaStreamSynchronize(st));
+    const auto t1 = clk::now();
+    DevBuf wt;
+    RS_TRY(wt.alloc(sizeof(float) * LEARNED_WEIGHTS));
+    RS_CUDA(cudaMemcpyAsync(wt.p, w_init_dev ? w_init_dev : S->wlearn.as<float>(), sizeof(float) * LEARNED_WEIGHTS,
+                            cudaMemcpyDeviceToDevice, st));
+    RS_TRY(train_pairs_impl(S->h, g, R.as<float>(), X.as<float>(), ld, c.n_res, c.train, wt.as<float>(), loss_host, st));
+    RS_TRY(store_weights(S, wt.as<float>(), st));
+    S->train_target_s = std::chrono::duration<double>(t1 - t0).count();
+    S->train_fit_s = std::chrono::duration<double>(clk::now() - t1).count();
     return RS_OK;
+}
+
+// Weight file: the 4 bytes "RSNN", then little-endian uint32 version (1),
+// uint32 count (2160), count FP32 values, and the uint32 FNV-1a hash of the
+// value bytes.
+static uint32_t fnv1a(const unsigned char *p, size_t n) {
+    uint32_t h = 2166136261u;
+    for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 16777619u;
+    return h;
+}
+static void put_u32(unsigned char *d, uint32_t v) {
+    for (int i = 0; i < 4; ++i) d[i] = (unsigned char)(v >> (8 * i));
+}
+static uint32_t get_u32(const unsigned char *d) {
+    return (uint32_t)d[0] | (uint32_t)d[1] << 8 | (uint32_t)d[2] << 16 | (uint32_t)d[3] << 24;
+}
+
+extern "C" int rs_precond_save(rs_solver *S, const char *path) {
+    if (!S || !path) return fail(RS_EINVAL, "rs_precond_save: null argument");
+    if (!S->has_wlearn) return fail(RS_EINVAL, "rs_precond_save: no learned weights set or trained");
+    std::vector<float> w(LEARNED_WEIGHTS);
+    RS_CUDA(cudaMemcpy(w.data(), S->wlearn.p, sizeof(float) * LEARNED_WEIGHTS, cudaMemcpyDeviceToHost));
+    const size_t nv = sizeof(float) * LEARNED_WEIGHTS;
+    std::vector<unsigned char> buf(12 + nv + 4);
+    memcpy(buf.data(), "RSNN", 4);
+    put_u32(buf.data() + 4, 1);
+    put_u32(buf.data() + 8, LEARNED_WEIGHTS);
+    for (int i = 0; i < LEARNED_WEIGHTS; ++i) {
+        uint32_t u;
+        memcpy(&u, &w[i], 4);
+        put_u32(buf.data() + 12 + 4 * i, u);
+    }
+    put_u32(buf.data() + 12 + nv, fnv1a(buf.data() + 12, nv));
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(RS_EINVAL, "rs_precond_save: cannot open %s", path);
+    const bool ok = fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    if (fclose(f) != 0 || !ok) return fail(RS_EINVAL, "rs_precond_save: write to %s failed", path);
+    return RS_OK;
+}
+
+extern "C" int rs_precond_load(rs_solver *S, const char *path) {
+    if (!S || !path) return fail(RS_EINVAL, "rs_precond_load: null argument");
+    if (S->pc->kind() != RS_PRECOND_LEARNED)
+        return fail(RS_EINVAL, "rs_precond_load: the solver's preconditioner is not the learned one");
+    const size_t nv = sizeof(float) * LEARNED_WEIGHTS;
+    std::vector<unsigned char> buf(12 + nv + 4 + 1);
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(RS_EINVAL, "rs_precond_load: cannot open %s", path);
+    const size_t got = fread(buf.data(), 1, buf.size(), f);
+    fclose(f);
+    if (got != 12 + nv + 4 || memcmp(buf.data(), "RSNN", 4) != 0 || get_u32(buf.data() + 4) != 1 ||
+        get_u32(buf.data() + 8) != (uint32_t)LEARNED_WEIGHTS)
+        return fail(RS_EINVAL, "rs_precond_load: %s is not a weight file of this library", path);
+    if (get_u32(buf.data() + 12 + nv) != fnv1a(buf.data() + 12, nv))
+        return fail(RS_EINVAL, "rs_precond_load: checksum mismatch in %s", path);
+    std::vector<float> w(LEARNED_WEIGHTS);
+    for (int i = 0; i < LEARNED_WEIGHTS; ++i) {
+        const uint32_t u = get_u32(buf.data() + 12 + 4 * i);
+        memcpy(&w[i], &u, 4);
+        if (!std::isfinite(w[i])) return fail(RS_ENAN, "rs_precond_load: non-finite weight in %s", path);
+    }
+    RS_CUDA(cudaDeviceSynchronize());   // no queued sweep still reads the weights
+    if (!S->wlearn.p) RS_TRY(S->wlearn.alloc(sizeof(float) * LEARNED_WEIGHTS));
+    RS_CUDA(cudaMemcpy(S->wlearn.p, w.data(), nv, cudaMemcpyHostToDevice));
+    return store_weights(S, S->wlearn.as<float>(), nullptr);
 }
 
 extern "C" int rs_solver_set_precond(rs_solver *S, int precond) {
@@ -504,6 +723,8 @@ extern "C" int rs_solver_set_precond(rs_solver *S, int precond) {
     delete S->pc;
     S->pc = p;
     S->cfg.precond = precond;
+    // a learned preconditioner selected again takes the weights last set
+    if (precond == RS_PRECOND_LEARNED && S->has_wlearn) RS_TRY(store_weights(S, S->wlearn.as<float>(), nullptr));
     return RS_OK;
 }
 

@@ -84,7 +84,8 @@ constexpr size_t MAX_SMEM = 226 * 1024;    // dynamic shared memory per CTA (227
 constexpr int MAX_SLAB = 1 << 16;          // planes per z-slab (at most)
 constexpr int MAX_UNITS = 64;              // units per CTA (shared-memory table)
 constexpr int SUSPEND_NS = 20000;          // suspension limit of one barrier test
-constexpr int SPIN = 100000;               // barrier tests before a wait gives up
+constexpr int SPIN = 100000;               // barrier tests before a wait gives up (default)
+constexpr int DRAIN_SPIN = 5000;           // barrier tests per slot when draining after a timeout
 
 // Window layout in a slot.  Window rows wy = 0..15 (tile rows at 4..11),
 // columns wx = 0..23 (tile columns at 4..19).  Columns 4..19 of every row
@@ -125,6 +126,7 @@ struct Args {
     float *hpsi;
     int64_t ldh;
     int nb, rec_slot, cs_atoms;   // cs_atoms: the largest atom count of a CTA
+    int spin;                     // barrier tests before a wait gives up
     float w[5];
     int *status;
 };
@@ -148,9 +150,9 @@ __device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// at most SPIN tests (about SPIN * SUSPEND_NS, two seconds, in all)
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity) {
-    for (int i = 0; i < SPIN; ++i)
+// at most `spin` tests (by default about SPIN * SUSPEND_NS, two seconds, in all)
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, int spin) {
+    for (int i = 0; i < spin; ++i)
         if (bar_try(b, parity)) return true;
     return false;
 }
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
     int j = 0;   // planes issued
     auto issue = [&]() {
         const int slot = j % RING, g = j % 3;
-        if (!__all_sync(0xffffffffu, j < RING || bar_wait(&emptyb[slot], ((j / RING) - 1) & 1))) {
+        if (!__all_sync(0xffffffffu, j < RING || bar_wait(&emptyb[slot], ((j / RING) - 1) & 1, a.spin))) {
             ok = false;
             return;
         }
@@ -454,13 +456,14 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
     float2 A[8][2][4];
 
     while (j < AHEAD && qi.k < nu && ok) issue();
-    for (int it = 0; qc.k < nu && ok; ++it) {
+    int it = 0;   // planes consumed
+    for (; qc.k < nu && ok; ++it) {
         if (qi.k < nu) {
             issue();
             if (!ok) break;
         }
         const int slot = it % RING;
-        if (!__all_sync(0xffffffffu, bar_wait(&fullb[slot], (it / RING) & 1))) {
+        if (!__all_sync(0xffffffffu, bar_wait(&fullb[slot], (it / RING) & 1, a.spin))) {
             ok = false;
             break;
         }
@@ -513,15 +516,22 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
         }
         advance(qc);
     }
-    if (!ok && lane == 0) atomicExch(a.status, 1);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (!ok) {
+        if (lane == 0) atomicExch(a.status, 1);
+        // A wait gave up.  The planes this thread issued but did not consume
+        // (at most RING, in distinct slots) may still have arrivals pending
+        // from its copies; wait for their phases, with a fixed bound, so that
+        // no asynchronous arrival reaches shared memory after the CTA exits.
+        for (int q = it; q < j; ++q) bar_wait(&fullb[q % RING], (q / RING) & 1, DRAIN_SPIN);
+    }
 }
 
 }  // namespace
 
 struct RingPlan {
     DevBuf units, cta, cta_atoms, desc, recs, rec, status;
-    int n_cta = 0, rec_slot = 0, cs_atoms = 0, ring = MAX_RING;
+    int n_cta = 0, rec_slot = 0, cs_atoms = 0, ring = MAX_RING, spin = SPIN;
     int64_t npts = 0;
     size_t smem = 0;
 };
@@ -806,26 +816,12 @@ int ring_launch(RingPlan *p, const float *psi, int64_t ldp, float *hpsi, int64_t
     a.ldh = ldh;
     a.nb = nb;
     a.rec_slot = p->rec_slot;
+    a.spin = p->spin;
     for (int j = 0; j < 5; ++j) a.w[j] = w[j];
     a.status = p->status.as<int>();
     const dim3 grid((unsigned)p->n_cta, (unsigned)(nb / SG));
-    // the shared-memory limit is an attribute of the kernel, not of the plan:
-    // it is raised once to the largest any plan may ask for
-    // (the device's opt-in maximum less the kernel's static shared memory)
-    static bool limit_set[2] = {false, false};
     const int r4 = p->ring == 4 ? 1 : 0;
-    if (!limit_set[r4]) {
-        const void *fn = r4 ? (const void *)k_hpsi_ring<4> : (const void *)k_hpsi_ring<3>;
-        cudaFuncAttributes fa;
-        int dev = 0, optin = 0;
-        RS_CUDA(cudaFuncGetAttributes(&fa, fn));
-        RS_CUDA(cudaGetDevice(&dev));
-        RS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const int lim = optin - (int)fa.sharedSizeBytes;
-        if (lim < (int)p->smem) return fail(RS_ECUDA, "ring kernel: %zu bytes of shared memory above the device limit", p->smem);
-        RS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        limit_set[r4] = true;
-    }
+    RS_TRY(smem_optin(r4 ? (const void *)k_hpsi_ring<4> : (const void *)k_hpsi_ring<3>, p->smem));
     if (r4) k_hpsi_ring<4><<<grid, NT, p->smem, st>>>(a);
     else k_hpsi_ring<3><<<grid, NT, p->smem, st>>>(a);
     RS_LAUNCH_CHECK();
@@ -837,6 +833,18 @@ int ring_status(const RingPlan *p, int *flag) {
     if (!p) return RS_OK;
     RS_CUDA(cudaMemcpy(flag, p->status.as<int>(), sizeof(int), cudaMemcpyDeviceToHost));
     return RS_OK;
+}
+
+int ring_reset_status(RingPlan *p) {
+    if (!p) return RS_OK;
+    RS_CUDA(cudaMemset(p->status.p, 0, sizeof(int)));
+    return RS_OK;
+}
+
+int *ring_status_word(RingPlan *p) { return p ? p->status.as<int>() : nullptr; }
+
+void ring_set_wait_limit(RingPlan *p, int tests) {
+    if (p) p->spin = tests < 0 ? SPIN : tests;
 }
 
 }  // namespace rs

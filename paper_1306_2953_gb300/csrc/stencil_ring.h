@@ -35,5 +35,11 @@ int ring_launch(RingPlan *p, const float *psi, int64_t ldp, float *hpsi, int64_t
 
 // Status word of the kernel's bounded waits (0 = none timed out); blocking.
 int ring_status(const RingPlan *p, int *flag);
+// Clears the status word (blocking).
+int ring_reset_status(RingPlan *p);
+// Device address of the status word (nullptr without a plan).
+int *ring_status_word(RingPlan *p);
+// Barrier tests before a wait gives up (tests < 0: the default).
+void ring_set_wait_limit(RingPlan *p, int tests);
 
 }  // namespace rs

@@ -359,11 +359,7 @@ int make_map(CUtensorMap *m, const void *P, int rows, int Kp, int box_rows) {
 template <int BN> int launch(const CUtensorMap &ta, const CUtensorMap &tb, const UmmaArgs &a, int splits, cudaStream_t st) {
     constexpr int STAGE = 3 * UM_BM * UM_BK * 2 + 3 * BN * UM_BK * 2;
     const size_t smem = (size_t)um_stages(BN) * STAGE + 1024;
-    static bool attr = false;
-    if (!attr) {
-        RS_CUDA(cudaFuncSetAttribute(k_umma_tn<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    RS_TRY(smem_optin((const void *)k_umma_tn<BN>, smem));
     dim3 grid((unsigned)((a.M + UM_BM - 1) / UM_BM), (unsigned)((a.N + BN - 1) / BN), (unsigned)splits);
     k_umma_tn<BN><<<grid, UM_NT, smem, st>>>(ta, tb, a);
     RS_LAUNCH_CHECK();

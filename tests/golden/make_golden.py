@@ -2,6 +2,7 @@
 and the benchmark's time-to-accuracy measurement.
 
     python tests/golden/make_golden.py ho32_h0.3 mol20_h0.35 [mol100_h0.3 ...]
+    python tests/golden/make_golden.py --annotate <workload> ...   (margins only)
 
 Calls only the FP64 CPU oracle (``oracle/``) on the seeded synthetic
 workloads of ``workloads``: block CG from the workload's random start
@@ -10,6 +11,12 @@ vectors, converged until every judged state's residual norm is below 1e-9
 order residual^2 / gap, is far below the 1e-8 Ha / 1e-6 Ha targets, plus,
 for the harmonic oscillator, the separable closed form.  Output:
 tests/golden/eigs_<workload>.json.
+
+Margin of a file: the smallest gap between adjacent stored eigenvalues and
+the eigenvalue error bound residual^2 / gap it gives (a Ritz value whose
+residual norm is r lies within r^2 / gap of an eigenvalue when gap separates
+it from the rest of the spectrum).  ``--annotate`` adds these two figures to
+existing files from their own stored values, without solving again.
 """
 from __future__ import annotations
 
@@ -51,6 +58,34 @@ def separable_levels(s: wl.BoxSpec, k: int) -> list[float]:
     return sorted((e[:, None, None] + e[None, :, None] + e[None, None, :]).ravel())[:k]
 
 
+def margins(out: dict) -> dict:
+    """Smallest adjacent gap among the stored eigenvalues and the error
+    bound max_residual^2 / gap (degenerate levels, gap below 1e-8 Ha, are
+    treated as one cluster and skipped)."""
+    e = np.sort(np.array(out["eigenvalues"]))
+    gaps = np.diff(e)
+    gaps = gaps[gaps > 1e-8]
+    if len(gaps) == 0:
+        return out
+    g = float(gaps.min())
+    out["min_gap_ha"] = g
+    out["error_bound_ha"] = float(out["max_residual"]) ** 2 / g
+    out["margin_note"] = ("min_gap_ha: smallest gap between adjacent judged eigenvalues (levels closer than 1e-8 Ha "
+                          "counted as one cluster); error_bound_ha = max_residual^2 / min_gap_ha; the gap to the "
+                          "first state above the judged ones is not stored")
+    return out
+
+
+def annotate(names):
+    for name in names:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"eigs_{name}.json")
+        with open(path) as f:
+            out = json.load(f)
+        with open(path, "w") as f:
+            json.dump(margins(out), f, indent=1)
+        print(name, out.get("min_gap_ha"), out.get("error_bound_ha"))
+
+
 def main(names):
     for name in names:
         w = wl.WORKLOADS[name]
@@ -79,6 +114,7 @@ def main(names):
                "source": "oracle/eigensolver.py BlockCG (FP64), written by tests/golden/make_golden.py"}
         if isinstance(w.system, wl.BoxSpec):
             out["separable_closed_form"] = [float(v) for v in separable_levels(w.system, w.judged)]
+        out = margins(out)
         path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"eigs_{name}.json")
         with open(path, "w") as f:
             json.dump(out, f, indent=1)
@@ -86,4 +122,7 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:])
+    if sys.argv[1:2] == ["--annotate"]:
+        annotate(sys.argv[2:])
+    else:
+        main(sys.argv[1:])

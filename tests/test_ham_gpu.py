@@ -7,6 +7,20 @@ plus the potential, so FP32 rounding bounds its error by roughly
 30 * 2^-24 * max|term|; per state this gives a relative norm error below
 2e-6 for random orbitals and below 3e-5 for smooth ones, where the Laplacian
 cancels most of the terms (the bounds asserted below).
+
+Element-wise FP32 bound (full-size molecules).  With u = 2^-24, every
+output element of the FP32 kernel differs from the FP64 value of the same
+FP32 inputs by at most u (c_loc M_loc + c_nl M_nl), where the oracle gives
+the term magnitudes at that element:
+  M_loc = 1/(2h^2) sum_taps |c_j| |psi| + |V| |psi|   (stencil and potential),
+  M_nl  = sum_{A,q} |gamma_Aq(p)| |E_Aq| dV sum_{p'} |gamma_Aq(p')| |psi(p')|.
+The local part is a recursive sum of 27 terms whose inputs (weights, V) are
+themselves rounded once: c_loc = 32 covers (27 - 1) + 2 roundings.  The
+projection integral sums a sphere of ~4200 products in FP32 partial sums
+and atomics; its error grows like sqrt(n) u for rounding errors of random
+sign (~65 u) and its worst case is n u: c_nl = 512 is eight times the
+typical growth.  A wrong or missing nonlocal entry changes an element by a
+term of size ~M_nl, 2^24 / 512 = 32768 times this bound.
 """
 import numpy as np
 import pytest
@@ -33,6 +47,29 @@ def _lib_system(kind, params):
     idx = lib_to_oracle_index(g_ora, lg.ijk())
     H = api.Hamiltonian(lg, H_ora.V[idx], proj)
     return lg, H, g_ora, H_ora, idx
+
+
+def _term_magnitudes(g_ora, H_ora, psi):
+    """Oracle term magnitudes (M_loc, M_nl) of H psi at every element (see
+    the module docstring): the oracle's own operator with every weight,
+    potential value, coupling and projector value replaced by its absolute
+    value, applied to |psi|."""
+    from oracle import hamiltonian as oh
+    a = np.abs(psi)
+    zero = np.zeros(g_ora.npts)
+    kin = oh.Hamiltonian(g_ora, zero, None, cw=np.abs(H_ora.cw)).apply(a)        # -1/(2h^2) sum |c||psi|
+    pr = H_ora.proj
+    pabs = oh.Projectors(pr.n_atoms, pr.sph_off, pr.sph_idx, np.abs(pr.gam), np.abs(pr.E))
+    full = oh.Hamiltonian(g_ora, zero, pabs, cw=np.abs(H_ora.cw)).apply(a)
+    m_loc = -kin + np.abs(H_ora.V)[:, None] * a
+    return m_loc, full - kin
+
+
+def _assert_elementwise_f32(out, ref, m_loc, m_nl):
+    u = 2.0 ** -24
+    bound = u * (32.0 * m_loc + 512.0 * m_nl)
+    ratio = np.abs(out - ref) / bound
+    assert np.all(np.isfinite(ratio)) and ratio.max() <= 1.0, f"worst element at {ratio.max():.3f} of the bound"
 
 
 def _rel_err_per_state(got, ref):
@@ -171,13 +208,15 @@ def test_hpsi_full_size_mol100(dtype):
     out = H.apply(psi).double().cpu().numpy()
     tol = 1e-12 if dtype == "f64" else 2e-6
     assert np.max(_rel_err_per_state(out, ref)) <= tol
+    if dtype == "f32":
+        m_loc, m_nl = _term_magnitudes(g_ora, H_ora, psi_ora)
+        _assert_elementwise_f32(out, ref, m_loc[idx], m_nl[idx])
     assert H.status() == 0
 
 
 def test_hpsi_full_size_mol300_f32():
     """The 300-atom molecule (1.8 million points, the largest workload) at
-    full size: one FP32 block of 32 states, whose coefficients no longer fit
-    the ring kernel's shared memory (global-memory nonlocal path)."""
+    full size: one FP32 block of 32 states, per state and element by element."""
     spec = wl.MOL300.system
     lg, H, g_ora, H_ora, idx = _lib_system("mol", (spec,))
     psi_ora = wl.random_block(g_ora.npts, 32, 77).astype(np.float32).astype(np.float64)
@@ -185,4 +224,6 @@ def test_hpsi_full_size_mol300_f32():
     psi = torch.from_numpy(np.ascontiguousarray(psi_ora[idx])).float().cuda()
     out = H.apply(psi).double().cpu().numpy()
     assert np.max(_rel_err_per_state(out, ref)) <= 2e-6
+    m_loc, m_nl = _term_magnitudes(g_ora, H_ora, psi_ora)
+    _assert_elementwise_f32(out, ref, m_loc[idx], m_nl[idx])
     assert H.status() == 0

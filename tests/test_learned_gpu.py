@@ -8,7 +8,18 @@ differences stay small).  The network runs in FP32 with BF16 weights and
 inputs; the oracle is given the same BF16-rounded values and computes in
 FP64, so outputs agree to FP32 accumulation accuracy (1e-5 relative) and
 gradients, which sum ~1e4 products, to 1e-4.
+
+Training (Adam on the FP32 master weights, BF16 weights in the network):
+after T steps the weight change w_T - w_0 of the GPU agrees with the
+oracle's, stepped on the same tiles from the same weights, to 1e-2
+relative in norm (the BF16-weight bound of the gradient pin).  Adam's first
+steps move each weight by about lr * sign(g), so a gradient entry whose
+sign the FP32 rounding flips moves that weight the other way; the test
+allows that only where |g| is below 1e-3 of the largest gradient entry.
 """
+import os
+import tempfile
+
 import numpy as np
 import pytest
 
@@ -80,6 +91,106 @@ def test_convnet_forward_and_gradients_match_oracle():
     assert np.abs(gg - grf).max() <= 1e-4 * np.abs(grf).max()
 
 
+def test_convnet_at_training_tile_size_matches_oracle():
+    """The training tiles' own size, 22^3 (a 16^3 interior plus 3 points of
+    halo), where the weight-gradient kernel stages two planes per CTA."""
+    from oracle import precond as op
+    from paper_1306_2953_gb300 import api
+    ws = wl.conv_init(6)
+    w = np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel() for a in ws]).astype(np.float32)
+    D = 22
+    x, mask, tgt, valid = _tiles(ntiles=3, D=D, seed=4)
+    valid[:] = False
+    valid[3:-3, 3:-3, 3:-3] = True
+    dev = lambda a, t=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(t).cuda()
+    y, g, loss = api.convnet_tiles(dev(w), dev(x), dev(mask.astype(np.uint8), torch.uint8), dev(tgt),
+                                   dev(valid.astype(np.uint8), torch.uint8))
+    wq = [op.bf16_round(a).astype(np.float64) for a in ws]
+    yr, cache = op.net_forward(op.bf16_round(x).astype(np.float64), mask, wq)
+    lr, gy = op.tile_loss(yr, tgt.astype(np.float64), valid[None] & mask)
+    grf = np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel() for a in op.net_backward(gy, cache, wq)])
+    assert np.abs(y.cpu().numpy() - yr).max() <= 1e-5 * np.abs(yr).max()
+    assert abs(loss - lr) <= 1e-5 * lr
+    assert np.abs(g.cpu().numpy() - grf).max() <= 1e-4 * np.abs(grf).max()
+
+
+def test_adam_training_steps_match_oracle():
+    """rs_precond_train_tiles (the GPU forward, backward and Adam kernels)
+    against the oracle's net_forward / net_backward / Adam over the same
+    seeded 22^3 tiles at the training batch size: 128 tiles in batches of
+    64, two epochs (four Adam steps)."""
+    from oracle import precond as op
+    from paper_1306_2953_gb300 import api
+    D, ntiles, batch, epochs, lr = 22, 128, 64, 2, 1e-3
+    x, mask, tgt, valid = _tiles(ntiles=ntiles, D=D, seed=12)
+    valid[:] = False
+    valid[3:-3, 3:-3, 3:-3] = True
+    ws0 = wl.conv_init(3)
+    w = torch.from_numpy(_flat_weights(ws0)).cuda()
+    dev = lambda a, t=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(t).cuda()
+    losses = api.precond_train_tiles(w, dev(x), dev(mask.astype(np.uint8), torch.uint8), dev(tgt),
+                                     dev(valid.astype(np.uint8), torch.uint8), batch, epochs, lr)
+    w_gpu = w.cpu().numpy().astype(np.float64)
+    # the oracle: FP64 master weights, used in BF16 (rounded through FP32)
+    params = [a.astype(np.float32).astype(np.float64) for a in ws0]
+    opt = op.Adam(params, lr=lr)
+    xq = op.bf16_round(x).astype(np.float64)
+    ora_losses, gmax = [], []
+    for ep in range(epochs):
+        tot = 0.0
+        for t0 in range(0, ntiles, batch):
+            wq = [op.bf16_round(p.astype(np.float32)).astype(np.float64) for p in params]
+            y, cache = op.net_forward(xq[t0:t0 + batch], mask[t0:t0 + batch], wq)
+            l, gy = op.tile_loss(y, tgt[t0:t0 + batch].astype(np.float64), valid[None] & mask[t0:t0 + batch])
+            grads = op.net_backward(gy, cache, wq)
+            gmax.append(np.concatenate([gg.ravel() for gg in grads]))
+            params = opt.step(params, grads)
+            tot += l
+        ora_losses.append(tot / (ntiles // batch))
+    w_ora = np.concatenate([p.reshape(p.shape[0], p.shape[1], 27).ravel() for p in params])
+    w0 = _flat_weights(ws0).astype(np.float64)
+    d_gpu, d_ora = w_gpu - w0, w_ora - w0
+    assert np.linalg.norm(d_gpu - d_ora) <= 1e-2 * np.linalg.norm(d_ora)
+    # element by element: a weight may move the other way only where a
+    # gradient entry is too small for its sign to survive FP32 rounding
+    small = np.min(np.abs(np.stack(gmax)), axis=0) <= 1e-3 * np.abs(np.stack(gmax)).max()
+    big_diff = np.abs(d_gpu - d_ora) > 0.1 * lr
+    assert not np.any(big_diff & ~small), np.nonzero(big_diff & ~small)
+    # the epoch losses use each side's own BF16 weights, which may differ by
+    # one BF16 unit where the master weights straddle a rounding boundary
+    assert np.allclose(losses, ora_losses, rtol=1e-3)
+
+
+def test_precond_save_load_roundtrip(tmp_path):
+    """rs_precond_save writes the solver's weights; rs_precond_load reads them
+    into another solver, which then preconditions identically; corrupted or
+    foreign files are refused."""
+    from paper_1306_2953_gb300 import _lib, api
+    from paper_1306_2953_gb300._lib import RsError
+    lg, g_ora, idx = _grid()
+    H = api.Hamiltonian(lg, np.zeros(lg.npts))
+    psi0 = torch.from_numpy(np.ascontiguousarray(wl.random_block(g_ora.npts, 16, 2)[idx])).float().cuda()
+    w = torch.from_numpy(_flat_weights(wl.conv_init(4))).cuda()
+    a = api.Solver(H, psi0, 16, 1e-4, precond=_lib.RS_PRECOND_LEARNED)
+    a.set_precond_weights(w)
+    path = tmp_path / "w.rsnn"
+    a.save_precond(str(path))
+    raw = path.read_bytes()
+    assert raw[:4] == b"RSNN" and len(raw) == 12 + 4 * 2160 + 4
+    b = api.Solver(H, psi0, 16, 1e-4, precond=_lib.RS_PRECOND_LEARNED)
+    b.load_precond(str(path))
+    ea, ra, _ = a.step()
+    eb, rb, _ = b.step()
+    assert torch.equal(ea, eb) and torch.equal(ra, rb)
+    bad = bytearray(raw)
+    bad[100] ^= 1
+    (tmp_path / "bad.rsnn").write_bytes(bytes(bad))
+    with pytest.raises(RsError):
+        b.load_precond(str(tmp_path / "bad.rsnn"))
+    with pytest.raises(RsError):
+        api.Solver(H, psi0, 16, 1e-4).load_precond(str(path))   # not a learned solver
+
+
 def _flat_weights(ws):
     return np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel() for a in ws]).astype(np.float32)
 
@@ -145,12 +256,13 @@ def test_learned_preconditioner_speeds_up_early_sweeps():
         return float(res.max())
 
     S0 = api.Solver(H, psi0, w_.block, 1e-4, precond=_lib.RS_PRECOND_LEARNED)
-    R = S0.residual(0, 32).float().contiguous()
-    Hs = api.Hamiltonian(lg, np.full(lg.npts, 1.0))
-    X = api.shifted_poisson_cg(Hs, R, 200)
-    X = X / X.pow(2).mean(dim=0, keepdim=True).sqrt()
-    w = torch.from_numpy(_flat_weights(wl.conv_init(11))).cuda()
-    api.precond_train(Hs, R, X, w, n_tiles=10000, epochs=5, batch=64, seed=11)
+    S0.train_precond(lg, torch.from_numpy(_flat_weights(wl.conv_init(11))).cuda(), n_res=32, n_tiles=10000,
+                     epochs=5, batch=64, seed=11)
+    w = torch.empty(2160, dtype=torch.float32, device="cuda")
+    path = os.path.join(tempfile.mkdtemp(), "w.rsnn")
+    S0.save_precond(path)
+    raw = np.frombuffer(open(path, "rb").read()[12:12 + 4 * 2160], dtype="<f4")
+    w.copy_(torch.from_numpy(raw.copy()))
     learned = run(_lib.RS_PRECOND_LEARNED, w)
     plain = run(_lib.RS_PRECOND_FILTER)
     assert learned < 0.7 * plain, (learned, plain)

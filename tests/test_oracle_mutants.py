@@ -199,6 +199,18 @@ MUTANTS = [
            "vh = self.v[i] / (1 - self.b2 ** self.t)",
            "vh = self.v[i]",
            "adam"),
+    Mutant("adam_momentum_dropped", "precond.py",
+           "self.m[i] = self.b1 * self.m[i] + (1 - self.b1) * g",
+           "self.m[i] = (1 - self.b1) * g",
+           "adam"),
+    Mutant("adam_first_moment_bias_correction_dropped", "precond.py",
+           "mh = self.m[i] / (1 - self.b1 ** self.t)",
+           "mh = self.m[i]",
+           "adam"),
+    Mutant("adam_second_moment_uses_gradient", "precond.py",
+           "self.v[i] = self.b2 * self.v[i] + (1 - self.b2) * g * g",
+           "self.v[i] = self.b2 * self.v[i] + (1 - self.b2) * np.abs(g)",
+           "adam"),
 ]
 
 

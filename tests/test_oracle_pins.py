@@ -487,3 +487,34 @@ def test_adam_first_step_is_signed_lr():
     g = [np.array([0.3, -4.0, 1e-3])]
     out = op.Adam(p).step(p, g)[0]
     assert np.allclose(out, p[0] - 1e-3 * g[0] / (np.abs(g[0]) + 1e-8), rtol=0, atol=1e-12)
+
+
+def test_adam_constant_gradient_closed_form():
+    # A constant gradient g makes the bias-corrected moments exact at every
+    # step: m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so m_hat = g and
+    # v_hat = g^2, and after t steps w_t = w_0 - t lr g / (|g| + eps).
+    w0 = np.array([1.0, -2.0, 0.5, 0.0])
+    g = np.array([0.3, -4.0, 1e-3, 2.5])
+    opt = op.Adam([w0], lr=1e-3)
+    p = [w0]
+    for t in range(1, 8):
+        p = opt.step(p, [g])
+        assert np.allclose(p[0], w0 - t * 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-12), t
+
+
+def test_adam_alternating_gradient_closed_form():
+    # Gradients g, -g, g, ...: the first moment follows
+    #   m_t = b1 m_{t-1} + (1 - b1) (-1)^(t+1) g
+    #       = (1 - b1) g (-1)^(t+1) (1 - (-b1)^t) / (1 + b1),
+    # the second stays v_t = (1 - b2^t) g^2; each step moves w by
+    #   -lr (m_t / (1 - b1^t)) / (|g| + eps).
+    b1, b2, lr, eps = 0.9, 0.999, 1e-3, 1e-8
+    w0 = np.array([0.7, -1.3, 2.0])
+    g = np.array([0.5, -2.0, 3e-2])
+    opt = op.Adam([w0], lr=lr, b1=b1, b2=b2, eps=eps)
+    p, w = [w0], w0.copy()
+    for t in range(1, 9):
+        p = opt.step(p, [(-1.0) ** (t + 1) * g])
+        m = (1 - b1) * g * (-1.0) ** (t + 1) * (1 - (-b1) ** t) / (1 + b1)
+        w = w - lr * (m / (1 - b1 ** t)) / (np.sqrt((1 - b2 ** t) * g * g / (1 - b2 ** t)) + eps)
+        assert np.allclose(p[0], w, rtol=0, atol=1e-12), t

@@ -144,3 +144,121 @@ def test_mol20_mixed_cg_preconditioner_fewer_sweeps():
         e = S.rayleigh_ritz_f64().cpu().numpy()
         assert np.abs(e[:w.judged] - ref).max() <= 1e-6, kind
     assert sweeps["cg"] < sweeps["filter"], sweeps
+
+
+def _solve_to_golden(S, ref, tol, max_sweeps):
+    """Steps until the eigenvalues the solver reports (from its closing FP64
+    Rayleigh-Ritz in FP32 mode, as its schedule decides) are within tol Ha of
+    the oracle's reference; returns (sweeps, max error)."""
+    judged = len(ref)
+    err = float("inf")
+    for _ in range(max_sweeps):
+        eps, _, _ = S.step()
+        st = S.stats()
+        if st["eps_f64"]:
+            err = float(np.abs(eps.cpu().numpy()[:judged] - ref).max())
+            if err <= tol:
+                return st["sweeps"], err
+    raise AssertionError(f"not within {tol} Ha of the oracle after {max_sweeps} sweeps (last error {err:.2e})")
+
+
+SCHEDULE = dict(stall_sweeps=3, stall_ratio=0.9, rr64_every=10, rr64_below=3e-3, rr64_always=1e-4)
+
+
+def test_mol100_mixed_filter_reaches_oracle_eigenvalues():
+    """The 100-atom molecule (654 520 points, 256 FP32 states in blocks of 32,
+    the mixed-precision workload) from the seeded random start: every one of
+    the 224 judged eigenvalues within 1e-6 Ha of the oracle's FP64 reference,
+    through the solver's own FP64 Rayleigh-Ritz schedule."""
+    from paper_1306_2953_gb300 import api
+    w = wl.MOL100
+    lg, H, g_ora, H_ora, idx = _system(w)
+    ref = np.array(golden(w.name)["eigenvalues"])
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).float().cuda(), w.block, 1e-4,
+                   n_wanted=len(ref), **SCHEDULE)
+    sweeps, err = _solve_to_golden(S, ref, 1e-6, 200)
+    assert S.stats()["eps_f64"] == 1 and err <= 1e-6
+    assert H.status() == 0
+
+
+def test_mol20_mixed_learned_reaches_oracle_eigenvalues():
+    """The learned mode as a sequence of library calls (solver with the
+    learned preconditioner, rs_precond_train on the method's own residuals,
+    sweeps with the stall fallback and the FP64 Rayleigh-Ritz schedule):
+    every eigenvalue of the 20-atom molecule within 1e-6 Ha of the oracle."""
+    from paper_1306_2953_gb300 import _lib, api
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    ref = np.array(golden(w.name)["eigenvalues"])
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).float().cuda(), w.block, 1e-4,
+                   precond=_lib.RS_PRECOND_LEARNED, n_wanted=len(ref), **SCHEDULE)
+    w0 = torch.from_numpy(np.concatenate([a.reshape(a.shape[0], a.shape[1], 27).ravel()
+                                          for a in wl.conv_init(11)]).astype(np.float32)).cuda()
+    losses = S.train_precond(lg, w0, n_res=40, n_tiles=2048, epochs=3)
+    assert len(losses) == 3 and losses[-1] < losses[0]
+    st = S.stats()
+    assert st["precond"] == _lib.RS_PRECOND_LEARNED and st["train_fit_seconds"] > 0
+    _solve_to_golden(S, ref, 1e-6, 400)
+
+
+def test_nan_in_orbitals_is_reported():
+    """A NaN written into one orbital on the host (copied into the solver's
+    own orbitals) makes the next sweep return RS_ENAN instead of iterating."""
+    from paper_1306_2953_gb300 import api
+    from paper_1306_2953_gb300._lib import RS_ENAN, RsError
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]
+    for dt in (torch.float64, torch.float32):
+        S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).to(dt).cuda(), w.block, 1e-4)
+        S.step()
+        host = S.psi().cpu()
+        host[1234, 5] = float("nan")
+        S.psi().copy_(host.cuda())
+        torch.cuda.synchronize()
+        with pytest.raises(RsError) as e:
+            S.step()
+        assert e.value.code == RS_ENAN, dt
+
+
+def test_hpsi_wait_timeout_is_reported_without_a_hang():
+    """Failure detection without a GPU fault: the FP32 H psi kernel's bounded
+    pipeline waits are given a limit of zero tests, so every wait gives up at
+    once; the kernel returns, its status word is set, and a solver sweep that
+    uses it returns RS_ETIMEOUT.  With the default limit restored and the word
+    cleared, the same Hamiltonian computes correctly again."""
+    from paper_1306_2953_gb300 import api
+    from paper_1306_2953_gb300._lib import RS_ETIMEOUT, RsError
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    psi32 = wl.random_block(g_ora.npts, 32, 9).astype(np.float32)
+    psi = torch.from_numpy(np.ascontiguousarray(psi32[idx])).cuda()
+    assert H.status() == 0
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]))
+                   .float().cuda(), w.block, 1e-4)
+    H.set_wait_limit(0)
+    H.apply(psi)
+    torch.cuda.synchronize()
+    assert H.status() == 1
+    with pytest.raises(RsError) as e:
+        S.step()
+    assert e.value.code == RS_ETIMEOUT
+    H.set_wait_limit(-1)
+    H.reset_status()
+    out = H.apply(psi).double().cpu().numpy()
+    ref = H_ora.apply(psi32.astype(np.float64))[idx]
+    assert np.max(np.linalg.norm(out - ref, axis=0) / np.linalg.norm(ref, axis=0)) <= 2e-6
+    assert H.status() == 0
+
+
+def test_solver_schedule_config_rejected_when_invalid():
+    from paper_1306_2953_gb300 import api
+    from paper_1306_2953_gb300._lib import RsError
+    w = wl.HO32
+    lg, H, g_ora, H_ora, idx = _system(w)
+    psi0 = torch.zeros((g_ora.npts, 16), dtype=torch.float64, device="cuda")
+    for bad in (dict(n_wanted=17), dict(stall_sweeps=2, stall_ratio=1.5), dict(rr64_every=-1)):
+        with pytest.raises(RsError):
+            api.Solver(H, psi0, 16, 1e-6, **bad)

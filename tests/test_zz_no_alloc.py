@@ -1,9 +1,8 @@
 """The allocation-free orthonormalisation entry point.
 
 rs_orthonormalize_noalloc is for callers that cannot allocate device memory
-when they need the operation (graph capture without allocation nodes,
-frameworks that own every device buffer, loops that forbid cudaMalloc after
-start-up).  It keeps its scratch in a fixed device array inside the library.
+when they need the operation (frameworks that own every device buffer and
+hand out no workspace, loops that forbid cudaMalloc after start-up).  It keeps its scratch in a fixed device array inside the library.
 This test calls it through the C ABI and checks it against the workspace
 entry point rs_orthonormalize, on two calls in a row with different sizes
 and precisions (the second call must not be disturbed by what the first left
