@@ -343,34 +343,59 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
     return out
 
 
-def nb_sweep(workload):
-    """H psi throughput against the block size: for nb = 1..64 states and
-    FP32 / FP64, the algorithmic bytes of one block application
-    (rs_ham_apply_bytes) over its CUDA-event time, ψ [npts][64] resident."""
+ORDER_NAMES = {4: "brick4", 1: "lexicographic", 2: "brick2", 8: "brick8", -1: "morton", -2: "tile_column"}
+
+
+def nb_sweep(workload, orders=(4,)):
+    """H psi throughput against the block size and the grid's point order
+    (the analogue of the paper's block-size and ordering study, Sec. V.A):
+    for every order, nb = 1..64 states and FP32 / FP64, the algorithmic
+    bytes of one block application (rs_ham_apply_bytes) over its CUDA-event
+    time, psi [npts][64] resident.  Every order runs the generic fused kernel
+    (neighbours through the point map); the default brick order also runs the
+    automatic selection, whose FP32 blocks of 32 and 64 take the ring kernel."""
     import torch
-    from paper_1306_2953_gb300 import _lib
-    g, H = build_system(workload)
+    from paper_1306_2953_gb300 import _lib, api
+    spec = workload.system
+    atoms = wl.atom_positions(spec)
+    E = wl.kb_couplings(spec)
     peak, kind = measured_peaks()
-    out = {"workload": workload.name, "npts": g.npts, "peak_gbs": peak, "peak_source": kind, "rows": []}
-    for dt, code in ((torch.float32, _lib.RS_F32), (torch.float64, _lib.RS_F64)):
-        psi = torch.from_numpy(wl.random_block(g.npts, 64, 5)).to(dt).cuda()
-        hpsi = torch.empty_like(psi)
-        for nb in (1, 2, 4, 8, 16, 32, 64):
-            reps = max(3, min(200, int(2e9 / max(H.apply_bytes(nb, code), 1))))
-            for _ in range(3):
-                H.apply(psi[:, :nb], hpsi[:, :nb], nb=nb)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                H.apply(psi[:, :nb], hpsi[:, :nb], nb=nb)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
-            gbs = H.apply_bytes(nb, code) / (ms * 1e-3) / 1e9
-            out["rows"].append({"dtype": "f32" if code == _lib.RS_F32 else "f64", "nb": nb, "us_per_apply": ms * 1e3,
-                                "gbs": gbs, "frac_of_peak": gbs / peak})
-        del psi, hpsi
+    out = {"workload": workload.name, "peak_gbs": peak, "peak_source": kind, "rows": []}
+    for order in orders:
+        g = api.Grid.spheres(atoms, spec.radius, spec.h, order=order)
+        H = api.Hamiltonian(g, wl.local_potential(g.coords(), atoms), api.Projectors(g, atoms, E, spec.r_c, spec.r_cut))
+        out["npts"] = g.npts
+        kernels = [_lib.RS_KERNEL_GENERIC] + ([_lib.RS_KERNEL_AUTO] if order == 4 else [])
+        for kern in kernels:
+            H.select_kernel(kern)
+            for dt, code in ((torch.float32, _lib.RS_F32), (torch.float64, _lib.RS_F64)):
+                if kern == _lib.RS_KERNEL_AUTO and code == _lib.RS_F64:
+                    continue   # FP64 blocks always take the generic kernel
+                psi = torch.from_numpy(wl.random_block(g.npts, 64, 5)).to(dt).cuda()
+                hpsi = torch.empty_like(psi)
+                for nb in (1, 2, 4, 8, 16, 32, 64):
+                    if kern == _lib.RS_KERNEL_AUTO and nb < 32:
+                        continue
+                    reps = max(3, min(200, int(2e9 / max(H.apply_bytes(nb, code), 1))))
+                    for _ in range(3):
+                        H.apply(psi[:, :nb], hpsi[:, :nb], nb=nb)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        H.apply(psi[:, :nb], hpsi[:, :nb], nb=nb)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / reps
+                    gbs = H.apply_bytes(nb, code) / (ms * 1e-3) / 1e9
+                    out["rows"].append({"order": ORDER_NAMES[order],
+                                        "kernel": "generic" if kern == _lib.RS_KERNEL_GENERIC else "auto (ring)",
+                                        "dtype": "f32" if code == _lib.RS_F32 else "f64", "nb": nb,
+                                        "us_per_apply": ms * 1e3, "gbs": gbs, "frac_of_peak": gbs / peak})
+                del psi, hpsi
+        if H.status() != 0:
+            raise RuntimeError("an H psi pipeline wait gave up during the sweep")
+        del H, g
     print(json.dumps(out))
     return 0
 
@@ -452,6 +477,9 @@ def main():
     ap.add_argument("--nb-sweep", action="store_true",
                     help="print H psi GB/s of algorithmic bytes for blocks of 1..64 states (FP32 and FP64) on "
                          "--workload and exit (no benchmark line)")
+    ap.add_argument("--orders", default="4",
+                    help="point orders of the --nb-sweep, comma separated: 4, 1, 2, 8 (brick edges; 1 = "
+                         "lexicographic), -1 (Morton), -2 (tile columns), or 'all'")
     ap.add_argument("--learned-apply", type=int, default=0,
                     help="profiling aid: time this many learned-preconditioner applications to one 32-state "
                          "block of --workload (seeded initial weights) and exit (no benchmark line)")
@@ -467,7 +495,8 @@ def main():
     if args.profile_sweeps > 0:
         return profile_sweeps(workload, args.profile_sweeps, args.sweep_precision)
     if args.nb_sweep:
-        return nb_sweep(workload)
+        orders = (4, 1, 2, 8, -1, -2) if args.orders == "all" else tuple(int(x) for x in args.orders.split(","))
+        return nb_sweep(workload, orders)
     if args.learned_apply > 0:
         return learned_apply_timing(workload, args.learned_apply)
 

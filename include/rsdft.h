@@ -69,20 +69,36 @@ int rs_last_error(char *buf, size_t len);
 const char *rs_version(void);
 
 /* ------------------------------------------------------------------ grid --
- * Sec. II (Fig. 1): a uniform grid of spacing h whose shape is the union of
+ * Point order (the `order` argument; Sec. V.A orders the grid by small
+ * boxes of points for cache locality).  With map coordinates (u, v, w) along
+ * axes 0, 1, 2 (w fastest):
+ *   0 or 4   bricks of 4x4x4 points in brick raster order, each brick
+ *            lexicographic (the default; the FP32 32-state kernel needs it)
+ *   1, 2, 8  bricks of order^3 points (1: plain lexicographic)
+ *   RS_ORDER_MORTON   the Morton Z-curve (bits of u, v, w interleaved)
+ *   RS_ORDER_TILECOL  columns of 16 x 8 points along axes 2 and 1 in raster
+ *            order, each column plane by plane along axis 0, each plane row
+ *            by row (every tile-plane one contiguous run of points)
+ * Every order numbers the same points; kernels other than the FP32
+ * 32-state one address neighbours through the point map and run on any. */
+enum { RS_ORDER_MORTON = -1, RS_ORDER_TILECOL = -2 };
+
+/* Sec. II (Fig. 1): a uniform grid of spacing h whose shape is the union of
  * spheres of `radius` around the atoms.  Lattice points are r = h*(i,j,k);
  * a point is included iff for some atom A, (x-X)^2+(y-Y)^2+(z-Z)^2 <=
  * radius^2, evaluated in IEEE double in that order with x = h*i (exact
  * integer decisions; no contraction into FMA).  Host-only: no GPU needed.
  *   xyz      host [n_atoms][3] atom positions (Bohr)
+ *   order    point order (see above)
  *   out      receives a new handle (free with rs_grid_destroy)
  * Errors: RS_EINVAL for n_atoms < 1, radius <= 0, h <= 0, non-finite input,
- * or a grid that would exceed 2^31-1 points or map entries. */
-int rs_grid_create_spheres(const double *xyz, int n_atoms, double radius, double h, rs_grid **out);
+ * an unknown order, or a grid that would exceed 2^31-1 points or map entries. */
+int rs_grid_create_spheres(const double *xyz, int n_atoms, double radius, double h, int order, rs_grid **out);
 
 /* Full n0 x n1 x n2 box (zero boundary conditions beyond it), point (i,j,k)
- * at ((i-(n0-1)/2) h, (j-(n1-1)/2) h, (k-(n2-1)/2) h).  Host-only. */
-int rs_grid_create_box(int n0, int n1, int n2, double h, rs_grid **out);
+ * at ((i-(n0-1)/2) h, (j-(n1-1)/2) h, (k-(n2-1)/2) h), in the given point
+ * order.  Host-only. */
+int rs_grid_create_box(int n0, int n1, int n2, double h, int order, rs_grid **out);
 
 /* Number of points, lattice coordinate of map element (0,0,0), map
  * dimensions (the bounding box plus a 4-point margin on every side) and the
@@ -162,6 +178,14 @@ int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi, void *hps
  * iteration limit (that call's hpsi is incomplete).  Blocking: it reads a
  * device word after the work queued before it.  Errors: RS_EINVAL, RS_ECUDA. */
 int rs_ham_status(rs_ham *h, int *flags);
+
+/* Kernel selection of rs_ham_apply_block (a profiling aid for comparisons
+ * such as the point-order study): RS_KERNEL_AUTO (0, the default) lets FP32
+ * 32-state blocks take the persistent ring kernel where the grid allows it;
+ * RS_KERNEL_GENERIC (1) sends every block to the generic fused kernel, which
+ * addresses neighbours through the point map in any point order.  Host-only. */
+enum { RS_KERNEL_AUTO = 0, RS_KERNEL_GENERIC = 1 };
+int rs_ham_select_kernel(rs_ham *h, int which);
 
 /* Clears the status word read by rs_ham_status (blocking). */
 int rs_ham_reset_status(rs_ham *h);

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(_HERE, "librsdft.so")
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENOTSPD, RS_ENOCONV, RS_ENAN, RS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 RS_F64, RS_F32 = 0, 1
 RS_PRECOND_NONE, RS_PRECOND_FILTER, RS_PRECOND_LEARNED, RS_PRECOND_CG = 0, 1, 2, 3
+RS_ORDER_MORTON, RS_ORDER_TILECOL = -1, -2
+RS_KERNEL_AUTO, RS_KERNEL_GENERIC = 0, 1
 _NAMES = {RS_EINVAL: "RS_EINVAL", RS_ENOMEM: "RS_ENOMEM", RS_ECUDA: "RS_ECUDA", RS_ENOTSPD: "RS_ENOTSPD",
           RS_ENOCONV: "RS_ENOCONV", RS_ENAN: "RS_ENAN", RS_ETIMEOUT: "RS_ETIMEOUT"}
 
@@ -61,8 +63,8 @@ PP = ctypes.POINTER(ctypes.c_void_p)
 SIGNATURES = {
     "rs_last_error": (I32, [ctypes.c_char_p, ctypes.c_size_t]),
     "rs_version": (ctypes.c_char_p, []),
-    "rs_grid_create_spheres": (None, [P, I32, F64, F64, PP]),
-    "rs_grid_create_box": (None, [I32, I32, I32, F64, PP]),
+    "rs_grid_create_spheres": (None, [P, I32, F64, F64, I32, PP]),
+    "rs_grid_create_box": (None, [I32, I32, I32, F64, I32, PP]),
     "rs_grid_info": (None, [P, P, P, P, P]),
     "rs_grid_ijk": (None, [P, P]),
     "rs_grid_coords": (None, [P, P]),
@@ -78,6 +80,7 @@ SIGNATURES = {
     "rs_ham_apply_bytes": (I64, [P, I32, I32]),
     "rs_ham_status": (None, [P, P]),
     "rs_ham_reset_status": (None, [P]),
+    "rs_ham_select_kernel": (None, [P, I32]),
     "rs_ham_set_wait_limit": (None, [P, I32]),
     "rs_ham_timing": (None, [P, I32]),
     "rs_ham_timing_read": (None, [P, P, P, P]),

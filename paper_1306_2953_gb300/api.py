@@ -43,16 +43,18 @@ class Grid:
         self._h = handle
 
     @classmethod
-    def spheres(cls, xyz, radius: float, h: float) -> "Grid":
+    def spheres(cls, xyz, radius: float, h: float, order: int = 0) -> "Grid":
+        """order: 0/4 bricks of 4^3 (default), 1/2/8 other bricks,
+        _lib.RS_ORDER_MORTON or _lib.RS_ORDER_TILECOL."""
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         out = ctypes.c_void_p()
-        call("rs_grid_create_spheres", _ptr(xyz), len(xyz), float(radius), float(h), ctypes.byref(out))
+        call("rs_grid_create_spheres", _ptr(xyz), len(xyz), float(radius), float(h), int(order), ctypes.byref(out))
         return cls(out)
 
     @classmethod
-    def box(cls, n0: int, n1: int, n2: int, h: float) -> "Grid":
+    def box(cls, n0: int, n1: int, n2: int, h: float, order: int = 0) -> "Grid":
         out = ctypes.c_void_p()
-        call("rs_grid_create_box", n0, n1, n2, float(h), ctypes.byref(out))
+        call("rs_grid_create_box", n0, n1, n2, float(h), int(order), ctypes.byref(out))
         return cls(out)
 
     def info(self):
@@ -178,6 +180,10 @@ class Hamiltonian:
         f = ctypes.c_int32()
         call("rs_ham_status", self._h, ctypes.byref(f))
         return int(f.value)
+
+    def select_kernel(self, which: int):
+        """rs_ham_select_kernel: _lib.RS_KERNEL_AUTO or RS_KERNEL_GENERIC."""
+        call("rs_ham_select_kernel", self._h, int(which))
 
     def reset_status(self):
         """rs_ham_reset_status: clears the status word (blocking)."""

@@ -22,6 +22,7 @@ struct rs_grid {
     int32_t origin[3] = {0, 0, 0};   // lattice coordinate of map element (0,0,0)
     int32_t dims[3] = {0, 0, 0};     // map extents (bounding box + 4-point margin)
     double h = 0.0;
+    int order = 4;                   // point order: brick edge (1, 2, 4, 8), RS_ORDER_MORTON or RS_ORDER_TILECOL
     double center[3] = {0.0, 0.0, 0.0};  // coords = (ijk - center) * h
     std::vector<int32_t> ijk;        // [npts][3]
     std::vector<int32_t> map;        // [dims0][dims1][dims2], -1 = not a grid point

@@ -37,14 +37,31 @@ int fail(int code, const char *fmt, ...) {
 
 const std::string &last_error() { return g_err; }
 
-// Brick edge of the point ordering (bricks of BRICK^3 lattice points).
-static const int BRICK = 4;
 // Margin of the point map: the star stencil's half-width.
 static const int MARGIN = 4;
+// Tile of the tile-column order: 16 points along map axis 2, 8 along axis 1.
+static const int TILE_X = 16, TILE_Y = 8;
 
-// Orders the marked lattice points brick by brick and fills ijk / map.
-// mask covers the lattice box [lo, lo+ext) (ext[2] fastest).
-static int finish_grid(rs_grid *g, const std::vector<uint8_t> &mask, const int64_t lo[3], const int64_t ext[3]) {
+static bool valid_order(int order) {
+    return order == 0 || order == 1 || order == 2 || order == 4 || order == 8 || order == RS_ORDER_MORTON ||
+           order == RS_ORDER_TILECOL;
+}
+
+// Interleaves the bits of (u, v, w), u the most significant at every level.
+static uint64_t morton_key(uint64_t u, uint64_t v, uint64_t w) {
+    uint64_t k = 0;
+    for (int b = 20; b >= 0; --b) k = (k << 3) | (((u >> b) & 1) << 2) | (((v >> b) & 1) << 1) | ((w >> b) & 1);
+    return k;
+}
+
+// Orders the marked lattice points and fills ijk / map.  mask covers the
+// lattice box [lo, lo+ext) (ext[2] fastest).  Orders (map coordinates u, v, w
+// along axes 0, 1, 2): bricks of order^3 points in brick raster order, each
+// brick lexicographic (order 1: plain lexicographic); the Morton Z-curve; or
+// tile columns of TILE_X x TILE_Y points along axes 2 and 1 in raster
+// order, each column plane by plane along axis 0, each plane row by row.
+static int finish_grid(rs_grid *g, const std::vector<uint8_t> &mask, const int64_t lo[3], const int64_t ext[3],
+                       int order) {
     int64_t mn[3] = {std::numeric_limits<int64_t>::max(), std::numeric_limits<int64_t>::max(),
                      std::numeric_limits<int64_t>::max()};
     int64_t mx[3] = {std::numeric_limits<int64_t>::min(), std::numeric_limits<int64_t>::min(),
@@ -78,26 +95,57 @@ static int finish_grid(rs_grid *g, const std::vector<uint8_t> &mask, const int64
         return fail(RS_ENOMEM, "host allocation failed");
     }
     g->npts = count;
-    int64_t nb[3];
-    for (int d = 0; d < 3; ++d) nb[d] = (dims[d] + BRICK - 1) / BRICK;
+    g->order = order == 0 ? 4 : order;
     int64_t next = 0;
-    for (int64_t B0 = 0; B0 < nb[0]; ++B0)
-        for (int64_t B1 = 0; B1 < nb[1]; ++B1)
-            for (int64_t B2 = 0; B2 < nb[2]; ++B2)
-                for (int64_t u = B0 * BRICK; u < std::min(dims[0], (B0 + 1) * BRICK); ++u)
-                    for (int64_t v = B1 * BRICK; v < std::min(dims[1], (B1 + 1) * BRICK); ++v)
-                        for (int64_t w = B2 * BRICK; w < std::min(dims[2], (B2 + 1) * BRICK); ++w) {
-                            int64_t p[3] = {g->origin[0] + u, g->origin[1] + v, g->origin[2] + w};
-                            int64_t a = p[0] - lo[0], b = p[1] - lo[1], c = p[2] - lo[2];
-                            if (a < 0 || b < 0 || c < 0 || a >= ext[0] || b >= ext[1] || c >= ext[2]) continue;
-                            if (!mask[(a * ext[1] + b) * ext[2] + c]) continue;
-                            g->map[(size_t)((u * dims[1] + v) * dims[2] + w)] = (int32_t)next;
-                            g->ijk[3 * next + 0] = (int32_t)p[0];
-                            g->ijk[3 * next + 1] = (int32_t)p[1];
-                            g->ijk[3 * next + 2] = (int32_t)p[2];
-                            ++next;
-                        }
-    return RS_OK;
+    // numbers map position (u, v, w) if it is a marked lattice point
+    auto take = [&](int64_t u, int64_t v, int64_t w) {
+        const int64_t p[3] = {g->origin[0] + u, g->origin[1] + v, g->origin[2] + w};
+        const int64_t a = p[0] - lo[0], b = p[1] - lo[1], c = p[2] - lo[2];
+        if (a < 0 || b < 0 || c < 0 || a >= ext[0] || b >= ext[1] || c >= ext[2]) return;
+        if (!mask[(a * ext[1] + b) * ext[2] + c]) return;
+        g->map[(size_t)((u * dims[1] + v) * dims[2] + w)] = (int32_t)next;
+        g->ijk[3 * next + 0] = (int32_t)p[0];
+        g->ijk[3 * next + 1] = (int32_t)p[1];
+        g->ijk[3 * next + 2] = (int32_t)p[2];
+        ++next;
+    };
+    if (g->order > 0) {
+        const int B = g->order;
+        int64_t nb[3];
+        for (int d = 0; d < 3; ++d) nb[d] = (dims[d] + B - 1) / B;
+        for (int64_t B0 = 0; B0 < nb[0]; ++B0)
+            for (int64_t B1 = 0; B1 < nb[1]; ++B1)
+                for (int64_t B2 = 0; B2 < nb[2]; ++B2)
+                    for (int64_t u = B0 * B; u < std::min(dims[0], (B0 + 1) * B); ++u)
+                        for (int64_t v = B1 * B; v < std::min(dims[1], (B1 + 1) * B); ++v)
+                            for (int64_t w = B2 * B; w < std::min(dims[2], (B2 + 1) * B); ++w) take(u, v, w);
+    } else if (g->order == RS_ORDER_TILECOL) {
+        for (int64_t t1 = 0; t1 < (dims[1] + TILE_Y - 1) / TILE_Y; ++t1)
+            for (int64_t t2 = 0; t2 < (dims[2] + TILE_X - 1) / TILE_X; ++t2)
+                for (int64_t u = 0; u < dims[0]; ++u)
+                    for (int64_t v = t1 * TILE_Y; v < std::min(dims[1], (t1 + 1) * TILE_Y); ++v)
+                        for (int64_t w = t2 * TILE_X; w < std::min(dims[2], (t2 + 1) * TILE_X); ++w) take(u, v, w);
+    } else {   // Morton
+        std::vector<std::pair<uint64_t, int64_t>> keys;
+        try {
+            keys.reserve((size_t)count);
+        } catch (const std::bad_alloc &) {
+            return fail(RS_ENOMEM, "host allocation failed");
+        }
+        for (int64_t u = 0; u < dims[0]; ++u)
+            for (int64_t v = 0; v < dims[1]; ++v)
+                for (int64_t w = 0; w < dims[2]; ++w) {
+                    const int64_t a = g->origin[0] + u - lo[0], b = g->origin[1] + v - lo[1], c = g->origin[2] + w - lo[2];
+                    if (a < 0 || b < 0 || c < 0 || a >= ext[0] || b >= ext[1] || c >= ext[2]) continue;
+                    if (mask[(a * ext[1] + b) * ext[2] + c]) keys.emplace_back(morton_key(u, v, w), (u * dims[1] + v) * dims[2] + w);
+                }
+        std::sort(keys.begin(), keys.end());
+        for (const auto &k : keys) {
+            const int64_t m = k.second, w = m % dims[2], v = (m / dims[2]) % dims[1], u = m / (dims[2] * dims[1]);
+            take(u, v, w);
+        }
+    }
+    return next == count ? RS_OK : fail(RS_EINVAL, "grid ordering lost points");
 }
 
 }  // namespace rs
@@ -116,8 +164,10 @@ extern "C" int rs_last_error(char *buf, size_t len) {
 
 extern "C" const char *rs_version(void) { return "rsdft 0.1 sm_103a"; }
 
-extern "C" int rs_grid_create_spheres(const double *xyz, int n_atoms, double radius, double h, rs_grid **out) {
+extern "C" int rs_grid_create_spheres(const double *xyz, int n_atoms, double radius, double h, int order,
+                                      rs_grid **out) {
     if (!xyz || !out || n_atoms < 1) return fail(RS_EINVAL, "rs_grid_create_spheres: bad arguments");
+    if (!rs::valid_order(order)) return fail(RS_EINVAL, "rs_grid_create_spheres: bad point order %d", order);
     if (!(radius > 0) || !(h > 0) || !std::isfinite(radius) || !std::isfinite(h))
         return fail(RS_EINVAL, "rs_grid_create_spheres: radius and h must be positive");
     for (int i = 0; i < 3 * n_atoms; ++i)
@@ -170,7 +220,7 @@ extern "C" int rs_grid_create_spheres(const double *xyz, int n_atoms, double rad
     rs_grid *g = new (std::nothrow) rs_grid;
     if (!g) return fail(RS_ENOMEM, "host allocation failed");
     g->h = h;
-    int rc = rs::finish_grid(g, mask, lo, ext);
+    int rc = rs::finish_grid(g, mask, lo, ext, order);
     if (rc != RS_OK) {
         delete g;
         return rc;
@@ -179,9 +229,10 @@ extern "C" int rs_grid_create_spheres(const double *xyz, int n_atoms, double rad
     return RS_OK;
 }
 
-extern "C" int rs_grid_create_box(int n0, int n1, int n2, double h, rs_grid **out) {
+extern "C" int rs_grid_create_box(int n0, int n1, int n2, double h, int order, rs_grid **out) {
     if (!out || n0 < 1 || n1 < 1 || n2 < 1 || !(h > 0) || !std::isfinite(h))
         return fail(RS_EINVAL, "rs_grid_create_box: bad arguments");
+    if (!rs::valid_order(order)) return fail(RS_EINVAL, "rs_grid_create_box: bad point order %d", order);
     if ((int64_t)n0 * n1 * n2 > (int64_t)1 << 30) return fail(RS_EINVAL, "rs_grid_create_box: grid too large");
     *out = nullptr;
     int64_t lo[3] = {0, 0, 0}, ext[3] = {n0, n1, n2};
@@ -192,7 +243,7 @@ extern "C" int rs_grid_create_box(int n0, int n1, int n2, double h, rs_grid **ou
     g->center[0] = (n0 - 1) / 2.0;
     g->center[1] = (n1 - 1) / 2.0;
     g->center[2] = (n2 - 1) / 2.0;
-    int rc = rs::finish_grid(g, mask, lo, ext);
+    int rc = rs::finish_grid(g, mask, lo, ext, order);
     if (rc != RS_OK) {
         delete g;
         return rc;

@@ -471,6 +471,7 @@ struct rs_ham {
         cproj, dummy, scratch;
     std::map<std::pair<int, int>, WorkList *> work;
     RingPlan *ring = nullptr;      // tables of the ring-buffer FP32 kernel (nullptr: not usable)
+    int kernel = RS_KERNEL_AUTO;   // rs_ham_select_kernel
     // optional per-launch timing (rs_ham_timing)
     bool timing = false;
     std::vector<cudaEvent_t> events;   // 3 per recorded call
@@ -735,7 +736,7 @@ static int apply_t(rs_ham *H, const T *psi, int64_t ldp, T *hpsi, int64_t ldh, i
         default:
             if constexpr (SGMAX >= 32) {
                 if constexpr (sizeof(T) == 4) {
-                    if (ring_usable(H->ring, psi, ldp, nb)) {
+                    if (H->kernel == RS_KERNEL_AUTO && ring_usable(H->ring, psi, ldp, nb)) {
                         float w[5];
                         for (int j = 0; j < 5; ++j) w[j] = (float)H->w[j];
                         rc = ring_launch(H->ring, psi, ldp, hpsi, ldh, H->cproj.as<float>(), nb, w, st);
@@ -795,6 +796,12 @@ extern "C" int rs_ham_status(rs_ham *h, int *flags) {
     int f = 0;
     RS_TRY(ring_status(h->ring, &f));
     *flags = f;
+    return RS_OK;
+}
+
+extern "C" int rs_ham_select_kernel(rs_ham *h, int which) {
+    if (!h || (which != RS_KERNEL_AUTO && which != RS_KERNEL_GENERIC)) return fail(RS_EINVAL, "rs_ham_select_kernel: bad argument");
+    h->kernel = which;
     return RS_OK;
 }
 

@@ -542,7 +542,9 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
                     const std::vector<float> &cg32, const std::vector<float> &v32, float w0, int n_atoms, int slab) {
     (void)n_atoms;
     *out = nullptr;
-    if (g->npts >= (1 << 28) || slab < 1 || slab > MAX_SLAB) return RS_OK;
+    // the descriptors describe four consecutive points per brick row: the
+    // kernel needs the order of bricks of 4^3 points
+    if (g->order != 4 || g->npts >= (1 << 28) || slab < 1 || slab > MAX_SLAB) return RS_OK;
     const int d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
     auto at = [&](int a0, int a1, int a2) -> int32_t {
         if (a0 < 0 || a1 < 0 || a2 < 0 || a0 >= d0 || a1 >= d1 || a2 >= d2) return -1;

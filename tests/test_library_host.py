@@ -7,7 +7,7 @@ import pytest
 import workloads as wl
 from oracle import grid as og, hamiltonian as oh
 from paper_1306_2953_gb300 import api
-from paper_1306_2953_gb300._lib import RS_EINVAL, RsError
+from paper_1306_2953_gb300._lib import RS_EINVAL, RS_ORDER_MORTON, RS_ORDER_TILECOL, RsError
 from tests.helpers import SMALL_ATOMS, SMALL_E, SMALL_H, SMALL_RADIUS, lib_to_oracle_index
 
 
@@ -44,6 +44,50 @@ def test_brick_order():
     brick = rel // 4
     key = (brick[:, 0] * 10000 + brick[:, 1]) * 10000 + brick[:, 2]
     assert np.all(np.diff(key) >= 0), "points are not grouped brick by brick in brick order"
+
+
+def _order_key(rel, order, dims):
+    """The sort key each point order defines on map coordinates (u, v, w)."""
+    u, v, w = (rel[:, d].astype(np.int64) for d in range(3))
+    if order > 0:
+        b = order
+        return ((((u // b) * 10000 + v // b) * 10000 + w // b) * 10000 + (u % b)) * 10000 * 10000 \
+            + (v % b) * 10000 + (w % b)
+    if order == RS_ORDER_TILECOL:
+        nt2 = (dims[2] + 15) // 16
+        col = (v // 8) * nt2 + w // 16
+        return ((col * 10000 + u) * 100 + v % 8) * 100 + w % 16
+    key = np.zeros(len(u), dtype=np.int64)       # Morton: bits interleaved, u most significant
+    for bit in range(20, -1, -1):
+        key = (key << 3) | (((u >> bit) & 1) << 2) | (((v >> bit) & 1) << 1) | ((w >> bit) & 1)
+    return key
+
+
+@pytest.mark.parametrize("order", [1, 2, 4, 8, RS_ORDER_MORTON, RS_ORDER_TILECOL])
+def test_point_orders(order):
+    """Every point order numbers the same lattice points (bit-exact against
+    the oracle's grid) with a consistent map, in the sequence its definition
+    gives: the order's key strictly increases with the point index."""
+    spec = wl.MoleculeSpec(7, 5.0, 1.5, 2.5, 0.41, 11)
+    atoms = wl.atom_positions(spec)
+    lg = api.Grid.spheres(atoms, spec.radius, spec.h, order=order)
+    ref = og.sphere_union_grid(atoms, spec.radius, spec.h)
+    lib_ijk = _same_points(lg, ref)
+    npts, origin, dims, h = lg.info()
+    rel = lib_ijk - np.array(origin)
+    mp = lg.point_map()
+    assert np.array_equal(mp[rel[:, 0], rel[:, 1], rel[:, 2]], np.arange(npts))
+    assert np.all(np.diff(_order_key(rel, order, dims)) > 0)
+    box = api.Grid.box(9, 6, 20, 0.3, order=order)
+    _, bo, bd, _ = box.info()
+    brel = box.ijk() - np.array(bo)
+    assert box.npts == 9 * 6 * 20 and np.all(np.diff(_order_key(brel, order, bd)) > 0)
+
+
+def test_point_order_rejects_unknown():
+    with pytest.raises(RsError) as e:
+        api.Grid.spheres(np.array([[0.0, 0.0, 0.0]]), 2.0, 0.3, order=3)
+    assert e.value.code == RS_EINVAL
 
 
 def test_box_grid_bit_exact():
