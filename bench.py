@@ -346,6 +346,97 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
 ORDER_NAMES = {4: "brick4", 1: "lexicographic", 2: "brick2", 8: "brick8", -1: "morton", -2: "tile_column"}
 
 
+def certificate_bound(eps, res):
+    """Per-state eigenvalue error bound from FP64 Ritz values and residual
+    norms (rs_solver_certify): r^2 / gap where the gap to the nearest other
+    Ritz value exceeds r, else r."""
+    e = np.asarray(eps)
+    srt = np.sort(e)
+    pos = np.searchsorted(srt, e)
+    lo = np.where(pos > 0, e - srt[np.maximum(pos - 1, 0)], np.inf)
+    hi = np.where(pos + 1 < len(srt), srt[np.minimum(pos + 1, len(srt) - 1)] - e, np.inf)
+    gap = np.minimum(lo, hi)
+    r = np.asarray(res)
+    return np.where(gap > r, r * r / np.maximum(gap, 1e-300), r)
+
+
+def certified_solve(workload, modes, r_stop=1e-4, tol=1e-6, max_seconds=720.0, f64_sweeps=2):
+    """Time to a certified tol Ha for a workload without an oracle reference
+    (the 300-atom molecule): sweeps until the largest FP32-measured residual of
+    the judged states is below r_stop, then rs_solver_certify (FP64
+    Rayleigh-Ritz and FP64 residual norms of the Ritz vectors); the error
+    bound r^2/gap of every judged state must be <= tol, otherwise ten more
+    sweeps and a new certificate.  The plain FP64 path is timed for
+    f64_sweeps sweeps and extrapolated to the filter mode's sweep count."""
+    import torch
+    from paper_1306_2953_gb300 import api, _lib
+    g, H = build_any(workload)
+    judged = workload.judged
+    out = {"workload": workload.name, "npts": g.npts, "states": workload.n_states, "judged": judged,
+           "tolerance_ha": tol, "r_stop": r_stop, "reference": "FP64 certificate (rs_solver_certify): "
+           "max over judged states of r^2/gap (r where gap <= r)", "modes": {}}
+    psi0 = wl.random_block(g.npts, workload.n_states, workload.seed)
+    w0 = initial_weights(LEARN["seed"])
+    for mode in modes:
+        dt = torch.float64 if mode.startswith("f64") else torch.float32
+        pc = _lib.RS_PRECOND_LEARNED if mode.endswith("learned") else _lib.RS_PRECOND_FILTER
+        psi0_d = torch.from_numpy(psi0).to(dt).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = api.Solver(H, psi0_d, workload.block, 1e-4, precond=pc, n_wanted=judged, stall_sweeps=3, stall_ratio=0.9)
+        t_create = time.perf_counter() - t0
+        if mode.endswith("_cg"):
+            S.set_precond_cg(api.Hamiltonian(g, np.full(g.npts, 2.0)), 5)
+        if pc == _lib.RS_PRECOND_LEARNED:
+            S.train_precond(g, w0, **LEARN)
+        if mode.startswith("f64"):
+            ts = []
+            for _ in range(f64_sweeps):
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                S.step()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t1)
+            out["modes"][mode] = {"solver_create_seconds": t_create, "seconds_per_sweep": float(np.mean(ts[1:] or ts)),
+                                  "sweeps_timed": f64_sweeps}
+            del S, psi0_d
+            continue
+        certs, bound, nxt = [], float("inf"), None
+        while True:
+            _, res, _ = S.step()
+            st = S.stats()
+            el = time.perf_counter() - t0
+            rmax = float(res[:judged].max())
+            if (nxt is None and rmax <= r_stop) or (nxt is not None and st["sweeps"] >= nxt):
+                tc = time.perf_counter()
+                eps, r64 = S.certify()
+                e, r = eps.cpu().numpy(), r64.cpu().numpy()
+                b = certificate_bound(e, r)[:judged]
+                bound = float(b.max())
+                certs.append({"sweep": st["sweeps"], "seconds": time.perf_counter() - t0,
+                              "certify_seconds": time.perf_counter() - tc, "max_r64": float(r[:judged].max()),
+                              "bound_ha": bound, "fp32_max_residual": rmax})
+                nxt = st["sweeps"] + 10
+                if bound <= tol:
+                    break
+            if el > max_seconds:
+                break
+        el = time.perf_counter() - t0
+        out["modes"][mode] = {"seconds": el, "sweeps": st["sweeps"], "certified": bound <= tol, "bound_ha": bound,
+                              "solver_create_seconds": t_create, "certificates": certs,
+                              "train_seconds": st["train_target_seconds"] + st["train_fit_seconds"],
+                              "filter_fallback_after_sweep": st["fallback_sweep"] or None,
+                              "eigenvalues_head": [float(x) for x in e[:8]] if certs else None}
+        del S, psi0_d
+    f = out["modes"].get("mixed_filter")
+    f64 = out["modes"].get("f64_filter")
+    if f and f64:
+        f64["extrapolated_seconds"] = f64["solver_create_seconds"] + f64["seconds_per_sweep"] * f["sweeps"]
+        f64["extrapolation"] = "measured FP64 seconds per sweep x the sweeps of the mixed filter solve (same start)"
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def nb_sweep(workload, orders=(4,)):
     """H psi throughput against the block size and the grid's point order
     (the analogue of the paper's block-size and ordering study, Sec. V.A):
@@ -485,6 +576,11 @@ def main():
                          "block of --workload (seeded initial weights) and exit (no benchmark line)")
     ap.add_argument("--sweep-precision", default="f32", choices=["f32", "f64"],
                     help="precision of the --profile-sweeps solver")
+    ap.add_argument("--certified", default="",
+                    help="workload(s) for the certified time to 1e-6 Ha without an oracle reference (e.g. "
+                         "mol300_h0.3): prints one JSON object per workload and exits (no benchmark line)")
+    ap.add_argument("--certified-modes", default="f64_filter,mixed_filter,mixed_learned")
+    ap.add_argument("--certified-max-seconds", type=float, default=720.0)
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling aid: run this many mixed-precision eigensolver sweeps on --workload, "
                          "print their times and exit (no benchmark line)")
@@ -492,6 +588,11 @@ def main():
     workload = wl.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, workload)
+    if args.certified:
+        for n in args.certified.split(","):
+            certified_solve(wl.WORKLOADS[n], args.certified_modes.split(","),
+                            max_seconds=args.certified_max_seconds)
+        return 0
     if args.profile_sweeps > 0:
         return profile_sweeps(workload, args.profile_sweeps, args.sweep_precision)
     if args.nb_sweep:

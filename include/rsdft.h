@@ -478,6 +478,18 @@ int rs_precond_load(rs_solver *s, const char *path);
  * call allocates two FP64 copies of the orbitals. */
 int rs_solver_rayleigh_ritz_f64(rs_solver *s, double *eps_dev, void *stream);
 
+/* Certificate of the solver's current subspace (no counterpart in the paper;
+ * for workloads without a reference solution): the FP64 Rayleigh-Ritz of
+ * rs_solver_rayleigh_ritz_f64 (orbitals widened to FP64, H applied in FP64,
+ * h x = eps S x solved in FP64), then the Ritz vectors x_k = Psi C_k and
+ * their FP64 residual norms r_k = ||H x_k - eps_k x_k|| with <x_k|x_k> = 1.
+ * For a symmetric H an eigenvalue lies within r_k of eps_k, and within
+ * r_k^2 / gap_k when gap_k separates eps_k from the rest of the spectrum.
+ * eps_dev, res_dev: device double [nst].  The iteration state is not
+ * modified.  Blocking; the first call allocates two FP64 copies of the
+ * orbitals.  Errors: RS_ENOTSPD, RS_ENOCONV (dense eigensolver cap). */
+int rs_solver_certify(rs_solver *s, double *eps_dev, double *res_dev, void *stream);
+
 /* Ritz residuals R = H psi_k - eps_k psi_k of states first..first+ncols-1
  * of the current orbitals (after the last sweep's subspace diagonalisation),
  * into R_dev [npts][ldr] (the solver's dtype): the residuals the method

@@ -101,6 +101,7 @@ SIGNATURES = {
     "rs_solver_psi": (None, [P, PP]),
     "rs_solver_residual": (None, [P, I32, I32, P, I64, P]),
     "rs_solver_rayleigh_ritz_f64": (None, [P, P, P]),
+    "rs_solver_certify": (None, [P, P, P, P]),
     "rs_solver_set_precond_weights": (None, [P, P]),
     "rs_solver_set_precond": (None, [P, I32]),
     "rs_solver_set_precond_cg": (None, [P, P, I32]),

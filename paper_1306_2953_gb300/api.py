@@ -325,6 +325,15 @@ class Solver:
         call("rs_solver_rayleigh_ritz_f64", self._h, _c(eps.data_ptr()), _stream(stream))
         return eps
 
+    def certify(self, stream=None):
+        """rs_solver_certify: FP64 Ritz values and FP64 residual norms of the
+        current subspace's Ritz vectors, as device tensors (eps, res)."""
+        import torch
+        eps = torch.empty(self.nst, dtype=torch.float64, device=self.device)
+        res = torch.empty(self.nst, dtype=torch.float64, device=self.device)
+        call("rs_solver_certify", self._h, _c(eps.data_ptr()), _c(res.data_ptr()), _stream(stream))
+        return eps, res
+
     def residual(self, first: int, ncols: int, stream=None):
         """Ritz residuals of states first..first+ncols-1 as a device tensor."""
         import torch

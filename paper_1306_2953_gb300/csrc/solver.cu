@@ -364,6 +364,87 @@ static int rayleigh_ritz_f64_impl(rs_solver *S, double *eps_dev, cudaStream_t st
     return RS_OK;
 }
 
+// out[k] = sum_p (Q[p][k] - eps[k] P[p][k])^2, Kahan-compensated FP64 sums;
+// grid (column chunks of 256, row chunks), out zeroed by the caller
+__global__ void k_resid_norm2(const double *__restrict__ P, const double *__restrict__ Q, int64_t ld, int n,
+                              const double *__restrict__ eps, int64_t npts, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double e = eps[k];
+    double acc = 0, comp = 0;
+    for (int64_t p = blockIdx.y; p < npts; p += gridDim.y) {
+        const double d = Q[p * ld + k] - e * P[p * ld + k];
+        const double y = d * d - comp;
+        const double t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+    }
+    atomicAdd(out + k, acc);
+}
+
+__global__ void k_sqrt_scale(double *a, int n, double s) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) a[k] = sqrt(s * a[k]);
+}
+
+extern "C" int rs_solver_certify(rs_solver *S, double *eps_dev, double *res_dev, void *stream) {
+    if (!S || !eps_dev || !res_dev) return fail(RS_EINVAL, "rs_solver_certify: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const rs_solver_cfg &c = S->cfg;
+    const int n = c.nst;
+    const size_t nn = (size_t)n * n;
+    if (!S->psi64.p) {
+        RS_TRY(S->psi64.alloc(sizeof(double) * (size_t)S->npts * n));
+        RS_TRY(S->hpsi64.alloc(sizeof(double) * (size_t)S->npts * n));
+        RS_TRY(S->rr64.alloc(sizeof(double) * (4 * nn + 16) + eigh_work_bytes(n)));
+    }
+    DevBuf cbuf;
+    RS_TRY(cbuf.alloc(sizeof(double) * (2 * nn)));
+    double *Sm = S->rr64.as<double>(), *h = Sm + nn, *Ui = h + nn, *T = Ui + nn;
+    double *Y = cbuf.as<double>(), *C = Y + nn;
+    int *status = reinterpret_cast<int *>(T + nn);
+    void *ew = reinterpret_cast<void *>(T + nn + 16);
+    double *P = S->psi64.as<double>(), *Q = S->hpsi64.as<double>();
+    // FP64 orbitals (a widened copy of FP32 ones) and H applied in FP64
+    if (c.dtype == RS_F32) {
+        k_widen<<<1024, 256, 0, st>>>(S->psi.as<float>(), P, S->npts * n);
+        RS_LAUNCH_CHECK();
+    } else {
+        RS_CUDA(cudaMemcpyAsync(P, S->psi.p, sizeof(double) * (size_t)S->npts * n, cudaMemcpyDeviceToDevice, st));
+    }
+    for (int b = 0; b < n; b += c.nb) RS_TRY(rs_ham_apply_block(S->h, P + b, n, Q + b, n, c.nb, RS_F64, st));
+    // h x = eps S x (Sec. VI, Eq. 7) with S = U^T U: the Ritz vectors are
+    // Psi C with C = U^-1 Y, Y the eigenvectors of U^-T h U^-1
+    RS_TRY(gram<double>(P, n, n, P, n, n, S->npts, S->dV, Sm, n, st));
+    RS_TRY(gram<double>(P, n, n, Q, n, n, S->npts, S->dV, h, n, st));
+    RS_TRY(symmetrize(Sm, n, n, st));
+    RS_TRY(symmetrize(h, n, n, st));
+    RS_TRY(cholesky(Sm, n, n, 1e-14, status, st));
+    int bad = 0;
+    RS_CUDA(cudaMemcpyAsync(&bad, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    if (bad) return fail(RS_ENOTSPD, "rs_solver_certify: the orbitals' overlap is not positive definite");
+    RS_TRY(tri_inv(Sm, n, n, Ui, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, Ui, n, true, h, n, false, 0.0, T, n, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, T, n, false, Ui, n, false, 0.0, h, n, st));
+    RS_TRY(symmetrize(h, n, n, st));
+    RS_TRY(eigh(h, n, n, eps_dev, Y, n, 2, status, ew, st));
+    RS_TRY(gemm_small(n, n, n, 1.0, Ui, n, false, Y, n, false, 0.0, C, n, st));
+    // the Ritz vectors and H applied to them (rotated in place), their FP64
+    // residual norms ||H x_k - eps_k x_k|| with <x_k|x_k> = 1
+    RS_TRY(rowmul<double>(P, n, n, C, n, n, P, n, S->npts, 1.0, 0.0, st));
+    RS_TRY(rowmul<double>(Q, n, n, C, n, n, Q, n, S->npts, 1.0, 0.0, st));
+    RS_CUDA(cudaMemsetAsync(res_dev, 0, sizeof(double) * n, st));
+    k_resid_norm2<<<dim3((unsigned)((n + 255) / 256), 512), 256, 0, st>>>(P, Q, n, n, eps_dev, S->npts, res_dev);
+    k_sqrt_scale<<<(n + 255) / 256, 256, 0, st>>>(res_dev, n, S->dV);
+    RS_LAUNCH_CHECK();
+    int info = 0;
+    RS_CUDA(cudaMemcpyAsync(&info, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    if (info) return fail(RS_ENOCONV, "rs_solver_certify: the dense eigensolver hit its sweep cap");
+    return RS_OK;
+}
+
 extern "C" int rs_solver_rayleigh_ritz_f64(rs_solver *S, double *eps_dev, void *stream) {
     if (!S || !eps_dev) return fail(RS_EINVAL, "rs_solver_rayleigh_ritz_f64: null argument");
     return rayleigh_ritz_f64_impl(S, eps_dev, (cudaStream_t)stream);

@@ -262,3 +262,35 @@ def test_solver_schedule_config_rejected_when_invalid():
     for bad in (dict(n_wanted=17), dict(stall_sweeps=2, stall_ratio=1.5), dict(rr64_every=-1)):
         with pytest.raises(RsError):
             api.Solver(H, psi0, 16, 1e-6, **bad)
+
+
+def certificate_bound(eps, res):
+    """Per-state eigenvalue error bound from FP64 Ritz values and residual
+    norms: r^2 / gap where the gap to the nearest other Ritz value exceeds r,
+    else r (an eigenvalue lies within r of every Ritz value)."""
+    e = np.asarray(eps)
+    gap = np.array([np.min(np.abs(np.delete(e, k) - e[k])) for k in range(len(e))])
+    r = np.asarray(res)
+    return np.where(gap > r, r * r / np.maximum(gap, 1e-300), r)
+
+
+def test_certificate_bounds_the_error_against_the_oracle():
+    """rs_solver_certify on the converged mixed solve of the 20-atom
+    molecule: its FP64 Ritz values agree with the oracle's eigenvalues to
+    1e-6 Ha, and its residual-norm bound covers the actual error of every
+    state (an honest certificate where no reference exists)."""
+    from paper_1306_2953_gb300 import api
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    ref = np.array(golden(w.name)["eigenvalues"])
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).float().cuda(), w.block, 1e-4,
+                   n_wanted=len(ref), **SCHEDULE)
+    _solve_to_golden(S, ref, 1e-6, 400)
+    eps, res = S.certify()
+    e, r = eps.cpu().numpy(), res.cpu().numpy()
+    err = np.abs(e[:len(ref)] - ref)
+    assert err.max() <= 1e-6
+    assert np.all(r > 0) and np.all(np.isfinite(r))
+    bound = certificate_bound(e, r)[:len(ref)]
+    assert np.all(err <= bound + 1e-12), (err.max(), bound.max())
