@@ -164,3 +164,141 @@ class BlockCG:
             if np.all(res[:judged] <= self.tol):
                 break
         return self.eps[:judged].copy()
+
+
+def diis_coefficients(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """The DIIS combination of RMM-DIIS (Kresse and Furthmueller 1996, after
+    Wood and Zunger 1985): the coefficients alpha that minimise the norm of
+    the combined residual sum_i alpha_i r_i relative to the norm of the
+    combined vector sum_i alpha_i x_i, i.e. the eigenvector of the lowest
+    eigenvalue of the generalized problem A alpha = mu B alpha with
+    A_ij = <r_i|r_j>, B_ij = <x_i|x_j>; normalised so that <xbar|xbar> = 1 and
+    signed so that sum_i alpha_i >= 0.  When the iterates are numerically
+    dependent (a Cholesky pivot of B below 1e-12 of its diagonal) the latest
+    iterate alone is kept."""
+    try:
+        U = _chol_checked(0.5 * (B + B.T))
+    except NotPositiveDefinite:
+        a = np.zeros(len(B))
+        a[-1] = 1.0
+        return a
+    Ui = tri_inv_upper(U)
+    C = Ui.T @ A @ Ui
+    w, V = jacobi_eigh(0.5 * (C + C.T))
+    a = Ui @ V[:, int(np.argmin(w))]
+    return a if a.sum() >= 0 else -a
+
+
+def rayleigh_step(xx, xp, pp, xhx, xhp, php) -> float:
+    """The lambda that minimises the Rayleigh quotient of x + lambda p: the
+    lower eigenvector (c0, c1) of the 2x2 pencil
+    [[<x|Hx>, <x|Hp>], [<x|Hp>, <p|Hp>]] c = mu [[<x|x>, <x|p>], [<x|p>, <p|p>]] c,
+    lambda = c1 / c0 (0 when the pencil is degenerate or c0 vanishes)."""
+    B = np.array([[xx, xp], [xp, pp]])
+    A = np.array([[xhx, xhp], [xhp, php]])
+    try:
+        U = _chol_checked(B)
+    except NotPositiveDefinite:
+        return 0.0
+    Ui = tri_inv_upper(U)
+    C = Ui.T @ A @ Ui
+    w, V = jacobi_eigh(0.5 * (C + C.T))
+    c = Ui @ V[:, int(np.argmin(w))]
+    return float(c[1] / c[0]) if c[0] != 0 else 0.0
+
+
+class RMMDIIS:
+    """RMM-DIIS, the eigensolver the paper uses (Sec. III, refs. Wood 1985,
+    Kresse 1996), with the filter preconditioner and the orthonormalisation
+    and subspace diagonalisation of Sec. VI after every sweep.  Every state
+    is refined on its own (block by block only for the bookkeeping of the
+    per-block convergence rule, Sec. VIII):
+
+      x_0 = psi, e_i = <x_i|H x_i>/<x_i|x_i>, r_i = H x_i - e_i x_i;
+      a block whose states all have ||r_0|| <= tol is left alone;
+      step 0: p = K r_0, the trial step lambda minimises the Rayleigh quotient of
+              x_0 + lambda p (the lower Ritz pair of span{x_0, p}),
+              x_1 = x_0 + lambda p;
+      steps m = 1 .. n_steps - 1: alpha = diis_coefficients over x_0..x_m,
+              xbar = sum alpha_i x_i, rbar = sum alpha_i r_i,
+              x_{m+1} = xbar + lambda K rbar (the same lambda);
+      psi <- x_{n_steps}.
+    H is applied once per step (H x_{m+1} = H xbar + lambda H p by linearity)."""
+
+    def __init__(self, ham: Hamiltonian, Psi0: np.ndarray, nb: int, precond=None, tol: float = 1e-9,
+                 n_steps: int = 3):
+        self.ham = ham
+        self.dV = ham.grid.dV
+        self.nb = nb
+        self.tol = tol
+        self.n_steps = n_steps
+        self.precond = precond if precond is not None else FilterPreconditioner(ham.grid)
+        nst = Psi0.shape[1]
+        assert nst % nb == 0 and n_steps >= 1
+        Psi, _ = orthonormalize(np.array(Psi0, dtype=np.float64), self.dV)
+        self.eps, self.Psi, self.HPsi, _ = subspace_diag(ham.apply, Psi, self.dV)
+        self.resnorm = np.full(nst, np.inf)
+        self.iterations = 0
+
+    def _dots(self, a, b):
+        return self.dV * np.sum(a * b, axis=0)
+
+    def _block(self, b: int):
+        sl = slice(b * self.nb, (b + 1) * self.nb)
+        x, hx = self.Psi[:, sl].copy(), self.HPsi[:, sl].copy()
+        e = self._dots(x, hx) / self._dots(x, x)
+        r = hx - x * e
+        res = np.sqrt(self._dots(r, r))
+        self.resnorm[sl] = res
+        if np.all(res <= self.tol):
+            return
+        xs, hxs, rs = [x], [hx], [r]
+        p = self.precond(r)
+        hp = self.ham.apply(p)
+        lam = np.zeros(x.shape[1])
+        for j in range(x.shape[1]):
+            if res[j] <= self.tol:
+                continue          # a converged state is not moved
+            lam[j] = rayleigh_step(self._dots(x[:, j], x[:, j]), self._dots(x[:, j], p[:, j]),
+                                   self._dots(p[:, j], p[:, j]), self._dots(x[:, j], hx[:, j]),
+                                   self._dots(x[:, j], hp[:, j]), self._dots(p[:, j], hp[:, j]))
+        for m in range(self.n_steps):
+            if m > 0:
+                k = len(xs)
+                alpha = np.empty((k, x.shape[1]))
+                for j in range(x.shape[1]):
+                    A = np.array([[self._dots(rs[i][:, j], rs[l][:, j]) for l in range(k)] for i in range(k)])
+                    B = np.array([[self._dots(xs[i][:, j], xs[l][:, j]) for l in range(k)] for i in range(k)])
+                    alpha[:, j] = diis_coefficients(A, B)
+                x = sum(alpha[i] * xs[i] for i in range(k))
+                hx = sum(alpha[i] * hxs[i] for i in range(k))
+                r = sum(alpha[i] * rs[i] for i in range(k))
+                p = self.precond(r)
+                hp = self.ham.apply(p)
+            x = x + lam * p
+            hx = hx + lam * hp
+            e = self._dots(x, hx) / self._dots(x, x)
+            xs.append(x)
+            hxs.append(hx)
+            rs.append(hx - x * e)
+        self.Psi[:, sl] = xs[-1]
+
+    def step(self):
+        """One sweep over all blocks, then orthonormalise + subspace
+        diagonalisation.  Returns (eps, resnorm, n_converged)."""
+        for b in range(self.Psi.shape[1] // self.nb):
+            self._block(b)
+        self.Psi, _ = orthonormalize(self.Psi, self.dV)
+        self.eps, self.Psi, self.HPsi, _ = subspace_diag(self.ham.apply, self.Psi, self.dV)
+        self.iterations += 1
+        return self.eps.copy(), self.resnorm.copy(), int(np.sum(self.resnorm <= self.tol))
+
+    def solve(self, max_iter: int = 1000, judged: int | None = None, callback=None):
+        judged = self.Psi.shape[1] if judged is None else judged
+        for _ in range(max_iter):
+            eps, res, nconv = self.step()
+            if callback is not None:
+                callback(self)
+            if np.all(res[:judged] <= self.tol):
+                break
+        return self.eps[:judged].copy()

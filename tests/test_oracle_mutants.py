@@ -146,8 +146,8 @@ MUTANTS = [
            "R = HX + X * lam",
            "tiny_molecule"),
     Mutant("block_stops_on_any_state", "eigensolver.py",
-           "if np.all(res <= self.tol):\n            return",
-           "if np.any(res <= self.tol):\n            return",
+           "self.resnorm[sl] = res\n        if np.all(res <= self.tol):\n            return\n        W = ",
+           "self.resnorm[sl] = res\n        if np.any(res <= self.tol):\n            return\n        W = ",
            "tiny_molecule"),
     Mutant("ritz_picks_highest", "eigensolver.py",
            "C = Ui @ Yv[:, :nb]",
@@ -207,6 +207,27 @@ MUTANTS = [
            "mh = self.m[i] / (1 - self.b1 ** self.t)",
            "mh = self.m[i]",
            "adam"),
+    # RMM-DIIS (the paper's eigensolver, Sec. III)
+    Mutant("rmm_trial_step_sign", "eigensolver.py",
+           "            x = x + lam * p",
+           "            x = x - lam * p",
+           "rmm"),
+    Mutant("diis_highest_eigenvector", "eigensolver.py",
+           "a = Ui @ V[:, int(np.argmin(w))]",
+           "a = Ui @ V[:, int(np.argmax(w))]",
+           "diis or rmm"),
+    Mutant("rayleigh_step_upper_pair", "eigensolver.py",
+           "c = Ui @ V[:, int(np.argmin(w))]",
+           "c = Ui @ V[:, int(np.argmax(w))]",
+           "rayleigh_trial or rmm"),
+    Mutant("rmm_residual_not_combined", "eigensolver.py",
+           "r = sum(alpha[i] * rs[i] for i in range(k))",
+           "r = rs[-1]",
+           "rmm"),
+    Mutant("rmm_hx_not_updated", "eigensolver.py",
+           "            hx = hx + lam * hp",
+           "            hx = hx + 0.0 * hp",
+           "rmm"),
     Mutant("adam_second_moment_uses_gradient", "precond.py",
            "self.v[i] = self.b2 * self.v[i] + (1 - self.b2) * g * g",
            "self.v[i] = self.b2 * self.v[i] + (1 - self.b2) * np.abs(g)",

@@ -518,3 +518,102 @@ def test_adam_alternating_gradient_closed_form():
         m = (1 - b1) * g * (-1.0) ** (t + 1) * (1 - (-b1) ** t) / (1 + b1)
         w = w - lr * (m / (1 - b1 ** t)) / (np.sqrt((1 - b2 ** t) * g * g / (1 - b2 ** t)) + eps)
         assert np.allclose(p[0], w, rtol=0, atol=1e-12), t
+
+
+# ---------------------------------------------------------------- RMM-DIIS ---
+
+def test_diis_coefficients_minimise_the_residual_quotient():
+    # The DIIS combination minimises <rbar|rbar> / <xbar|xbar> over the span
+    # of the iterates: its quotient is the lowest eigenvalue of the pencil
+    # (A, B) (the library's generalized symmetric eigensolver), normalised
+    # to <xbar|xbar> = 1 with a non-negative coefficient sum.
+    import scipy.linalg as sla
+    rng = np.random.default_rng(3)
+    for k in (2, 3, 4):
+        X = rng.standard_normal((50, k))
+        R = rng.standard_normal((50, k)) * np.array([1.0, 0.3, 0.1, 0.05][:k])
+        A, B = R.T @ R, X.T @ X
+        a = eigensolver.diis_coefficients(A, B)
+        lowest = sla.eigh(A, B, eigvals_only=True)[0]
+        assert abs(a @ A @ a / (a @ B @ a) - lowest) <= 1e-12 * max(1.0, abs(lowest))
+        assert abs(a @ B @ a - 1.0) <= 1e-12 and a.sum() >= 0
+        # no other combination does better
+        for _ in range(200):
+            c = rng.standard_normal(k)
+            assert c @ A @ c / (c @ B @ c) >= lowest - 1e-12
+
+
+def test_rayleigh_trial_step_minimises_the_quotient():
+    # lambda from the 2x2 pencil minimises the Rayleigh quotient of x + lambda p
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((30, 30))
+    Hm = M + M.T
+    for _ in range(5):
+        x, p = rng.standard_normal(30), rng.standard_normal(30)
+        hx, hp = Hm @ x, Hm @ p
+        lam = eigensolver.rayleigh_step(x @ x, x @ p, p @ p, x @ hx, x @ hp, p @ hp)
+        rq = lambda t: (x + t * p) @ Hm @ (x + t * p) / ((x + t * p) @ (x + t * p))
+        for d in (1e-3, -1e-3, 0.1, -0.1, 1.0, -1.0):
+            assert rq(lam) <= rq(lam + d) + 1e-12
+
+
+def test_harmonic_oscillator_rmm_diis():
+    # the paper's eigensolver on the separable oscillator (a 20^3 box with the
+    # same spacing, 16 states, lowest 10): the Kronecker-sum spectrum (P1)
+    n, h, om = 20, 0.3, 1.0
+    g = og.box_grid(n, h)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, om))
+    solver = eigensolver.RMMDIIS(H, wl.random_block(g.npts, 16, 5), 16, tol=1e-8)
+    eps = solver.solve(max_iter=300, judged=10)
+    e1, _ = one_d_levels(n, h, om)
+    expect = np.sort((e1[:, None, None] + e1[None, :, None] + e1[None, None, :]).ravel())[:10]
+    assert np.abs(eps - expect).max() < 1e-9
+
+
+def test_tiny_molecule_dense_vs_rmm_diis():
+    # P8 for the paper's eigensolver: dense diagonalisation of a tiny
+    # two-atom grid with projectors against RMM-DIIS
+    atoms = np.array([[0.0, 0.0, 0.0], [1.8, 0.0, 0.0]])
+    g = og.sphere_union_grid(atoms, 2.5, 0.6)
+    pr = oh.make_projectors(g, atoms, np.array([[1.0, 0.8], [1.5, 0.6]]), 1.0, 3.0)
+    H = oh.Hamiltonian(g, wl.local_potential(g.coords, atoms), pr)
+    ref = np.linalg.eigvalsh(H.dense())
+    solver = eigensolver.RMMDIIS(H, wl.random_block(g.npts, 8, 2), 4, tol=1e-9)
+    eps = solver.solve(max_iter=500)
+    assert np.abs(eps - ref[:8]).max() < 1e-9
+
+
+def test_rmm_diis_two_steps_against_brute_force():
+    # One state, identity preconditioner, two RMM-DIIS steps on a tiny
+    # oscillator box, rebuilt from the method's definition with brute-force
+    # one-dimensional minimisations instead of the oracle's 2x2 and DIIS
+    # eigenproblems: lambda minimises the Rayleigh quotient of x0 + t r0;
+    # alpha minimises |a0 r0 + a1 r1| / |a0 x0 + a1 x1| over directions
+    # (a0, a1) = (cos th, sin th); x2 = xbar + lambda rbar.
+    from scipy.optimize import minimize_scalar
+    g = og.box_grid(5, 0.5)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, 1.0))
+    Hd = H.dense()
+    dV = g.dV
+    x0 = wl.random_block(g.npts, 1, 8)[:, 0]
+    x0 = x0 / np.sqrt(dV * x0 @ x0)
+    dot = lambda a, b: dV * (a @ b)
+    rq = lambda v: dot(v, Hd @ v) / dot(v, v)
+    r0 = Hd @ x0 - rq(x0) * x0
+    ts = np.linspace(-20, 20, 40001)
+    t0 = ts[np.argmin([rq(x0 + t * r0) for t in ts])]
+    lam = minimize_scalar(lambda t: rq(x0 + t * r0), bracket=(t0 - 1e-3, t0, t0 + 1e-3), tol=1e-14).x
+    x1 = x0 + lam * r0
+    r1 = Hd @ x1 - rq(x1) * x1
+    quot = lambda th: (dot(np.cos(th) * r0 + np.sin(th) * r1, np.cos(th) * r0 + np.sin(th) * r1)
+                       / dot(np.cos(th) * x0 + np.sin(th) * x1, np.cos(th) * x0 + np.sin(th) * x1))
+    thg = np.linspace(0, np.pi, 20001)
+    th0 = thg[np.argmin([quot(t) for t in thg])]
+    th = minimize_scalar(quot, bracket=(th0 - 1e-3, th0, th0 + 1e-3), tol=1e-14).x
+    a0, a1 = np.cos(th), np.sin(th)
+    x2 = (a0 * x0 + a1 * x1) + lam * (a0 * r0 + a1 * r1)
+    solver = eigensolver.RMMDIIS(H, x0[:, None], 1, precond=lambda R: R.copy(), tol=0.0, n_steps=2)
+    solver.step()
+    got = solver.Psi[:, 0]
+    cosang = abs(dot(got, x2)) / np.sqrt(dot(got, got) * dot(x2, x2))
+    assert 1.0 - cosang < 1e-10
