@@ -315,10 +315,11 @@ def eigensolve_bench(workload, modes, max_seconds=600.0, tol=1e-6):
     for mode in modes:
         dt = torch.float64 if mode.startswith("f64") else torch.float32
         pc = _lib.RS_PRECOND_LEARNED if mode.endswith("learned") else _lib.RS_PRECOND_FILTER
+        method = _lib.RS_EIG_RMMDIIS if mode.endswith("_rmm") else _lib.RS_EIG_BLOCK_CG
         psi0_d = torch.from_numpy(psi0).to(dt).cuda()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S = api.Solver(H, psi0_d, workload.block, 1e-4, precond=pc, n_wanted=judged, **SCHEDULE)
+        S = api.Solver(H, psi0_d, workload.block, 1e-4, precond=pc, n_wanted=judged, method=method, **SCHEDULE)
         losses = None
         if mode.endswith("_cg"):
             # five CG iterations on (-1/2 Lap + 2) W = R (kept alive by S)
@@ -736,7 +737,8 @@ def main():
             line["cpu_baseline"]["single_thread"] = {"value": by / dt1 / 1e9, "unit": "GB/s", "cores": 1,
                                                      "seconds_per_block": dt1}
     if rank == 0 and world == 1 and args.eigensolve != "none":
-        line["eigensolve"] = [eigensolve_bench(wl.WORKLOADS[n], ["mixed_learned", "mixed_cg", "mixed_filter", "f64_filter"])
+        line["eigensolve"] = [eigensolve_bench(wl.WORKLOADS[n], ["mixed_learned", "mixed_cg", "mixed_filter", "mixed_rmm",
+                                                                 "f64_filter", "f64_rmm"])
                               for n in args.eigensolve.split(",")]
     if rank == 0:
         print(json.dumps(line))

@@ -311,13 +311,21 @@ int rs_subspace_diag(rs_ham *h, void *Psi_dev, void *HPsi_dev, int64_t ld, int n
                      double *eps_dev, double *xi_dev, void *work_dev, void *stream);
 
 /* --------------------------------------------------------------- solver --
- * Block conjugate-gradient eigensolver.  The paper's RMM-DIIS (Sec. III) is
- * replaced by LOBPCG swept block by block with a per-block convergence rule
+ * Block eigensolvers swept block by block with a per-block convergence rule
  * (a block stops only when all its states are converged, Sec. VIII) and
- * orthonormalisation + subspace diagonalisation after every sweep
- * (Sec. VI).  Precision RS_F64 runs everything in FP64; RS_F32 runs H psi
- * and the inner iterations in FP32 and keeps Cholesky, Rayleigh-Ritz,
- * residual norms and eigenvalues in FP64. */
+ * orthonormalisation + subspace diagonalisation after every sweep (Sec. VI):
+ *   RS_EIG_BLOCK_CG  LOBPCG (Knyazev 2001) on every block;
+ *   RS_EIG_RMMDIIS   the paper's RMM-DIIS (Sec. III; Wood and Zunger 1985,
+ *                    Kresse and Furthmueller 1996): every state refined on
+ *                    its own by a Rayleigh-quotient trial step along K r and
+ *                    rmm_steps - 1 DIIS steps that combine the iterates by
+ *                    the lowest pair of the pencil (<r_i|r_j>, <x_i|x_j>) and
+ *                    step by the same lambda along K of the combined
+ *                    residual; H applied rmm_steps times per state and sweep.
+ * Precision RS_F64 runs everything in FP64; RS_F32 runs H psi and the inner
+ * iterations in FP32 and keeps Cholesky, Rayleigh-Ritz, residual norms,
+ * dot products and eigenvalues in FP64. */
+enum { RS_EIG_BLOCK_CG = 0, RS_EIG_RMMDIIS = 1 };
 typedef struct {
     int nst;              /* states (a multiple of nb) */
     int nb;               /* block size: power of two, 1..64 */
@@ -341,6 +349,8 @@ typedef struct {
     int rr64_every;
     double rr64_below;
     double rr64_always;
+    int method;           /* RS_EIG_BLOCK_CG (0) or RS_EIG_RMMDIIS */
+    int rmm_steps;        /* RMM-DIIS steps per state and sweep, 1 .. 8 (0: 3) */
 } rs_solver_cfg;
 
 /* Creates a solver and allocates its device workspace (blocking).

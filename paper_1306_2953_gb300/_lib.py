@@ -18,6 +18,7 @@ RS_F64, RS_F32 = 0, 1
 RS_PRECOND_NONE, RS_PRECOND_FILTER, RS_PRECOND_LEARNED, RS_PRECOND_CG = 0, 1, 2, 3
 RS_ORDER_MORTON, RS_ORDER_TILECOL = -1, -2
 RS_KERNEL_AUTO, RS_KERNEL_GENERIC = 0, 1
+RS_EIG_BLOCK_CG, RS_EIG_RMMDIIS = 0, 1
 _NAMES = {RS_EINVAL: "RS_EINVAL", RS_ENOMEM: "RS_ENOMEM", RS_ECUDA: "RS_ECUDA", RS_ENOTSPD: "RS_ENOTSPD",
           RS_ENOCONV: "RS_ENOCONV", RS_ENAN: "RS_ENAN", RS_ETIMEOUT: "RS_ETIMEOUT"}
 
@@ -42,7 +43,8 @@ class SolverCfg(ctypes.Structure):
     _fields_ = [("nst", ctypes.c_int), ("nb", ctypes.c_int), ("dtype", ctypes.c_int), ("precond", ctypes.c_int),
                 ("tol", ctypes.c_double), ("filter_alpha", ctypes.c_double), ("n_wanted", ctypes.c_int),
                 ("stall_sweeps", ctypes.c_int), ("stall_ratio", ctypes.c_double), ("rr64_every", ctypes.c_int),
-                ("rr64_below", ctypes.c_double), ("rr64_always", ctypes.c_double)]
+                ("rr64_below", ctypes.c_double), ("rr64_always", ctypes.c_double), ("method", ctypes.c_int),
+                ("rmm_steps", ctypes.c_int)]
 
 
 class SolverStats(ctypes.Structure):

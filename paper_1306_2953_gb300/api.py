@@ -250,10 +250,11 @@ class Solver:
 
     def __init__(self, ham: Hamiltonian, Psi0, nb: int, tol: float, precond: int = _lib.RS_PRECOND_FILTER,
                  filter_alpha: float = 0.5, n_wanted: int = 0, stall_sweeps: int = 0, stall_ratio: float = 0.9,
-                 rr64_every: int = 0, rr64_below: float = 0.0, rr64_always: float = 0.0, stream=None):
+                 rr64_every: int = 0, rr64_below: float = 0.0, rr64_always: float = 0.0,
+                 method: int = _lib.RS_EIG_BLOCK_CG, rmm_steps: int = 0, stream=None):
         cfg = _lib.SolverCfg(Psi0.shape[1], nb, dtype_code(Psi0), precond, float(tol), float(filter_alpha),
                              int(n_wanted), int(stall_sweeps), float(stall_ratio), int(rr64_every), float(rr64_below),
-                             float(rr64_always))
+                             float(rr64_always), int(method), int(rmm_steps))
         assert Psi0.is_contiguous()
         out = ctypes.c_void_p()
         call("rs_solver_create", ham._h, ctypes.byref(cfg), _c(Psi0.data_ptr()), _stream(stream), ctypes.byref(out))

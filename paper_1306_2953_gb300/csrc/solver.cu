@@ -140,6 +140,244 @@ int coldots(int dtype, const void *A, int64_t lda, const void *B, int64_t ldb, i
     return RS_OK;
 }
 
+// ------------------------------------------------------------ RMM-DIIS ---
+// Column-wise kernels over [npts][nb] blocks (ld = nb) for the RMM-DIIS
+// refinement of every state (see rmm_block_step).
+
+constexpr int RMM_MAXK = 9;       // iterates kept per state (n_steps + 1 <= 9)
+constexpr int MD_MAX = 2 * RMM_MAXK;   // dot pairs of one k_multidot pass
+
+struct DotPairs {
+    const void *a[MD_MAX];
+    const void *b[MD_MAX];
+    int n;
+};
+
+// out[q * 64 + k] = sum_p a_q[p][k] b_q[p][k] for q < d.n, k < ncols (out
+// zeroed by the caller), accumulated to FP64-level accuracy as in k_coldots
+template <typename T>
+__global__ void __launch_bounds__(256) k_multidot(DotPairs d, int ncols, int64_t npts, double *out) {
+    __shared__ double red[256];
+    const int rows = blockDim.x / ncols;
+    const int k = threadIdx.x % ncols, r = threadIdx.x / ncols;
+    for (int q = 0; q < d.n; ++q) {
+        const T *A = (const T *)d.a[q], *B = (const T *)d.b[q];
+        double acc = 0.0;
+        if (r < rows) {
+            if constexpr (sizeof(T) == 4) {
+                float hi = 0.f, lo = 0.f;
+                for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+                    const float a = A[p * ncols + k], b = B[p * ncols + k];
+                    const float pr = __fmul_rn(a, b);
+                    const float pe = fmaf(a, b, -pr);
+                    const float sum = __fadd_rn(hi, pr);
+                    const float bb = __fsub_rn(sum, hi);
+                    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(pr, bb));
+                    hi = sum;
+                    lo = __fadd_rn(lo, __fadd_rn(err, pe));
+                }
+                acc = (double)hi + (double)lo;
+            } else {
+                double comp = 0.0;
+                for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+                    const double v = (double)A[p * ncols + k] * (double)B[p * ncols + k];
+                    const double y = v - comp;
+                    const double t = acc + y;
+                    comp = (t - acc) - y;
+                    acc = t;
+                }
+            }
+        }
+        red[threadIdx.x] = r < rows ? acc : 0.0;
+        __syncthreads();
+        if (r == 0) {
+            double s = 0;
+            for (int qq = 0; qq < rows; ++qq) s += red[qq * ncols + k];
+            atomicAdd(out + q * 64 + k, s);
+        }
+        __syncthreads();
+    }
+}
+
+// Lowest eigenpair of the symmetric pencil (A, B) of order n <= RMM_MAXK
+// (row-major n x n): B = U^T U (Cholesky; false when a pivot^2 falls below
+// 1e-12 of its diagonal), cyclic Jacobi on U^-T A U^-1, v = U^-1 y.
+__device__ bool small_pencil_lowest(int n, const double *A, const double *B, double *v) {
+    double U[RMM_MAXK][RMM_MAXK], Ui[RMM_MAXK][RMM_MAXK], C[RMM_MAXK][RMM_MAXK], V[RMM_MAXK][RMM_MAXK];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) U[i][j] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = 0.5 * (B[j * n + j] + B[j * n + j]);
+        for (int k = 0; k < j; ++k) d -= U[k][j] * U[k][j];
+        if (!(d > 1e-12 * B[j * n + j])) return false;
+        const double ujj = sqrt(d);
+        U[j][j] = ujj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = 0.5 * (B[j * n + i] + B[i * n + j]);
+            for (int k = 0; k < j; ++k) t -= U[k][j] * U[k][i];
+            U[j][i] = t / ujj;
+        }
+    }
+    for (int c = 0; c < n; ++c)
+        for (int i = n - 1; i >= 0; --i) {
+            double t = i == c ? 1.0 : 0.0;
+            for (int k = i + 1; k < n; ++k) t -= U[i][k] * Ui[k][c];
+            Ui[i][c] = i > c ? 0.0 : t / U[i][i];
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double t = 0;
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) t += Ui[a][i] * 0.5 * (A[a * n + b] + A[b * n + a]) * Ui[b][j];
+            C[i][j] = t;
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0, dia = 0;
+        for (int i = 0; i < n; ++i) {
+            dia += C[i][i] * C[i][i];
+            for (int j = i + 1; j < n; ++j) off += C[i][j] * C[i][j];
+        }
+        if (off <= 1e-32 * dia) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (C[p][q] == 0.0) continue;
+                const double th = (C[q][q] - C[p][p]) / (2.0 * C[p][q]);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double ckp = C[k][p], ckq = C[k][q];
+                    C[k][p] = c * ckp - s * ckq;
+                    C[k][q] = s * ckp + c * ckq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double cpk = C[p][k], cqk = C[q][k];
+                    C[p][k] = c * cpk - s * cqk;
+                    C[q][k] = s * cpk + c * cqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    int lo = 0;
+    for (int i = 1; i < n; ++i)
+        if (C[i][i] < C[lo][lo]) lo = i;
+    for (int i = 0; i < n; ++i) {
+        double t = 0;
+        for (int k = 0; k < n; ++k) t += Ui[i][k] * V[k][lo];
+        v[i] = t;
+    }
+    return true;
+}
+
+// Trial step of every column: lambda minimising the Rayleigh quotient of
+// x + lambda p, from the dots (xx, xp, pp, xhx, xhp, php) at rows q * 64;
+// 0 for columns whose residual norm is <= tol (converged states stay).
+__global__ void k_rmm_lambda(const double *dots, const double *res, double tol, int nb, double *lam) {
+    const int k = threadIdx.x;
+    if (k >= nb) return;
+    double l = 0.0;
+    if (res[k] > tol) {
+        const double B[4] = {dots[0 * 64 + k], dots[1 * 64 + k], dots[1 * 64 + k], dots[2 * 64 + k]};
+        const double A[4] = {dots[3 * 64 + k], dots[4 * 64 + k], dots[4 * 64 + k], dots[5 * 64 + k]};
+        double v[2];
+        if (small_pencil_lowest(2, A, B, v) && v[0] != 0.0) l = v[1] / v[0];
+    }
+    lam[k] = l;
+}
+
+// DIIS coefficients of every column over n iterates: the lowest pair of
+// (A, B), A_ij = <r_i|r_j>, B_ij = <x_i|x_j> (stored [i][j][64]), alpha
+// normalised to <xbar|xbar> = 1 and sum alpha >= 0; the latest iterate alone
+// when the iterates are numerically dependent.  alpha out [i][64].
+__global__ void k_rmm_diis(const double *A, const double *B, int n, int nb, double *alpha) {
+    const int k = threadIdx.x;
+    if (k >= nb) return;
+    double a[RMM_MAXK * RMM_MAXK], b[RMM_MAXK * RMM_MAXK], v[RMM_MAXK];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            a[i * n + j] = A[(i * RMM_MAXK + j) * 64 + k];
+            b[i * n + j] = B[(i * RMM_MAXK + j) * 64 + k];
+        }
+    if (small_pencil_lowest(n, a, b, v)) {
+        double s = 0;
+        for (int i = 0; i < n; ++i) s += v[i];
+        const double sg = s >= 0 ? 1.0 : -1.0;
+        for (int i = 0; i < n; ++i) alpha[i * 64 + k] = sg * v[i];
+    } else {
+        for (int i = 0; i < n; ++i) alpha[i * 64 + k] = i == n - 1 ? 1.0 : 0.0;
+    }
+}
+
+// xbar = sum_i alpha_i x_i, likewise H x and r, over n iterates stored at
+// hist + i * stride (x), + (slots + i) * stride (Hx), + (2 slots + i) * stride (r)
+template <typename T>
+__global__ void k_rmm_combine(const T *__restrict__ hist, int64_t stride, int slots, int n,
+                              const double *__restrict__ alpha, int nb, int64_t npts, T *__restrict__ xb,
+                              T *__restrict__ hxb, T *__restrict__ rb) {
+    const int rows = blockDim.x / nb, k = threadIdx.x % nb, r = threadIdx.x / nb;
+    if (r >= rows) return;
+    T al[RMM_MAXK];
+    for (int i = 0; i < RMM_MAXK; ++i) al[i] = i < n ? (T)alpha[i * 64 + k] : T(0);
+    for (int64_t p = blockIdx.x * (int64_t)rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+        const int64_t e = p * nb + k;
+        T x = 0, hx = 0, rr = 0;
+        for (int i = 0; i < n; ++i) {
+            x += al[i] * hist[i * stride + e];
+            hx += al[i] * hist[(slots + i) * stride + e];
+            rr += al[i] * hist[(2 * slots + i) * stride + e];
+        }
+        xb[e] = x;
+        hxb[e] = hx;
+        rb[e] = rr;
+    }
+}
+
+// x_out = x + lambda p, hx_out = hx + lambda hp (per-column lambda)
+template <typename T>
+__global__ void k_rmm_step(const T *__restrict__ x, const T *__restrict__ hx, const T *__restrict__ pp,
+                           const T *__restrict__ hp, const double *__restrict__ lam, int nb, int64_t npts,
+                           T *__restrict__ xo, T *__restrict__ hxo) {
+    const int rows = blockDim.x / nb, k = threadIdx.x % nb, r = threadIdx.x / nb;
+    if (r >= rows) return;
+    const T l = (T)lam[k];
+    for (int64_t p = blockIdx.x * (int64_t)rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+        const int64_t e = p * nb + k;
+        xo[e] = x[e] + l * pp[e];
+        hxo[e] = hx[e] + l * hp[e];
+    }
+}
+
+// A / B of the DIIS pencil from a k_multidot pass: pair q holds <r_i|r_j>
+// (kind 0) or <x_i|x_j> (kind 1) for (i, j) = idx[q]; stored symmetric.
+struct PairIndex {
+    int kind[MD_MAX], i[MD_MAX], j[MD_MAX], n;
+};
+__global__ void k_rmm_store(const double *dots, PairIndex t, int nb, double *A, double *B) {
+    const int k = threadIdx.x;
+    if (k >= nb) return;
+    for (int q = 0; q < t.n; ++q) {
+        double *M = t.kind[q] == 0 ? A : B;
+        const double v = dots[q * 64 + k];
+        M[(t.i[q] * RMM_MAXK + t.j[q]) * 64 + k] = v;
+        M[(t.j[q] * RMM_MAXK + t.i[q]) * 64 + k] = v;
+    }
+}
+
+int multidot(int dtype, const DotPairs &d, int ncols, int64_t npts, double *out, cudaStream_t st) {
+    RS_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 64 * d.n, st));
+    const int rows = 256 / ncols;
+    const unsigned blocks = (unsigned)std::min<int64_t>((npts + rows - 1) / rows, 152 * 8);
+    if (dtype == RS_F64) k_multidot<double><<<blocks, 256, 0, st>>>(d, ncols, npts, out);
+    else k_multidot<float><<<blocks, 256, 0, st>>>(d, ncols, npts, out);
+    RS_LAUNCH_CHECK();
+    return RS_OK;
+}
+
 }  // namespace rs
 
 struct rs_solver {
@@ -162,6 +400,10 @@ struct rs_solver {
     double best = std::numeric_limits<double>::infinity(), max_res = 0;
     double train_target_s = 0, train_fit_s = 0;
     DevBuf eps64;   // FP64 Rayleigh-Ritz eigenvalues when the caller passes no eps_dev
+    // RMM-DIIS: iterates x_i, H x_i, r_i ([slot][npts][nb] each kind), p, H p,
+    // the combinations, and the small per-column arrays
+    DevBuf rmm_hist, rmm_small;
+    int rmm_M = 3;
     // small FP64 buffers (inside `small`)
     double *dots = nullptr, *M = nullptr, *G = nullptr, *A = nullptr, *U = nullptr, *Ui = nullptr, *T1 = nullptr,
            *At = nullptr, *Yv = nullptr, *mu = nullptr, *C = nullptr;
@@ -319,6 +561,119 @@ int block_step(rs_solver *S, int b, cudaStream_t st) {
     return RS_OK;
 }
 
+// One RMM-DIIS refinement of block b (the paper's eigensolver, Sec. III:
+// Wood and Zunger 1985, Kresse and Furthmueller 1996), every state on its own:
+//   x_0 = psi, e_i = <x_i|H x_i>/<x_i|x_i>, r_i = H x_i - e_i x_i; a block whose
+//   states all have ||r_0|| <= tol is left alone (Sec. VIII);
+//   p = K r_0, lambda minimises the Rayleigh quotient of x_0 + lambda p,
+//   x_1 = x_0 + lambda p;
+//   then n_steps - 1 DIIS steps: alpha = the lowest pair of the pencil
+//   (<r_i|r_j>, <x_i|x_j>), xbar = sum alpha_i x_i, rbar = sum alpha_i r_i,
+//   x_{m+1} = xbar + lambda K rbar;  psi <- x_{n_steps}.
+// H is applied once per step (H x_{m+1} = H xbar + lambda H p).  Blocking
+// (reads the block's residuals).
+int rmm_block_step(rs_solver *S, int b, cudaStream_t st) {
+    const rs_solver_cfg &c = S->cfg;
+    const int nb = c.nb, nst = c.nst, dt = c.dtype, es = S->es, M = S->rmm_M, slots = M + 1;
+    const int64_t np = S->npts, sz = np * nb;
+    char *hist = (char *)S->rmm_hist.p;
+    auto X = [&](int i) { return (void *)(hist + (size_t)i * sz * es); };
+    auto HX = [&](int i) { return (void *)(hist + (size_t)(slots + i) * sz * es); };
+    auto R = [&](int i) { return (void *)(hist + (size_t)(2 * slots + i) * sz * es); };
+    void *P = hist + (size_t)(3 * slots) * sz * es, *HP = hist + (size_t)(3 * slots + 1) * sz * es;
+    void *XB = hist + (size_t)(3 * slots + 2) * sz * es, *HXB = hist + (size_t)(3 * slots + 3) * sz * es;
+    void *RB = hist + (size_t)(3 * slots + 4) * sz * es;
+    double *dots = S->rmm_small.as<double>();            // [MD_MAX][64]
+    double *A = dots + MD_MAX * 64, *B = A + RMM_MAXK * RMM_MAXK * 64;
+    double *alpha = B + RMM_MAXK * RMM_MAXK * 64, *lam = alpha + RMM_MAXK * 64;
+    double *rr = lam + 64;
+    const unsigned eb = elem_blocks(np, nb);
+    auto residual = [&](int i) -> int {   // e_i and r_i of iterate i
+        DotPairs d{};
+        d.a[0] = X(i), d.b[0] = HX(i), d.a[1] = X(i), d.b[1] = X(i), d.n = 2;
+        RS_TRY(multidot(dt, d, nb, np, dots, st));
+        if (dt == RS_F64)
+            k_residual<double><<<eb, 256, 0, st>>>((const double *)X(i), nb, (const double *)HX(i), nb, dots, dots + 64,
+                                                   (double *)R(i), nb, nb, np);
+        else
+            k_residual<float><<<eb, 256, 0, st>>>((const float *)X(i), nb, (const float *)HX(i), nb, dots, dots + 64,
+                                                  (float *)R(i), nb, nb, np);
+        RS_LAUNCH_CHECK();
+        return RS_OK;
+    };
+    RS_TRY(copy_cols(dt, off(S->psi, (int64_t)b * nb, es), nst, X(0), nb, nb, np, st));
+    RS_TRY(copy_cols(dt, off(S->hpsi, (int64_t)b * nb, es), nst, HX(0), nb, nb, np, st));
+    RS_TRY(residual(0));
+    RS_TRY(coldots(dt, R(0), nb, R(0), nb, nb, np, rr, st));
+    double *resb = S->res.as<double>() + (size_t)b * nb;
+    k_resnorm<<<1, 64, 0, st>>>(rr, nb, S->dV, resb);
+    RS_LAUNCH_CHECK();
+    std::vector<double> res(nb);
+    RS_CUDA(cudaMemcpyAsync(res.data(), resb, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    int ringerr = 0;
+    if (int *rw = ham_status_word(S->h)) RS_CUDA(cudaMemcpyAsync(&ringerr, rw, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    if (ringerr) return fail(RS_ETIMEOUT, "eigensolver: an H psi pipeline wait timed out");
+    bool conv = true;
+    for (double r : res) {
+        if (!std::isfinite(r)) return fail(RS_ENAN, "eigensolver: non-finite residual in block %d", b);
+        conv = conv && r <= c.tol;
+    }
+    if (conv) return RS_OK;
+    // step 0: the Rayleigh-quotient trial step along p = K r_0
+    RS_TRY(S->pc->apply(S->h, R(0), nb, P, nb, nb, dt, st));
+    RS_TRY(rs_ham_apply_block(S->h, P, nb, HP, nb, nb, dt, st));
+    {
+        DotPairs d{};
+        const void *a[6] = {X(0), X(0), P, X(0), X(0), P}, *bb[6] = {X(0), P, P, HX(0), HP, HP};
+        for (int q = 0; q < 6; ++q) d.a[q] = a[q], d.b[q] = bb[q];
+        d.n = 6;
+        RS_TRY(multidot(dt, d, nb, np, dots, st));
+        k_rmm_lambda<<<1, 64, 0, st>>>(dots, resb, c.tol, nb, lam);
+        RS_LAUNCH_CHECK();
+    }
+    auto advance = [&](const void *x, const void *hx, int to) -> int {
+        if (dt == RS_F64)
+            k_rmm_step<double><<<eb, 256, 0, st>>>((const double *)x, (const double *)hx, (const double *)P,
+                                                   (const double *)HP, lam, nb, np, (double *)X(to), (double *)HX(to));
+        else
+            k_rmm_step<float><<<eb, 256, 0, st>>>((const float *)x, (const float *)hx, (const float *)P,
+                                                  (const float *)HP, lam, nb, np, (float *)X(to), (float *)HX(to));
+        RS_LAUNCH_CHECK();
+        return RS_OK;
+    };
+    RS_TRY(advance(X(0), HX(0), 1));
+    for (int m = 1; m < M; ++m) {
+        RS_TRY(residual(m));
+        // column m of the DIIS pencil (and column 0 at the first DIIS step)
+        DotPairs d{};
+        PairIndex t{};
+        for (int col = (m == 1 ? 0 : m); col <= m; ++col)
+            for (int i = 0; i <= col; ++i)
+                for (int kind = 0; kind < 2; ++kind) {
+                    d.a[d.n] = kind == 0 ? R(i) : X(i);
+                    d.b[d.n] = kind == 0 ? R(col) : X(col);
+                    t.kind[t.n] = kind, t.i[t.n] = i, t.j[t.n] = col;
+                    ++d.n, ++t.n;
+                }
+        RS_TRY(multidot(dt, d, nb, np, dots, st));
+        k_rmm_store<<<1, 64, 0, st>>>(dots, t, nb, A, B);
+        k_rmm_diis<<<1, 64, 0, st>>>(A, B, m + 1, nb, alpha);
+        RS_LAUNCH_CHECK();
+        if (dt == RS_F64)
+            k_rmm_combine<double><<<eb, 256, 0, st>>>((const double *)hist, sz, slots, m + 1, alpha, nb, np,
+                                                      (double *)XB, (double *)HXB, (double *)RB);
+        else
+            k_rmm_combine<float><<<eb, 256, 0, st>>>((const float *)hist, sz, slots, m + 1, alpha, nb, np,
+                                                     (float *)XB, (float *)HXB, (float *)RB);
+        RS_LAUNCH_CHECK();
+        RS_TRY(S->pc->apply(S->h, RB, nb, P, nb, nb, dt, st));
+        RS_TRY(rs_ham_apply_block(S->h, P, nb, HP, nb, nb, dt, st));
+        RS_TRY(advance(XB, HXB, m + 1));
+    }
+    return copy_cols(dt, X(M), nb, offw(S->psi, (int64_t)b * nb, es), nst, nb, np, st);
+}
+
 }  // namespace
 
 __global__ void k_widen(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
@@ -464,6 +819,9 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
         return fail(RS_EINVAL, "rs_solver_create: stall_sweeps must be >= 0 and stall_ratio in (0, 1]");
     if (c.rr64_every < 0 || !(c.rr64_below >= 0) || !(c.rr64_always >= 0))
         return fail(RS_EINVAL, "rs_solver_create: bad FP64 Rayleigh-Ritz schedule");
+    if (c.method != RS_EIG_BLOCK_CG && c.method != RS_EIG_RMMDIIS) return fail(RS_EINVAL, "rs_solver_create: bad method");
+    if (c.rmm_steps < 0 || c.rmm_steps > RMM_MAXK - 1)
+        return fail(RS_EINVAL, "rs_solver_create: rmm_steps must be in 0 .. %d", RMM_MAXK - 1);
     *out = nullptr;
     rs_solver *S = new (std::nothrow) rs_solver;
     if (!S) return fail(RS_ENOMEM, "host allocation failed");
@@ -479,11 +837,18 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
     S->nblk = c.nst / c.nb;
     S->has_p.assign(S->nblk, 0);
     const size_t big = (size_t)S->npts * c.nst * S->es, zb = (size_t)S->npts * 3 * c.nb * S->es;
+    const bool rmm = c.method == RS_EIG_RMMDIIS;
+    S->rmm_M = c.rmm_steps > 0 ? c.rmm_steps : 3;
     int rc;
-    if ((rc = S->psi.alloc(big)) || (rc = S->hpsi.alloc(big)) || (rc = S->P.alloc(big)) || (rc = S->Z.alloc(zb)) ||
-        (rc = S->HZ.alloc(zb)) || (rc = S->R.alloc((size_t)S->npts * c.nb * S->es)) ||
+    if ((rc = S->psi.alloc(big)) || (rc = S->hpsi.alloc(big)) ||
         (rc = S->la.alloc(LaWork::bytes(c.nst))) || (rc = S->eig.alloc(sizeof(double) * c.nst)) ||
         (rc = S->res.alloc(sizeof(double) * c.nst)))
+        return bail(rc);
+    if (!rmm && ((rc = S->P.alloc(big)) || (rc = S->Z.alloc(zb)) || (rc = S->HZ.alloc(zb)) ||
+                 (rc = S->R.alloc((size_t)S->npts * c.nb * S->es))))
+        return bail(rc);
+    if (rmm && ((rc = S->rmm_hist.alloc((size_t)(3 * (S->rmm_M + 1) + 5) * S->npts * c.nb * S->es)) ||
+                (rc = S->rmm_small.alloc(sizeof(double) * 64 * (MD_MAX + 2 * RMM_MAXK * RMM_MAXK + RMM_MAXK + 2)))))
         return bail(rc);
     if (c.dtype == RS_F32) {
         const int64_t need = std::max({umma_work_bytes(c.nst, 2 * c.nb, S->npts), umma_work_bytes(S->npts, c.nst, c.nst),
@@ -523,7 +888,8 @@ extern "C" int rs_solver_create(rs_ham *h, const rs_solver_cfg *cfg, const void 
     if (!S->pc) return bail(fail(RS_EINVAL, "rs_solver_create: preconditioner %d unavailable", c.precond));
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(S->psi.p, Psi0_dev, big, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(S->P.p, 0, big, st) != cudaSuccess || cudaMemsetAsync(S->res.p, 0, sizeof(double) * c.nst, st) != cudaSuccess)
+        (S->P.p && cudaMemsetAsync(S->P.p, 0, big, st) != cudaSuccess) ||
+        cudaMemsetAsync(S->res.p, 0, sizeof(double) * c.nst, st) != cudaSuccess)
         return bail(fail(RS_ECUDA, "rs_solver_create: copy failed"));
     if ((rc = orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st, S->tc))) return bail(rc);
     if ((rc = subspace_diag_impl(h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st,
@@ -538,13 +904,14 @@ extern "C" int rs_eigensolver_step(rs_solver *S, double *eps_dev, double *resnor
     if (!S) return fail(RS_EINVAL, "rs_eigensolver_step: null solver");
     cudaStream_t st = (cudaStream_t)stream;
     const rs_solver_cfg &c = S->cfg;
-    for (int b = 0; b < S->nblk; ++b) RS_TRY(block_step(S, b, st));
+    const bool rmm = c.method == RS_EIG_RMMDIIS;
+    for (int b = 0; b < S->nblk; ++b) RS_TRY(rmm ? rmm_block_step(S, b, st) : block_step(S, b, st));
     RS_TRY(orthonormalize_impl(S->npts, S->dV, S->psi.p, c.nst, c.nst, c.dtype, S->la.p, st, S->tc));
     LaWork w(S->la.p, c.nst);
-    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.Ui, S->npts, c.dtype, st, S->tc));
+    if (!rmm) RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.Ui, S->npts, c.dtype, st, S->tc));
     RS_TRY(subspace_diag_impl(S->h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st,
                               S->tc));
-    RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.xi, S->npts, c.dtype, st, S->tc));
+    if (!rmm) RS_TRY(rotate_inplace(S->P.p, c.nst, c.nst, w.xi, S->npts, c.dtype, st, S->tc));
     if (eps_dev) RS_CUDA(cudaMemcpyAsync(eps_dev, S->eig.p, sizeof(double) * c.nst, cudaMemcpyDeviceToDevice, st));
     if (resnorm_dev) RS_CUDA(cudaMemcpyAsync(resnorm_dev, S->res.p, sizeof(double) * c.nst, cudaMemcpyDeviceToDevice, st));
     std::vector<double> res(c.nst);
