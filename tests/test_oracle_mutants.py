@@ -207,6 +207,23 @@ MUTANTS = [
            "mh = self.m[i] / (1 - self.b1 ** self.t)",
            "mh = self.m[i]",
            "adam"),
+    # Hartree potential by FFT (Sec. X)
+    Mutant("poisson_periodic_kernel", "poisson.py",
+           "v = 4.0 * np.pi * (1.0 - np.cos(G * Rc)) / G2",
+           "v = 4.0 * np.pi / G2",
+           "hartree"),
+    Mutant("poisson_g0_dropped", "poisson.py",
+           "v[0, 0, 0] = 2.0 * np.pi * Rc * Rc",
+           "v[0, 0, 0] = 0.0",
+           "hartree"),
+    Mutant("poisson_cube_too_small", "poisson.py",
+           "int(ext[a]) + int(math.ceil(Rc / grid.h)) + 1",
+           "int(ext[a]) + int(math.ceil(0.5 * Rc / grid.h)) + 1",
+           "hartree"),
+    Mutant("poisson_frequency_scale", "poisson.py",
+           "g = [2.0 * np.pi * np.fft.fftfreq(n, d=h) for n in shape]",
+           "g = [np.pi * np.fft.fftfreq(n, d=h) for n in shape]",
+           "hartree"),
     # RMM-DIIS (the paper's eigensolver, Sec. III)
     Mutant("rmm_trial_step_sign", "eigensolver.py",
            "            x = x + lam * p",

@@ -617,3 +617,51 @@ def test_rmm_diis_two_steps_against_brute_force():
     got = solver.Psi[:, 0]
     cosang = abs(dot(got, x2)) / np.sqrt(dot(got, got) * dot(x2, x2))
     assert 1.0 - cosang < 1e-10
+
+
+# -------------------------------------------------------- Hartree (FFT) ---
+
+def _gaussian_box(sigma, h, half):
+    n = int(round(2 * half / h)) + 1
+    g = og.box_grid(n, h)
+    r = np.linalg.norm(g.coords, axis=1)
+    rho = np.exp(-r * r / (2 * sigma * sigma)) / (2 * np.pi * sigma * sigma) ** 1.5
+    return g, r, rho
+
+
+def test_hartree_gaussian_closed_form():
+    # a normalised Gaussian charge of width sigma has the potential
+    # erf(r / (sqrt(2) sigma)) / r (sqrt(2/pi) / sigma at r = 0)
+    from scipy.special import erf
+    from oracle import poisson as op
+    sigma, h = 1.0, 0.25
+    g, r, rho = _gaussian_box(sigma, h, 6.5)
+    V = op.hartree(g, rho)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ref = np.where(r > 0, erf(r / (np.sqrt(2) * sigma)) / r, np.sqrt(2 / np.pi) / sigma)
+    assert np.abs(V - ref).max() <= 1e-9 * ref.max()
+
+
+def test_hartree_two_charges_and_symmetry():
+    # two Gaussians of opposite sign at +-a along an axis: the potential is
+    # the sum of the two closed forms, odd under the mirror x -> -x
+    from scipy.special import erf
+    from oracle import poisson as op
+    sigma, h, a = 0.8, 0.25, 1.5
+    n = 53
+    g = og.box_grid(n, h)
+    x = g.coords
+    rp = np.linalg.norm(x - np.array([a, 0, 0]), axis=1)
+    rm = np.linalg.norm(x + np.array([a, 0, 0]), axis=1)
+    gau = lambda r: np.exp(-r * r / (2 * sigma * sigma)) / (2 * np.pi * sigma * sigma) ** 1.5
+    V = op.hartree(g, gau(rp) - gau(rm))
+    pot = lambda r: np.where(r > 0, erf(r / (np.sqrt(2) * sigma)) / np.where(r > 0, r, 1), np.sqrt(2 / np.pi) / sigma)
+    ref = pot(rp) - pot(rm)
+    assert np.abs(V - ref).max() <= 1e-7
+    mirror = g.lookup(g.ijk * np.array([-1, 1, 1]) + np.array([n - 1, 0, 0]))
+    assert np.abs(V + V[mirror]).max() <= 1e-10
+
+
+def test_smooth_sizes():
+    from oracle import poisson as op
+    assert [op.smooth_size(n) for n in (1, 5, 7, 10, 17, 100, 289)] == [1, 6, 8, 12, 18, 108, 324]
