@@ -536,6 +536,34 @@ int rs_solver_set_precond_cg(rs_solver *s, rs_ham *shifted, int n_iter);
 
 int rs_solver_destroy(rs_solver *s);
 
+/* -------------------------------------------------------------- Hartree --
+ * The Hartree potential by FFT (Sec. X; Eq. 2, lap V_H = -4 pi n): the
+ * density is copied from the grid to a cube, Fourier transformed, multiplied
+ * by the Coulomb-interaction kernel, transformed back and copied to the grid.
+ * Free boundary conditions from an enlarged cube and the spherical-cutoff
+ * kernel of Rozzi et al. (2006): v(G) = 4 pi (1 - cos(|G| R_c)) / |G|^2,
+ * v(0) = 2 pi R_c^2, with R_c = D + h (D: the diagonal of the grid's
+ * bounding box) and N_a cube points along axis a, the smallest 2^p 3^q
+ * >= extent_a + ceil(R_c / h) + 1 (the radices of the paper's GPU FFT), so
+ * that the periodic convolution equals the free-space one on the grid.
+ * The transforms are the library's own complex FP64 Stockham kernels. */
+typedef struct rs_poisson rs_poisson;
+
+/* Plans the cube for grid g and allocates it on the current device
+ * (blocking).  Errors: RS_EINVAL (empty grid, an axis above 768 points),
+ * RS_ENOMEM. */
+int rs_poisson_create(const rs_grid *g, rs_poisson **out);
+
+/* Cube shape, the cutoff radius R_c (Bohr) and the cube's bytes. */
+int rs_poisson_info(const rs_poisson *p, int32_t shape[3], double *r_cut, int64_t *cube_bytes);
+
+/* vh_dev = V_H for the density n_dev (device double [npts] in grid order,
+ * electrons per Bohr^3); vh_dev in Hartree.  Calls on one handle share its
+ * cube: issue them on one stream.  Asynchronous. */
+int rs_poisson_solve(rs_poisson *p, const double *n_dev, double *vh_dev, void *stream);
+
+int rs_poisson_destroy(rs_poisson *p);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,6 +117,10 @@ SIGNATURES = {
     "rs_precond_save": (None, [P, ctypes.c_char_p]),
     "rs_precond_load": (None, [P, ctypes.c_char_p]),
     "rs_solver_destroy": (None, [P]),
+    "rs_poisson_create": (None, [P, PP]),
+    "rs_poisson_info": (None, [P, P, P, P]),
+    "rs_poisson_solve": (None, [P, P, P, P]),
+    "rs_poisson_destroy": (None, [P]),
 }
 
 _lock = threading.Lock()

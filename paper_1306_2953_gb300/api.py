@@ -466,3 +466,39 @@ def eigh(A, refine: int = 2, stream=None):
     A = A.contiguous()
     call("rs_eigh", _c(A.data_ptr()), n, _c(w.data_ptr()), _c(V.data_ptr()), refine, _c(work.data_ptr()), _stream(stream))
     return w, V
+
+
+class Poisson:
+    """FFT Hartree solver on a grid (rs_poisson_*)."""
+
+    def __init__(self, grid: Grid):
+        out = ctypes.c_void_p()
+        call("rs_poisson_create", grid._h, ctypes.byref(out))
+        self._h = out
+        self.grid = grid
+
+    def info(self):
+        shape = (ctypes.c_int32 * 3)()
+        rc = ctypes.c_double()
+        nbytes = ctypes.c_int64()
+        call("rs_poisson_info", self._h, shape, ctypes.byref(rc), ctypes.byref(nbytes))
+        return tuple(shape), rc.value, nbytes.value
+
+    def solve(self, n, vh=None, stream=None):
+        """V_H for the density n (FP64 device tensor [npts]); returns vh."""
+        import torch
+        vh = torch.empty_like(n) if vh is None else vh
+        assert n.dtype == torch.float64 and n.is_contiguous()
+        call("rs_poisson_solve", self._h, _c(n.data_ptr()), _c(vh.data_ptr()), _stream(stream))
+        return vh
+
+    def close(self):
+        if self._h:
+            _lib.lib().rs_poisson_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
