@@ -142,6 +142,13 @@ class BlockCG:
         self.Psi[:, sl] = Zc @ C
         self.P[:, sl] = Zc[:, nb:] @ C[nb:, :]
 
+    def set_potential(self, v: np.ndarray):
+        """New local potential of the Hamiltonian (an SCF step): the subspace
+        is rediagonalised with it and the search directions are dropped."""
+        self.ham.V = np.ascontiguousarray(v, dtype=np.float64)
+        self.eps, self.Psi, self.HPsi, _ = subspace_diag(self.ham.apply, self.Psi, self.dV)
+        self.P[:] = 0.0
+
     def step(self):
         """One sweep over all blocks, then orthonormalise + subspace
         diagonalisation.  Returns (eps, resnorm, n_converged)."""
@@ -282,6 +289,12 @@ class RMMDIIS:
             hxs.append(hx)
             rs.append(hx - x * e)
         self.Psi[:, sl] = xs[-1]
+
+    def set_potential(self, v: np.ndarray):
+        """New local potential of the Hamiltonian (an SCF step): the subspace
+        is rediagonalised with it."""
+        self.ham.V = np.ascontiguousarray(v, dtype=np.float64)
+        self.eps, self.Psi, self.HPsi, _ = subspace_diag(self.ham.apply, self.Psi, self.dV)
 
     def step(self):
         """One sweep over all blocks, then orthonormalise + subspace

@@ -224,6 +224,35 @@ MUTANTS = [
            "g = [2.0 * np.pi * np.fft.fftfreq(n, d=h) for n in shape]",
            "g = [np.pi * np.fft.fftfreq(n, d=h) for n in shape]",
            "hartree"),
+    # SCF: LDA, occupations, density, Broyden mixing (Sec. III)
+    Mutant("lda_exchange_potential_factor", "scf.py",
+           "vx = 4.0 / 3.0 * ex",
+           "vx = ex",
+           "lda"),
+    Mutant("pz_low_density_potential", "scf.py",
+           "7.0 / 6.0 * PZ_B1",
+           "6.0 / 7.0 * PZ_B1",
+           "lda"),
+    Mutant("pz_high_density_potential", "scf.py",
+           "(PZ_B - PZ_A / 3.0)",
+           "(PZ_B + PZ_A / 3.0)",
+           "lda"),
+    Mutant("broyden_correction_sign", "scf.py",
+           "out = out - t * (dn + self.alpha * dF)",
+           "out = out + t * (dn + self.alpha * dF)",
+           "broyden"),
+    Mutant("fermi_bisection_direction", "scf.py",
+           "if fd(mid).sum() < n_electrons:",
+           "if fd(mid).sum() > n_electrons:",
+           "fermi"),
+    Mutant("density_ignores_occupations", "scf.py",
+           "return np.sum(Psi ** 2 * f[None, :], axis=1)",
+           "return 2.0 * np.sum(Psi ** 2, axis=1)",
+           "scf_fixed_point"),
+    Mutant("scf_hartree_sign", "scf.py",
+           "return self.v_ext + vh + vxc, vh, exc, vxc",
+           "return self.v_ext - vh + vxc, vh, exc, vxc",
+           "scf_fixed_point"),
     # RMM-DIIS (the paper's eigensolver, Sec. III)
     Mutant("rmm_trial_step_sign", "eigensolver.py",
            "            x = x + lam * p",

@@ -665,3 +665,102 @@ def test_hartree_two_charges_and_symmetry():
 def test_smooth_sizes():
     from oracle import poisson as op
     assert [op.smooth_size(n) for n in (1, 5, 7, 10, 17, 100, 289)] == [1, 6, 8, 12, 18, 108, 324]
+
+
+# ------------------------------------------------------ SCF, LDA, mixing ---
+
+def test_lda_potential_is_the_density_derivative():
+    # v_xc = d(n e_xc)/dn, by central differences, on both branches of the
+    # Perdew-Zunger correlation (r_s above and below 1)
+    from oracle import scf as osc
+    n = np.geomspace(1e-4, 20.0, 400)
+    d = 1e-6 * n
+    exc_p, _ = osc.lda_xc(n + d)
+    exc_m, _ = osc.lda_xc(n - d)
+    fd = ((n + d) * exc_p - (n - d) * exc_m) / (2 * d)
+    _, vxc = osc.lda_xc(n)
+    assert np.abs(fd - vxc).max() <= 1e-6 * np.abs(vxc).max()
+
+
+def test_lda_exchange_and_correlation_limits():
+    from oracle import scf as osc
+    # Slater exchange of the uniform gas: e_x r_s = -(3/4)(9/(4 pi^2))^(1/3)
+    rs = np.array([0.5, 1.0, 2.0, 5.0])
+    n = 3.0 / (4.0 * np.pi * rs ** 3)
+    exc, _ = osc.lda_xc(n)
+    ex = exc - _pz_ec(rs)
+    assert np.allclose(ex * rs, -0.75 * (9.0 / (4.0 * np.pi ** 2)) ** (1.0 / 3.0), rtol=1e-12, atol=0)
+    # the two Perdew-Zunger branches meet at r_s = 1 (value and slope)
+    e1, e2 = osc.lda_xc(np.array([3.0 / (4.0 * np.pi) * (1 - 1e-9) ** -3, 3.0 / (4.0 * np.pi) * (1 + 1e-9) ** -3]))[0]
+    assert abs(e1 - e2) < 5e-5
+    assert np.all(osc.lda_xc(np.array([0.0, -1.0]))[0] == 0.0)
+
+
+def _pz_ec(rs):
+    # the published Perdew-Zunger 1981 fit of the Ceperley-Alder correlation
+    # energy (unpolarised), written out independently for the exchange check
+    return np.where(rs >= 1, -0.1423 / (1 + 1.0529 * np.sqrt(rs) + 0.3334 * rs),
+                    0.0311 * np.log(rs) - 0.048 + 0.0020 * rs * np.log(rs) - 0.0116 * rs)
+
+
+def test_broyden_mixing_solves_a_linear_fixed_point():
+    # F(n) = b - A n (A symmetric positive definite, dimension 6): Broyden's
+    # second method in Anderson form terminates like GMRES, within d + 2 steps
+    from oracle import scf as osc
+    rng = np.random.default_rng(7)
+    M = rng.standard_normal((6, 6))
+    A = M @ M.T / 6 + 0.5 * np.eye(6)
+    b = rng.standard_normal(6)
+    exact = np.linalg.solve(A, b)
+    mix = osc.Broyden(alpha=0.3, history=10)
+    n = np.zeros(6)
+    first = mix.mix(n, b - A @ n)
+    assert np.allclose(first, n + 0.3 * b, rtol=0, atol=1e-15)
+    n = first
+    for _ in range(8):
+        n = mix.mix(n, b - A @ n)
+    assert np.abs(n - exact).max() <= 1e-9 * np.abs(exact).max()
+
+
+def test_fermi_occupations():
+    from oracle import scf as osc
+    eps = np.array([-1.0, -0.5, 0.1, 0.1, 0.4, 0.9])
+    f, mu = osc.occupations(eps, 6.0, 0.01)
+    assert abs(f.sum() - 6.0) < 1e-12 and np.all(np.diff(f) <= 1e-15) and f.max() <= 2.0
+    assert abs(f[2] - f[3]) < 1e-15 and abs(f[2] - 1.0) < 1e-9     # the degenerate pair shares two electrons
+    f0, _ = osc.occupations(eps, 4.0, 1e-5)
+    assert np.allclose(f0, [2, 2, 0, 0, 0, 0], atol=1e-9)
+
+
+def test_scf_fixed_point_against_dense_diagonalisation():
+    # the SCF fixed point of a tiny two-atom molecule reached by the oracle's
+    # block CG with a few sweeps per step equals the one reached with dense
+    # diagonalisation of H[n] (every eigenpair) at every step
+    from oracle import poisson as op, scf as osc
+    atoms = np.array([[0.0, 0, 0], [2.2, 0.3, -0.4]])
+    g = og.sphere_union_grid(atoms, 3.2, 0.55)
+    pr = oh.make_projectors(g, atoms, np.array([[1.0, 0.8], [1.5, 0.6]]), 1.0, 3.0)
+    vext = wl.local_potential(g.coords, atoms)
+    n0 = wl.atomic_density_guess(g.coords, atoms, 8, g.dV)
+    S = eigensolver.BlockCG(oh.Hamiltonian(g, vext, pr), wl.random_block(g.npts, 12, 3), 4, tol=1e-11)
+    scf = osc.SCF(S, g, vext, n0, 8, sweeps=5)
+    for _ in range(80):
+        if scf.step()[0] < 1e-10:
+            break
+    assert scf.residual < 1e-10 and scf.f[-1] < 1e-8
+    # dense path: H[n] assembled column by column, all eigenpairs, same mixing
+    Hd = oh.Hamiltonian(g, vext, pr)
+    mix = osc.Broyden(0.3, 8, g.dV)
+    n = n0.copy()
+    for _ in range(80):
+        exc, vxc = osc.lda_xc(n)
+        Hd.V = vext + op.hartree(g, n) + vxc
+        w, V = np.linalg.eigh(Hd.dense())
+        V = V / np.sqrt(g.dV)
+        f, _ = osc.occupations(w, 8.0, 0.01)
+        F = (V * V) @ f - n          # Eq. 1b: sum_k f_k |phi_k|^2
+        if np.sqrt(g.dV * np.sum(F * F)) < 1e-10:
+            break
+        n = mix.mix(n, F)
+    assert np.abs(w[:12] - S.eps).max() < 1e-8
+    assert np.sqrt(g.dV * np.sum((n - scf.n_in) ** 2)) < 1e-8

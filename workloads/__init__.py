@@ -117,6 +117,17 @@ def local_potential(coords: np.ndarray, atoms: np.ndarray, z: float = Z_ION, a: 
     return out
 
 
+def atomic_density_guess(coords: np.ndarray, atoms: np.ndarray, n_electrons: float, dV: float,
+                         width: float = 1.0) -> np.ndarray:
+    """Starting density of an SCF run: one normalised Gaussian of the given
+    width per atom, scaled so that dV * sum = n_electrons on the grid."""
+    coords = np.asarray(coords, dtype=np.float64)
+    n = np.zeros(len(coords))
+    for A in np.asarray(atoms, dtype=np.float64):
+        n += np.exp(-((coords - A) ** 2).sum(axis=1) / (2.0 * width * width))
+    return n * (n_electrons / (dV * n.sum()))
+
+
 def harmonic_potential(coords: np.ndarray, omega: float) -> np.ndarray:
     """V(r) = omega^2 |r|^2 / 2 at ``coords`` [n,3]."""
     coords = np.asarray(coords, dtype=np.float64)
