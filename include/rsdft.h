@@ -179,6 +179,12 @@ int rs_ham_apply_block(rs_ham *h, const void *psi_dev, int64_t ld_psi, void *hps
  * device word after the work queued before it.  Errors: RS_EINVAL, RS_ECUDA. */
 int rs_ham_status(rs_ham *h, int *flags);
 
+/* Replaces the local potential of H (an SCF step, Sec. III): V_dev device
+ * double [npts] in grid order; every table derived from it (FP32 copy,
+ * per-point records of the fused kernels) is rewritten on the device.
+ * Asynchronous: later calls on the stream use the new potential. */
+int rs_ham_set_potential(rs_ham *h, const double *V_dev, void *stream);
+
 /* Kernel selection of rs_ham_apply_block (a profiling aid for comparisons
  * such as the point-order study): RS_KERNEL_AUTO (0, the default) lets FP32
  * 32-state blocks take the persistent ring kernel where the grid allows it;
@@ -534,6 +540,12 @@ int rs_solver_set_precond(rs_solver *s, int precond);
  * (null argument, n_iter out of range, a grid of another size), RS_ENOMEM. */
 int rs_solver_set_precond_cg(rs_solver *s, rs_ham *shifted, int n_iter);
 
+/* New local potential for the solver's Hamiltonian (an SCF step): the
+ * Hamiltonian's potential is replaced (rs_ham_set_potential), the current
+ * subspace is rediagonalised with it and the search directions are dropped.
+ * V_dev device double [npts].  Blocking. */
+int rs_solver_set_potential(rs_solver *s, const double *V_dev, void *stream);
+
 int rs_solver_destroy(rs_solver *s);
 
 /* -------------------------------------------------------------- Hartree --
@@ -563,6 +575,47 @@ int rs_poisson_info(const rs_poisson *p, int32_t shape[3], double *r_cut, int64_
 int rs_poisson_solve(rs_poisson *p, const double *n_dev, double *vh_dev, void *stream);
 
 int rs_poisson_destroy(rs_poisson *p);
+
+/* ------------------------------------------------------------------ SCF --
+ * The self-consistent field loop of Sec. III (Fig. 2) around a solver: each
+ * step forms the Kohn-Sham potential of the input density n_in (Eq. 3:
+ * v_ext + v_H + v_xc, v_H by rs_poisson_solve, v_xc the local density
+ * approximation: Slater exchange and the Perdew-Zunger 1981 fit of the
+ * Ceperley-Alder correlation, unpolarised), sets it (rs_solver_set_potential),
+ * runs `sweeps` eigensolver sweeps, occupies the states with Fermi-Dirac
+ * occupations f_k = 2 / (1 + exp((eps_k - mu) / sigma)), sum f_k = n_electrons,
+ * forms n_out = sum f_k |phi_k|^2 (Eq. 1b over both spins) and mixes by
+ * Broyden's second update with uniform weights (Broyden 1965, Srivastava
+ * 1984) in its Anderson form: with F = n_out - n_in and the history dn_i,
+ * dF_i of the last `history` steps, n_in <- n_in + alpha F
+ * - sum theta_i (dn_i + alpha dF_i), theta minimising |F - sum theta_i dF_i|. */
+typedef struct {
+    double n_electrons;  /* electrons (at most 2 per state of the solver) */
+    double sigma;        /* Fermi smearing width (Ha), > 0 */
+    double alpha;        /* mixing parameter, > 0 */
+    int history;         /* Broyden history length, 0 .. 16 (0: linear mixing) */
+    int sweeps;          /* eigensolver sweeps per SCF step, >= 1 */
+} rs_scf_cfg;
+typedef struct rs_scf rs_scf;
+
+/* v_ext_host: host double [npts] (the external potential, e.g. the local
+ * pseudopotential the solver's Hamiltonian was built with); n0_host: host
+ * double [npts] starting density.  The solver's Hamiltonian potential is
+ * replaced at every step.  Blocking.  Errors: RS_EINVAL, RS_ENOMEM. */
+int rs_scf_create(rs_solver *s, const rs_grid *g, const double *v_ext_host, const double *n0_host,
+                  const rs_scf_cfg *cfg, rs_scf **out);
+
+/* One SCF step; residual = ||n_out - n_in|| (grid norm, before mixing) and
+ * energy = the Mermin free energy sum f eps - E_H - int n v_xc + E_xc
+ * - sigma S of the step's input density (ion-ion repulsion omitted), both
+ * may be NULL.  Blocking.  Errors: RS_ENAN, and the solver's. */
+int rs_scf_step(rs_scf *scf, double *residual, double *energy, void *stream);
+
+/* Current input density (device double [npts], may be NULL), the last
+ * occupations (host double [nst], may be NULL), mu and the step count. */
+int rs_scf_state(rs_scf *scf, double *n_in_dev, double *occupations_host, double *mu, int *iterations);
+
+int rs_scf_destroy(rs_scf *scf);
 
 #ifdef __cplusplus
 }

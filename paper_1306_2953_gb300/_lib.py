@@ -53,6 +53,11 @@ class SolverStats(ctypes.Structure):
                 ("train_target_seconds", ctypes.c_double), ("train_fit_seconds", ctypes.c_double)]
 
 
+class ScfCfg(ctypes.Structure):
+    _fields_ = [("n_electrons", ctypes.c_double), ("sigma", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("history", ctypes.c_int), ("sweeps", ctypes.c_int)]
+
+
 class LearnCfg(ctypes.Structure):
     _fields_ = [("n_res", ctypes.c_int), ("cg_iters", ctypes.c_int), ("sigma", ctypes.c_double), ("train", TrainCfg)]
 
@@ -121,6 +126,12 @@ SIGNATURES = {
     "rs_poisson_info": (None, [P, P, P, P]),
     "rs_poisson_solve": (None, [P, P, P, P]),
     "rs_poisson_destroy": (None, [P]),
+    "rs_ham_set_potential": (None, [P, P, P]),
+    "rs_solver_set_potential": (None, [P, P, P]),
+    "rs_scf_create": (None, [P, P, P, P, ctypes.POINTER(ScfCfg), PP]),
+    "rs_scf_step": (None, [P, P, P, P]),
+    "rs_scf_state": (None, [P, P, P, P, P]),
+    "rs_scf_destroy": (None, [P]),
 }
 
 _lock = threading.Lock()

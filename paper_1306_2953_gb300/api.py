@@ -502,3 +502,45 @@ class Poisson:
             self.close()
         except Exception:
             pass
+
+
+class SCF:
+    """Self-consistent field loop around a solver (rs_scf_*)."""
+
+    def __init__(self, solver: Solver, grid: Grid, v_ext, n0, n_electrons: float, sigma: float = 0.01,
+                 alpha: float = 0.3, history: int = 8, sweeps: int = 3):
+        v_ext = np.ascontiguousarray(v_ext, dtype=np.float64)
+        n0 = np.ascontiguousarray(n0, dtype=np.float64)
+        cfg = _lib.ScfCfg(float(n_electrons), float(sigma), float(alpha), int(history), int(sweeps))
+        out = ctypes.c_void_p()
+        call("rs_scf_create", solver._h, grid._h, _ptr(v_ext), _ptr(n0), ctypes.byref(cfg), ctypes.byref(out))
+        self._h = out
+        self.solver = solver
+        self.npts = grid.npts
+
+    def step(self, stream=None):
+        """One SCF step; returns (residual, energy)."""
+        r, e = ctypes.c_double(), ctypes.c_double()
+        call("rs_scf_step", self._h, ctypes.byref(r), ctypes.byref(e), _stream(stream))
+        return r.value, e.value
+
+    def state(self):
+        """(input density as a device tensor, occupations, mu, steps)."""
+        import torch
+        n = torch.empty(self.npts, dtype=torch.float64, device=self.solver.device)
+        occ = np.empty(self.solver.nst)
+        mu = ctypes.c_double()
+        it = ctypes.c_int()
+        call("rs_scf_state", self._h, _c(n.data_ptr()), _ptr(occ), ctypes.byref(mu), ctypes.byref(it))
+        return n, occ, mu.value, it.value
+
+    def close(self):
+        if self._h:
+            _lib.lib().rs_scf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -33,7 +33,7 @@ def _nvcc() -> str:
 
 
 # translation units of librsdft.so
-SOURCES = ["grid.cpp", "ham.cu", "linalg.cu", "subspace.cu", "precond.cu", "solver.cu", "learned.cu", "umma.cu", "noalloc.cu", "stencil_ring.cu", "device.cu", "poisson.cu"]
+SOURCES = ["grid.cpp", "ham.cu", "linalg.cu", "subspace.cu", "precond.cu", "solver.cu", "learned.cu", "umma.cu", "noalloc.cu", "stencil_ring.cu", "device.cu", "poisson.cu", "scf.cu"]
 
 
 def _sources():

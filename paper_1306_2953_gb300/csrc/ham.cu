@@ -799,6 +799,33 @@ extern "C" int rs_ham_status(rs_ham *h, int *flags) {
     return RS_OK;
 }
 
+__global__ void k_set_potential(const double *__restrict__ V, int64_t np, double *__restrict__ V64,
+                                float *__restrict__ V32, int4 *__restrict__ p64, int4 *__restrict__ p32) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+        const double v = V[p];
+        const float f = __double2float_rn(v);
+        V64[p] = v;
+        V32[p] = f;
+        const long long bits = __double_as_longlong(v);
+        int4 a = p64[p];
+        a.z = (int)(bits & 0xffffffffll);
+        a.w = (int)(bits >> 32);
+        p64[p] = a;
+        int4 b = p32[p];
+        b.z = __float_as_int(f);
+        p32[p] = b;
+    }
+}
+
+extern "C" int rs_ham_set_potential(rs_ham *h, const double *V_dev, void *stream) {
+    if (!h || !V_dev) return fail(RS_EINVAL, "rs_ham_set_potential: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    k_set_potential<<<(unsigned)std::min<int64_t>((h->npts + 255) / 256, 152 * 16), 256, 0, st>>>(
+        V_dev, h->npts, h->V64.as<double>(), h->V32.as<float>(), h->pinfo64.as<int4>(), h->pinfo32.as<int4>());
+    RS_LAUNCH_CHECK();
+    return ring_set_potential(h->ring, h->V32.as<float>(), st);
+}
+
 extern "C" int rs_ham_select_kernel(rs_ham *h, int which) {
     if (!h || (which != RS_KERNEL_AUTO && which != RS_KERNEL_GENERIC)) return fail(RS_EINVAL, "rs_ham_select_kernel: bad argument");
     h->kernel = which;

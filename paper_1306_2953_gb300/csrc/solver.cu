@@ -31,6 +31,7 @@
 #include "learned.h"
 #include "linalg.h"
 #include "precond.h"
+#include "solver_view.h"
 #include "umma.h"
 
 using namespace rs;
@@ -1187,6 +1188,31 @@ extern "C" int rs_solver_set_precond_cg(rs_solver *S, rs_ham *shifted, int n_ite
     S->pc = p;
     return RS_OK;
 }
+
+extern "C" int rs_solver_set_potential(rs_solver *S, const double *V_dev, void *stream) {
+    if (!S || !V_dev) return fail(RS_EINVAL, "rs_solver_set_potential: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const rs_solver_cfg &c = S->cfg;
+    RS_TRY(rs_ham_set_potential(S->h, V_dev, st));
+    // the current subspace rediagonalised with the new H; search directions dropped
+    RS_TRY(subspace_diag_impl(S->h, S->psi.p, S->hpsi.p, c.nst, c.nst, c.dtype, c.nb, S->la.p, S->eig.as<double>(), st,
+                              S->tc));
+    if (S->P.p) RS_CUDA(cudaMemsetAsync(S->P.p, 0, S->P.bytes, st));
+    std::fill(S->has_p.begin(), S->has_p.end(), 0);
+    RS_CUDA(cudaStreamSynchronize(st));
+    return RS_OK;
+}
+
+namespace rs {
+void solver_view(rs_solver *S, SolverView *v) {
+    v->psi = S->psi.p;
+    v->eig = S->eig.as<double>();
+    v->nst = S->cfg.nst;
+    v->dtype = S->cfg.dtype;
+    v->npts = S->npts;
+    v->dV = S->dV;
+}
+}  // namespace rs
 
 extern "C" int rs_solver_destroy(rs_solver *S) {
     delete S;

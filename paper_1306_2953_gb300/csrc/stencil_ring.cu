@@ -532,6 +532,8 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
 struct RingPlan {
     DevBuf units, cta, cta_atoms, desc, recs, rec, status;
     int n_cta = 0, rec_slot = 0, cs_atoms = 0, ring = MAX_RING, spin = SPIN;
+    int64_t nplanes = 0;
+    float w0 = 0.f;
     int64_t npts = 0;
     size_t smem = 0;
 };
@@ -781,6 +783,8 @@ int ring_plan_build(RingPlan **out, const rs_grid *g, const std::vector<int32_t>
             return bail(rc);
         if (cudaMemset(P->status.p, 0, sizeof(int)) != cudaSuccess) return bail(fail(RS_ECUDA, "cudaMemset failed"));
         P->n_cta = G;
+        P->nplanes = nplanes;
+        P->w0 = w0;
         P->rec_slot = (max_rec + 127) & ~127;
         P->cs_atoms = cs_atoms;
         P->npts = g->npts;
@@ -834,6 +838,30 @@ int ring_status(const RingPlan *p, int *flag) {
     *flag = 0;
     if (!p) return RS_OK;
     RS_CUDA(cudaMemcpy(flag, p->status.as<int>(), sizeof(int), cudaMemcpyDeviceToHost));
+    return RS_OK;
+}
+
+// the (w0 + V, w0 + V) pairs of every plane record from a new FP32
+// potential (the same FP32 sum the plan builder forms on the host)
+__global__ void k_ring_potential(const uint2 *__restrict__ recs, int64_t nplanes, unsigned char *__restrict__ rec,
+                                 const float *__restrict__ v32, float w0) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nplanes * NPOS) return;
+    const int64_t plane = t / NPOS;
+    const int pos = (int)(t - plane * NPOS);
+    unsigned char *r = rec + (size_t)recs[plane].x * 16;
+    const int idx = reinterpret_cast<const int *>(r + REC_IDX)[pos];
+    if (idx < 0) return;
+    const float vw = __fadd_rn(w0, v32[idx]);
+    reinterpret_cast<float2 *>(r + REC_V)[pos] = make_float2(vw, vw);
+}
+
+int ring_set_potential(RingPlan *p, const float *v32, cudaStream_t st) {
+    if (!p) return RS_OK;
+    const int64_t n = p->nplanes * NPOS;
+    k_ring_potential<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p->recs.as<uint2>(), p->nplanes,
+                                                                  p->rec.as<unsigned char>(), v32, p->w0);
+    RS_LAUNCH_CHECK();
     return RS_OK;
 }
 

@@ -35,6 +35,9 @@ int ring_launch(RingPlan *p, const float *psi, int64_t ldp, float *hpsi, int64_t
 
 // Status word of the kernel's bounded waits (0 = none timed out); blocking.
 int ring_status(const RingPlan *p, int *flag);
+// Rewrites the plan's potential values from a new FP32 potential [npts]
+// (asynchronous).
+int ring_set_potential(RingPlan *p, const float *v32, cudaStream_t st);
 // Clears the status word (blocking).
 int ring_reset_status(RingPlan *p);
 // Device address of the status word (nullptr without a plan).

@@ -86,6 +86,41 @@ def annotate(names):
         print(name, out.get("min_gap_ha"), out.get("error_bound_ha"))
 
 
+def scf_golden(spec: wl.ScfSpec):
+    """The oracle's SCF run (block CG, spec.sweeps sweeps per step) from the
+    atomic-Gaussian density guess and the workload's random start vectors,
+    until the density residual is below spec.tol; writes
+    tests/golden/scf_<name>.json with the eigenvalues, occupations, energy
+    and the residual history."""
+    from oracle import scf as osc
+    w = spec.base
+    g, H = build(w)
+    atoms = wl.atom_positions(w.system)
+    vext = H.V.copy()
+    n0 = wl.atomic_density_guess(g.coords, atoms, spec.n_electrons, g.dV)
+    t0 = time.time()
+    S = eigensolver.BlockCG(H, wl.random_block(g.npts, spec.n_states, w.seed), spec.block, tol=1e-10)
+    scf = osc.SCF(S, g, vext, n0, spec.n_electrons, sweeps=spec.sweeps, alpha=spec.alpha, history=spec.history,
+                  sigma=spec.sigma)
+    hist = []
+    for it in range(300):
+        r, e = scf.step()
+        hist.append(r)
+        print(f"  scf {it} residual {r:.3e} energy {e:.10f} {time.time() - t0:.0f}s", flush=True)
+        if r < spec.tol:
+            break
+    out = {"workload": spec.name, "npts": g.npts, "n_states": spec.n_states, "n_electrons": spec.n_electrons,
+           "eigenvalues": [float(v) for v in S.eps], "occupations": [float(v) for v in scf.f],
+           "energy": scf.energy, "mu": scf.mu, "residual": scf.residual, "iterations": scf.iterations,
+           "residual_history": hist, "cpu_seconds": time.time() - t0,
+           "source": "oracle/scf.py SCF around oracle/eigensolver.py BlockCG (FP64), written by "
+                     "tests/golden/make_golden.py"}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"scf_{spec.name}.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(spec.name, scf.iterations, f"{time.time() - t0:.1f}s", scf.residual, scf.energy)
+
+
 def main(names):
     for name in names:
         w = wl.WORKLOADS[name]
@@ -124,5 +159,8 @@ def main(names):
 if __name__ == "__main__":
     if sys.argv[1:2] == ["--annotate"]:
         annotate(sys.argv[2:])
+    elif sys.argv[1:2] == ["--scf"]:
+        for n in sys.argv[2:]:
+            scf_golden({s.name: s for s in (wl.SCF_MOL20,)}[n])
     else:
         main(sys.argv[1:])

@@ -73,6 +73,27 @@ MOL300 = Workload("mol300_h0.3", MoleculeSpec(300, 32.0, 2.0, 5.0, 0.3, 1308), 1
 WORKLOADS = {w.name: w for w in (HO32, MOL20, MOL100, MOL100_LEARNED, MOL300)}
 
 
+@dataclass(frozen=True)
+class ScfSpec:
+    """A self-consistent run on a workload's molecule: n_electrons (Z per
+    atom for a neutral molecule), states and block size of the eigensolver,
+    eigensolver sweeps per SCF step, Fermi smearing width (Ha), Broyden
+    mixing parameter and history, and the density-residual target."""
+    name: str
+    base: Workload
+    n_electrons: int
+    n_states: int
+    block: int
+    sweeps: int
+    sigma: float
+    alpha: float
+    history: int
+    tol: float
+
+
+SCF_MOL20 = ScfSpec("scf_mol20_h0.35", MOL20, 20 * 4, 64, 16, 3, 0.01, 0.3, 8, 1e-6)
+
+
 def atom_positions(spec: MoleculeSpec, max_tries: int = 1_000_000) -> np.ndarray:
     """Rejection-sample ``n_atoms`` points uniform in [0, cube]^3 with pairwise
     distance >= ``min_sep``.  Returns float64 [n_atoms, 3] (Bohr)."""
