@@ -381,10 +381,12 @@ def certified_solve(workload, modes, r_stop=1e-4, tol=1e-6, max_seconds=720.0, f
     for mode in modes:
         dt = torch.float64 if mode.startswith("f64") else torch.float32
         pc = _lib.RS_PRECOND_LEARNED if mode.endswith("learned") else _lib.RS_PRECOND_FILTER
+        method = _lib.RS_EIG_RMMDIIS if mode.endswith("_rmm") else _lib.RS_EIG_BLOCK_CG
         psi0_d = torch.from_numpy(psi0).to(dt).cuda()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S = api.Solver(H, psi0_d, workload.block, 1e-4, precond=pc, n_wanted=judged, stall_sweeps=3, stall_ratio=0.9)
+        S = api.Solver(H, psi0_d, workload.block, 1e-4, precond=pc, n_wanted=judged, stall_sweeps=3, stall_ratio=0.9,
+                       method=method)
         t_create = time.perf_counter() - t0
         if mode.endswith("_cg"):
             S.set_precond_cg(api.Hamiltonian(g, np.full(g.npts, 2.0)), 5)
@@ -402,13 +404,16 @@ def certified_solve(workload, modes, r_stop=1e-4, tol=1e-6, max_seconds=720.0, f
                                   "sweeps_timed": f64_sweeps}
             del S, psi0_d
             continue
-        certs, bound, nxt = [], float("inf"), None
+        certs, bound, nxt, traj = [], float("inf"), None, []
         while True:
             _, res, _ = S.step()
             st = S.stats()
             el = time.perf_counter() - t0
             rmax = float(res[:judged].max())
-            if (nxt is None and rmax <= r_stop) or (nxt is not None and st["sweeps"] >= nxt):
+            if st["sweeps"] % 10 == 0:
+                traj.append([st["sweeps"], round(el, 2), rmax])
+            final = el > max_seconds
+            if final or (nxt is None and rmax <= r_stop) or (nxt is not None and st["sweeps"] >= nxt):
                 tc = time.perf_counter()
                 eps, r64 = S.certify()
                 e, r = eps.cpu().numpy(), r64.cpu().numpy()
@@ -418,13 +423,11 @@ def certified_solve(workload, modes, r_stop=1e-4, tol=1e-6, max_seconds=720.0, f
                               "certify_seconds": time.perf_counter() - tc, "max_r64": float(r[:judged].max()),
                               "bound_ha": bound, "fp32_max_residual": rmax})
                 nxt = st["sweeps"] + 10
-                if bound <= tol:
+                if bound <= tol or final:
                     break
-            if el > max_seconds:
-                break
         el = time.perf_counter() - t0
         out["modes"][mode] = {"seconds": el, "sweeps": st["sweeps"], "certified": bound <= tol, "bound_ha": bound,
-                              "solver_create_seconds": t_create, "certificates": certs,
+                              "solver_create_seconds": t_create, "certificates": certs, "trajectory": traj,
                               "train_seconds": st["train_target_seconds"] + st["train_fit_seconds"],
                               "filter_fallback_after_sweep": st["fallback_sweep"] or None,
                               "eigenvalues_head": [float(x) for x in e[:8]] if certs else None}
@@ -435,6 +438,47 @@ def certified_solve(workload, modes, r_stop=1e-4, tol=1e-6, max_seconds=720.0, f
         f64["extrapolated_seconds"] = f64["solver_create_seconds"] + f64["seconds_per_sweep"] * f["sweeps"]
         f64["extrapolation"] = "measured FP64 seconds per sweep x the sweeps of the mixed filter solve (same start)"
     print(json.dumps(out), flush=True)
+    return out
+
+
+def scf_bench(spec, precisions=("f64", "f32"), max_steps=300):
+    """Seconds until the SCF density residual is below spec.tol (the 20-atom
+    molecule made self-consistent: FFT Hartree, LDA, Fermi occupations,
+    Broyden mixing around block CG), FP64 and mixed precision, against the
+    oracle's self-consistent reference (tests/golden) where it exists."""
+    import torch
+    from paper_1306_2953_gb300 import api
+    s = spec.base.system
+    atoms = wl.atom_positions(s)
+    g = api.Grid.spheres(atoms, s.radius, s.h)
+    coords = g.coords()
+    vext = wl.local_potential(coords, atoms)
+    pr = api.Projectors(g, atoms, wl.kb_couplings(s), s.r_c, s.r_cut)
+    H = api.Hamiltonian(g, vext, pr)
+    n0 = wl.atomic_density_guess(coords, atoms, spec.n_electrons, g.dV)
+    psi0 = wl.random_block(g.npts, spec.n_states, spec.base.seed)
+    gp = os.path.join(ROOT, "tests", "golden", f"scf_{spec.name}.json")
+    gold = json.load(open(gp)) if os.path.exists(gp) else None
+    out = {"workload": spec.name, "npts": g.npts, "electrons": spec.n_electrons, "states": spec.n_states,
+           "tolerance": spec.tol, "modes": {}}
+    for prec in precisions:
+        dt = torch.float64 if prec == "f64" else torch.float32
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = api.Solver(H, torch.from_numpy(psi0).to(dt).cuda(), spec.block, 1e-10)
+        scf = api.SCF(S, g, vext, n0, spec.n_electrons, sigma=spec.sigma, alpha=spec.alpha, history=spec.history,
+                      sweeps=spec.sweeps)
+        for _ in range(max_steps):
+            r, e = scf.step()
+            if r < spec.tol:
+                break
+        el = time.perf_counter() - t0
+        _, _, _, steps = scf.state()
+        m = {"seconds": el, "steps": steps, "residual": r, "energy_ha": e, "converged": r < spec.tol}
+        if gold is not None:
+            m["energy_error_vs_oracle_ha"] = abs(e - gold["energy"])
+        out["modes"][prec] = m
+        del scf, S
     return out
 
 
@@ -740,6 +784,8 @@ def main():
         line["eigensolve"] = [eigensolve_bench(wl.WORKLOADS[n], ["mixed_learned", "mixed_cg", "mixed_filter", "mixed_rmm",
                                                                  "f64_filter", "f64_rmm"])
                               for n in args.eigensolve.split(",")]
+    if rank == 0 and world == 1 and args.eigensolve != "none":
+        line["scf"] = scf_bench(wl.SCF_MOL20)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
