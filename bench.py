@@ -482,6 +482,39 @@ def scf_bench(spec, precisions=("f64", "f32"), max_steps=300):
     return out
 
 
+def poisson_timing(workload, n):
+    """n FFT Hartree solves (rs_poisson_solve) of a smooth density on the
+    workload's grid after three untimed ones; prints the time per solve and
+    the algorithmic bytes: six one-dimensional FFT passes reading and
+    writing the complex cube, the kernel multiplication (read + write), the
+    cube clear and the grid <-> cube copies, over CUDA-event time."""
+    import torch
+    from paper_1306_2953_gb300 import api
+    spec = workload.system
+    atoms = wl.atom_positions(spec)
+    g = api.Grid.spheres(atoms, spec.radius, spec.h)
+    P = api.Poisson(g)
+    shape, rc, cube_bytes = P.info()
+    rho = torch.from_numpy(wl.atomic_density_guess(g.coords(), atoms, 4 * spec.n_atoms, g.dV)).cuda()
+    vh = torch.empty_like(rho)
+    for _ in range(3):
+        P.solve(rho, vh)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        P.solve(rho, vh)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    by = cube_bytes * (6 * 2 + 2 + 1) + g.npts * (8 + 4 + 16) * 2
+    peak, kind = measured_peaks()
+    print(json.dumps({"workload": workload.name, "npts": g.npts, "cube": shape, "r_cut_bohr": rc,
+                      "ms_per_solve": ms, "algorithmic_bytes": by, "gbs": by / (ms * 1e-3) / 1e9,
+                      "frac_of_peak": by / (ms * 1e-3) / 1e9 / peak, "peak_source": kind}))
+    return 0
+
+
 def nb_sweep(workload, orders=(4,)):
     """H psi throughput against the block size and the grid's point order
     (the analogue of the paper's block-size and ordering study, Sec. V.A):
@@ -621,6 +654,8 @@ def main():
                          "block of --workload (seeded initial weights) and exit (no benchmark line)")
     ap.add_argument("--sweep-precision", default="f32", choices=["f32", "f64"],
                     help="precision of the --profile-sweeps solver")
+    ap.add_argument("--poisson-timing", type=int, default=0,
+                    help="profiling aid: time this many FFT Hartree solves on --workload's grid and exit")
     ap.add_argument("--certified", default="",
                     help="workload(s) for the certified time to 1e-6 Ha without an oracle reference (e.g. "
                          "mol300_h0.3): prints one JSON object per workload and exits (no benchmark line)")
@@ -633,6 +668,8 @@ def main():
     workload = wl.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, workload)
+    if args.poisson_timing > 0:
+        return poisson_timing(workload, args.poisson_timing)
     if args.certified:
         for n in args.certified.split(","):
             certified_solve(wl.WORKLOADS[n], args.certified_modes.split(","),
