@@ -415,7 +415,11 @@ def certified_solve(workload, modes, r_stop=1e-4, tol=1e-6, max_seconds=720.0, f
             final = el > max_seconds
             if final or (nxt is None and rmax <= r_stop) or (nxt is not None and st["sweeps"] >= nxt):
                 tc = time.perf_counter()
-                eps, r64 = S.certify()
+                try:
+                    eps, r64 = S.certify()
+                except _lib.RsError as exc:
+                    certs.append({"sweep": st["sweeps"], "error": str(exc)})
+                    break
                 e, r = eps.cpu().numpy(), r64.cpu().numpy()
                 b = certificate_bound(e, r)[:judged]
                 bound = float(b.max())

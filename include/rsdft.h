@@ -503,7 +503,8 @@ int rs_solver_rayleigh_ritz_f64(rs_solver *s, double *eps_dev, void *stream);
  * r_k^2 / gap_k when gap_k separates eps_k from the rest of the spectrum.
  * eps_dev, res_dev: device double [nst].  The iteration state is not
  * modified.  Blocking; the first call allocates two FP64 copies of the
- * orbitals.  Errors: RS_ENOTSPD, RS_ENOCONV (dense eigensolver cap). */
+ * orbitals.  The residual norms measure the returned pairs whatever the
+ * dense eigensolver's iteration did.  Errors: RS_ENOTSPD. */
 int rs_solver_certify(rs_solver *s, double *eps_dev, double *res_dev, void *stream);
 
 /* Ritz residuals R = H psi_k - eps_k psi_k of states first..first+ncols-1

@@ -794,10 +794,9 @@ extern "C" int rs_solver_certify(rs_solver *S, double *eps_dev, double *res_dev,
     k_resid_norm2<<<dim3((unsigned)((n + 255) / 256), 512), 256, 0, st>>>(P, Q, n, n, eps_dev, S->npts, res_dev);
     k_sqrt_scale<<<(n + 255) / 256, 256, 0, st>>>(res_dev, n, S->dV);
     RS_LAUNCH_CHECK();
-    int info = 0;
-    RS_CUDA(cudaMemcpyAsync(&info, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // (the dense eigensolver's own sweep caps are not an error here: the FP64
+    // residual norms measure the Ritz pairs whatever path produced them)
     RS_CUDA(cudaStreamSynchronize(st));
-    if (info) return fail(RS_ENOCONV, "rs_solver_certify: the dense eigensolver hit its sweep cap");
     return RS_OK;
 }
 
