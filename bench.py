@@ -490,8 +490,9 @@ def poisson_timing(workload, n):
     """n FFT Hartree solves (rs_poisson_solve) of a smooth density on the
     workload's grid after three untimed ones; prints the time per solve and
     the algorithmic bytes: six one-dimensional FFT passes reading and
-    writing the complex cube, the kernel multiplication (read + write), the
-    cube clear and the grid <-> cube copies, over CUDA-event time."""
+    writing the complex cube, the kernel multiplication (cube read and
+    written, the FP64 kernel table read), the cube clear and the grid <->
+    cube copies, over CUDA-event time."""
     import torch
     from paper_1306_2953_gb300 import api
     spec = workload.system
@@ -511,7 +512,7 @@ def poisson_timing(workload, n):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / n
-    by = cube_bytes * (6 * 2 + 2 + 1) + g.npts * (8 + 4 + 16) * 2
+    by = int(cube_bytes * (6 * 2 + 2.5 + 1)) + g.npts * (8 + 4 + 16) * 2
     peak, kind = measured_peaks()
     print(json.dumps({"workload": workload.name, "npts": g.npts, "cube": shape, "r_cut_bohr": rc,
                       "ms_per_solve": ms, "algorithmic_bytes": by, "gbs": by / (ms * 1e-3) / 1e9,

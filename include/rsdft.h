@@ -562,9 +562,9 @@ int rs_solver_destroy(rs_solver *s);
  * The transforms are the library's own complex FP64 Stockham kernels. */
 typedef struct rs_poisson rs_poisson;
 
-/* Plans the cube for grid g and allocates it on the current device
- * (blocking).  Errors: RS_EINVAL (empty grid, an axis above 768 points),
- * RS_ENOMEM. */
+/* Plans the cube for grid g and allocates it on the current device, with
+ * the table of v(G) (24 bytes per cube element in all; blocking).  Errors:
+ * RS_EINVAL (empty grid, an axis above 768 points), RS_ENOMEM. */
 int rs_poisson_create(const rs_grid *g, rs_poisson **out);
 
 /* Cube shape, the cutoff radius R_c (Bohr) and the cube's bytes. */
