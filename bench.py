@@ -348,20 +348,37 @@ ORDER_NAMES = {4: "brick4", 1: "lexicographic", 2: "brick2", 8: "brick8", -1: "m
 
 
 def certificate_bound(eps, res):
-    """Per-state eigenvalue error bound from FP64 Ritz values and residual
-    norms (rs_solver_certify): r^2 / gap where the gap to the nearest other
-    Ritz value exceeds r, else r."""
-    e = np.asarray(eps)
-    srt = np.sort(e)
-    pos = np.searchsorted(srt, e)
-    lo = np.where(pos > 0, e - srt[np.maximum(pos - 1, 0)], np.inf)
-    hi = np.where(pos + 1 < len(srt), srt[np.minimum(pos + 1, len(srt) - 1)] - e, np.inf)
-    gap = np.minimum(lo, hi)
-    r = np.asarray(res)
-    return np.where(gap > r, r * r / np.maximum(gap, 1e-300), r)
+    """Per-state eigenvalue error bounds from FP64 Ritz values and residual
+    norms (rs_solver_certify).  Ritz values closer than ten times their
+    combined residual are grouped into clusters; for a cluster C with
+    residual ||R_C||^2 = sum r_i^2 and gap delta_C to the nearest Ritz value
+    outside it, every eigenvalue it approximates lies within
+    ||R_C||^2 / delta_C (Kato-Temple for an invariant subspace) when
+    delta_C > ||R_C||, else within ||R_C||."""
+    e = np.asarray(eps, dtype=np.float64)
+    r = np.asarray(res, dtype=np.float64)
+    order = np.argsort(e)
+    es, rs = e[order], r[order]
+    clusters = [[0]]
+    for i in range(1, len(es)):
+        prev = clusters[-1]
+        if es[i] - es[prev[-1]] < 10.0 * np.sqrt(rs[i] ** 2 + rs[prev[-1]] ** 2):
+            prev.append(i)
+        else:
+            clusters.append([i])
+    b = np.empty(len(es))
+    for c in clusters:
+        R = np.sqrt(np.sum(rs[c] ** 2))
+        lo = es[c[0]] - es[c[0] - 1] if c[0] > 0 else np.inf
+        hi = es[c[-1] + 1] - es[c[-1]] if c[-1] + 1 < len(es) else np.inf
+        d = min(lo, hi)
+        b[c] = R * R / d if d > R else R
+    out = np.empty(len(es))
+    out[order] = b
+    return out
 
 
-def certified_solve(workload, modes, r_stop=1e-4, tol=1e-6, max_seconds=720.0, f64_sweeps=2):
+def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f64_sweeps=2):
     """Time to a certified tol Ha for a workload without an oracle reference
     (the 300-atom molecule): sweeps until the largest FP32-measured residual of
     the judged states is below r_stop, then rs_solver_certify (FP64
