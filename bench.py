@@ -397,13 +397,13 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
     w0 = initial_weights(LEARN["seed"])
     for mode in modes:
         dt = torch.float64 if mode.startswith("f64") else torch.float32
-        pc = _lib.RS_PRECOND_LEARNED if mode.endswith("learned") else _lib.RS_PRECOND_FILTER
-        method = _lib.RS_EIG_RMMDIIS if mode.endswith("_rmm") else _lib.RS_EIG_BLOCK_CG
+        pc = _lib.RS_PRECOND_LEARNED if "learned" in mode else _lib.RS_PRECOND_FILTER
+        method = _lib.RS_EIG_RMMDIIS if "_rmm" in mode else _lib.RS_EIG_BLOCK_CG
         psi0_d = torch.from_numpy(psi0).to(dt).cuda()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S = api.Solver(H, psi0_d, workload.block, 1e-4, precond=pc, n_wanted=judged, stall_sweeps=3, stall_ratio=0.9,
-                       method=method)
+        S = api.Solver(H, psi0_d, workload.block, r_stop, precond=pc, n_wanted=judged, stall_sweeps=3,
+                       stall_ratio=0.9, method=method)
         t_create = time.perf_counter() - t0
         if mode.endswith("_cg"):
             S.set_precond_cg(api.Hamiltonian(g, np.full(g.npts, 2.0)), 5)
@@ -453,11 +453,12 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
                               "filter_fallback_after_sweep": st["fallback_sweep"] or None,
                               "eigenvalues_head": [float(x) for x in e[:8]] if certs else None}
         del S, psi0_d
-    f = out["modes"].get("mixed_filter")
-    f64 = out["modes"].get("f64_filter")
-    if f and f64:
-        f64["extrapolated_seconds"] = f64["solver_create_seconds"] + f64["seconds_per_sweep"] * f["sweeps"]
-        f64["extrapolation"] = "measured FP64 seconds per sweep x the sweeps of the mixed filter solve (same start)"
+    for mixed, f64name in (("mixed_filter", "f64_filter"), ("mixed_rmm", "f64_rmm")):
+        f, f64 = out["modes"].get(mixed), out["modes"].get(f64name)
+        if f and f64:
+            f64["extrapolated_seconds"] = f64["solver_create_seconds"] + f64["seconds_per_sweep"] * f["sweeps"]
+            f64["extrapolation"] = (f"measured FP64 seconds per sweep x the sweeps of the {mixed} solve (same "
+                                    "start, same method)")
     print(json.dumps(out), flush=True)
     return out
 
