@@ -380,12 +380,15 @@ def certificate_bound(eps, res):
 
 def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f64_sweeps=2):
     """Time to a certified tol Ha for a workload without an oracle reference
-    (the 300-atom molecule): sweeps until the largest FP32-measured residual of
-    the judged states is below r_stop, then rs_solver_certify (FP64
-    Rayleigh-Ritz and FP64 residual norms of the Ritz vectors); the error
-    bound r^2/gap of every judged state must be <= tol, otherwise ten more
-    sweeps and a new certificate.  The plain FP64 path is timed for
-    f64_sweeps sweeps and extrapolated to the filter mode's sweep count."""
+    (the 300-atom molecule): sweeps, with r_stop as the solver's tolerance
+    (a block whose residuals are all below it is left alone), until the
+    largest FP32-measured residual of the judged states is below r_stop,
+    then rs_solver_certify (FP64 Rayleigh-Ritz and FP64 residual norms of
+    the Ritz vectors); the bound of certificate_bound for every judged state
+    must be <= tol, otherwise ten more sweeps and a new certificate; at the
+    time cap a last certificate is taken and reported.  The plain FP64 path
+    is timed for f64_sweeps sweeps and extrapolated to the sweep count of
+    the mixed solve of the same method."""
     import torch
     from paper_1306_2953_gb300 import api, _lib
     g, H = build_any(workload)
