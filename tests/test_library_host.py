@@ -193,3 +193,19 @@ def test_full_size_projector_lists_mol100():
         assert np.array_equal(lib_pts[order], pr_ref.points(A))
         g_ora = pr_ref.gamma(A).T
         assert np.abs(gam[off[A]:off[A + 1]][order] - g_ora).max() < 1e-13 * np.abs(g_ora).max()
+
+
+def test_empty_and_invalid_grids_are_rejected():
+    # a sphere too small to hold a lattice point, zero or negative sizes,
+    # and non-finite positions are all RS_EINVAL (no handle is returned)
+    with pytest.raises(RsError) as e:
+        api.Grid.spheres(np.array([[0.15, 0.15, 0.15]]), 0.01, 0.3)
+    assert e.value.code == RS_EINVAL
+    for args in ((np.array([[0.0, 0.0, 0.0]]), -1.0, 0.3), (np.array([[0.0, 0.0, 0.0]]), 2.0, 0.0),
+                 (np.array([[np.nan, 0.0, 0.0]]), 2.0, 0.3)):
+        with pytest.raises(RsError) as e:
+            api.Grid.spheres(*args)
+        assert e.value.code == RS_EINVAL
+    with pytest.raises(RsError) as e:
+        api.Grid.box(0, 4, 4, 0.3)
+    assert e.value.code == RS_EINVAL
