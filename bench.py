@@ -386,8 +386,9 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
     largest FP32-measured residual of the judged states is below r_stop,
     then rs_solver_certify (FP64 Rayleigh-Ritz and FP64 residual norms of
     the Ritz vectors); the bound of certificate_bound for every judged state
-    must be <= tol, otherwise ten more sweeps and a new certificate; at the
-    time cap a last certificate is taken and reported.  The plain FP64 path
+    must be <= tol, otherwise cert_every more sweeps and a new certificate;
+    certificates are also taken every cert_every sweeps once the residual is
+    below cert_below, and at the time cap a last one is taken and reported.  The plain FP64 path
     is timed for f64_sweeps sweeps and extrapolated to the sweep count of
     the mixed solve of the same method."""
     import torch
@@ -438,7 +439,7 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
             # every cert_every sweeps once it is below cert_below (the FP32
             # residuals of a large system can stall above r_stop while the
             # FP64 certificate already meets tol)
-            periodic = rmax <= cert_below and st["sweeps"] % cert_every == 0
+            periodic = nxt is None and rmax <= cert_below and st["sweeps"] % cert_every == 0
             if final or periodic or (nxt is None and rmax <= r_stop) or (nxt is not None and st["sweeps"] >= nxt):
                 tc = time.perf_counter()
                 try:
@@ -452,7 +453,7 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
                 certs.append({"sweep": st["sweeps"], "seconds": time.perf_counter() - t0,
                               "certify_seconds": time.perf_counter() - tc, "max_r64": float(r[:judged].max()),
                               "bound_ha": bound, "fp32_max_residual": rmax})
-                nxt = st["sweeps"] + 10
+                nxt = st["sweeps"] + cert_every
                 if bound <= tol or final:
                     break
         el = time.perf_counter() - t0
