@@ -642,20 +642,23 @@ def replica_throughput(world, bytes_per_step, steps, ms_max):
     return world * bytes_per_step * steps / (ms_max * 1e-3) / 1e9
 
 
-def profile_sweeps(workload, n, precision="f32"):
+def profile_sweeps(workload, n, precision="f32", method="cg"):
     """Solver creation and n eigensolver sweeps (filter preconditioner) in
-    FP32 (mixed: FP32 orbitals, FP64 subspace steps) or FP64, one JSON line
-    per sweep with its wall time and largest residual."""
+    FP32 (mixed: FP32 orbitals, FP64 subspace steps) or FP64, block CG or
+    RMM-DIIS, one JSON line per sweep with its wall time and largest
+    residual."""
     import torch
-    from paper_1306_2953_gb300 import api
+    from paper_1306_2953_gb300 import api, _lib
     g, H = build_system(workload)
     dt = torch.float64 if precision == "f64" else torch.float32
     psi0 = torch.from_numpy(wl.random_block(g.npts, workload.n_states, workload.seed)).to(dt).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    S = api.Solver(H, psi0, workload.block, 1e-4)
+    S = api.Solver(H, psi0, workload.block, 1e-4,
+                   method=_lib.RS_EIG_RMMDIIS if method == "rmm" else _lib.RS_EIG_BLOCK_CG)
     torch.cuda.synchronize()
-    print(json.dumps({"workload": workload.name, "precision": precision, "npts": g.npts, "states": workload.n_states,
+    print(json.dumps({"workload": workload.name, "precision": precision, "method": method, "npts": g.npts,
+                      "states": workload.n_states,
                       "solver_create_seconds": time.perf_counter() - t0}))
     for _ in range(n):
         torch.cuda.synchronize()
@@ -687,6 +690,8 @@ def main():
                          "block of --workload (seeded initial weights) and exit (no benchmark line)")
     ap.add_argument("--sweep-precision", default="f32", choices=["f32", "f64"],
                     help="precision of the --profile-sweeps solver")
+    ap.add_argument("--sweep-method", default="cg", choices=["cg", "rmm"],
+                    help="eigensolver of the --profile-sweeps solver: block CG or RMM-DIIS")
     ap.add_argument("--poisson-timing", type=int, default=0,
                     help="profiling aid: time this many FFT Hartree solves on --workload's grid and exit")
     ap.add_argument("--certified", default="",
@@ -709,7 +714,7 @@ def main():
                             max_seconds=args.certified_max_seconds)
         return 0
     if args.profile_sweeps > 0:
-        return profile_sweeps(workload, args.profile_sweeps, args.sweep_precision)
+        return profile_sweeps(workload, args.profile_sweeps, args.sweep_precision, args.sweep_method)
     if args.nb_sweep:
         orders = (4, 1, 2, 8, -1, -2) if args.orders == "all" else tuple(int(x) for x in args.orders.split(","))
         return nb_sweep(workload, orders)
