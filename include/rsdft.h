@@ -541,6 +541,17 @@ int rs_solver_set_precond(rs_solver *s, int precond);
  * (null argument, n_iter out of range, a grid of another size), RS_ENOMEM. */
 int rs_solver_set_precond_cg(rs_solver *s, rs_ham *shifted, int n_iter);
 
+/* Checkpoint and restart (no counterpart in the paper): the iteration state
+ * of a solver -- orbitals, H applied to them, block CG's search directions,
+ * eigenvalues, residual norms and the sweep count -- to a file, and back
+ * into a solver created with the same grid size and configuration, which
+ * then continues exactly where the saved one stood.  File: "RSCK", uint32
+ * version 1, int64 npts, int32 nst, nb, dtype, method, sweeps, uint32
+ * search-direction flag, the raw arrays, and an FNV-1a hash.  Blocking.
+ * Errors: RS_EINVAL (cannot open, another shape, damaged file), RS_ECUDA. */
+int rs_solver_checkpoint_save(rs_solver *s, const char *path);
+int rs_solver_checkpoint_load(rs_solver *s, const char *path);
+
 /* New local potential for the solver's Hamiltonian (an SCF step): the
  * Hamiltonian's potential is replaced (rs_ham_set_potential), the current
  * subspace is rediagonalised with it and the search directions are dropped.

@@ -128,6 +128,8 @@ SIGNATURES = {
     "rs_poisson_destroy": (None, [P]),
     "rs_ham_set_potential": (None, [P, P, P]),
     "rs_solver_set_potential": (None, [P, P, P]),
+    "rs_solver_checkpoint_save": (None, [P, ctypes.c_char_p]),
+    "rs_solver_checkpoint_load": (None, [P, ctypes.c_char_p]),
     "rs_scf_create": (None, [P, P, P, P, ctypes.POINTER(ScfCfg), PP]),
     "rs_scf_step": (None, [P, P, P, P]),
     "rs_scf_state": (None, [P, P, P, P, P]),

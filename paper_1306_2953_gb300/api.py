@@ -291,6 +291,14 @@ class Solver:
              _c(w_init.data_ptr()) if w_init is not None else None, losses, _stream(stream))
         return list(losses)[:epochs]
 
+    def checkpoint_save(self, path: str):
+        """rs_solver_checkpoint_save: the iteration state to a file."""
+        call("rs_solver_checkpoint_save", self._h, str(path).encode())
+
+    def checkpoint_load(self, path: str):
+        """rs_solver_checkpoint_load: continue from a saved iteration state."""
+        call("rs_solver_checkpoint_load", self._h, str(path).encode())
+
     def save_precond(self, path: str):
         call("rs_precond_save", self._h, str(path).encode())
 

@@ -1188,6 +1188,124 @@ extern "C" int rs_solver_set_precond_cg(rs_solver *S, rs_ham *shifted, int n_ite
     return RS_OK;
 }
 
+// Checkpoint file: "RSCK", then little-endian uint32 version (1), int64
+// npts, int32 nst, nb, dtype, method, sweeps, uint32 has-P flag, the
+// orbitals, H applied to them and (block CG) the search directions as raw
+// arrays [npts][nst] of the solver's element type, the eigenvalues and the
+// residual norms (double [nst] each), one byte per block (search direction
+// present), and the uint32 FNV-1a hash of everything after the magic.
+namespace {
+struct CkWriter {
+    FILE *f;
+    uint32_t h = 2166136261u;
+    bool ok = true;
+    void put(const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 16777619u;
+        ok = ok && fwrite(p, 1, n, f) == n;
+    }
+};
+struct CkReader {
+    FILE *f;
+    uint32_t h = 2166136261u;
+    bool ok = true;
+    void get(void *p, size_t n) {
+        ok = ok && fread(p, 1, n, f) == n;
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t i = 0; ok && i < n; ++i) h = (h ^ c[i]) * 16777619u;
+    }
+};
+}  // namespace
+
+extern "C" int rs_solver_checkpoint_save(rs_solver *S, const char *path) {
+    if (!S || !path) return fail(RS_EINVAL, "rs_solver_checkpoint_save: null argument");
+    const rs_solver_cfg &c = S->cfg;
+    const size_t big = (size_t)S->npts * c.nst * S->es;
+    std::vector<unsigned char> host(big);
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(RS_EINVAL, "rs_solver_checkpoint_save: cannot open %s", path);
+    CkWriter w{f};
+    if (fwrite("RSCK", 1, 4, f) != 4) w.ok = false;
+    const uint32_t ver = 1, hp = S->P.p ? 1u : 0u;
+    const int64_t np = S->npts;
+    const int32_t hdr[5] = {c.nst, c.nb, c.dtype, c.method, S->sweeps};
+    w.put(&ver, 4);
+    w.put(&np, 8);
+    w.put(hdr, sizeof(hdr));
+    w.put(&hp, 4);
+    int rc = RS_OK;
+    for (DevBuf *b : {&S->psi, &S->hpsi, &S->P}) {
+        if (b == &S->P && !hp) continue;
+        if (cudaMemcpy(host.data(), b->p, big, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = fail(RS_ECUDA, "rs_solver_checkpoint_save: copy failed");
+            break;
+        }
+        w.put(host.data(), big);
+    }
+    std::vector<double> e(c.nst), r(c.nst);
+    if (rc == RS_OK && (cudaMemcpy(e.data(), S->eig.p, 8 * c.nst, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                        cudaMemcpy(r.data(), S->res.p, 8 * c.nst, cudaMemcpyDeviceToHost) != cudaSuccess))
+        rc = fail(RS_ECUDA, "rs_solver_checkpoint_save: copy failed");
+    if (rc == RS_OK) {
+        w.put(e.data(), 8 * e.size());
+        w.put(r.data(), 8 * r.size());
+        w.put(S->has_p.data(), S->has_p.size());
+        const uint32_t hh = w.h;
+        w.ok = w.ok && fwrite(&hh, 1, 4, f) == 4;
+    }
+    if (fclose(f) != 0) w.ok = false;
+    if (rc != RS_OK) return rc;
+    if (!w.ok) return fail(RS_EINVAL, "rs_solver_checkpoint_save: write to %s failed", path);
+    return RS_OK;
+}
+
+extern "C" int rs_solver_checkpoint_load(rs_solver *S, const char *path) {
+    if (!S || !path) return fail(RS_EINVAL, "rs_solver_checkpoint_load: null argument");
+    const rs_solver_cfg &c = S->cfg;
+    const size_t big = (size_t)S->npts * c.nst * S->es;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(RS_EINVAL, "rs_solver_checkpoint_load: cannot open %s", path);
+    char magic[4] = {0, 0, 0, 0};
+    CkReader r{f};
+    r.ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "RSCK", 4) == 0;
+    uint32_t ver = 0, hp = 0;
+    int64_t np = 0;
+    int32_t hdr[5] = {0, 0, 0, 0, 0};
+    r.get(&ver, 4);
+    r.get(&np, 8);
+    r.get(hdr, sizeof(hdr));
+    r.get(&hp, 4);
+    const bool match = r.ok && ver == 1 && np == S->npts && hdr[0] == c.nst && hdr[1] == c.nb && hdr[2] == c.dtype &&
+                       hdr[3] == c.method && hp == (S->P.p ? 1u : 0u);
+    if (!match) {
+        fclose(f);
+        return fail(RS_EINVAL, "rs_solver_checkpoint_load: %s is not a checkpoint of a solver of this shape", path);
+    }
+    std::vector<unsigned char> psi(big), hpsi(big), P(hp ? big : 0);
+    std::vector<double> e(c.nst), res(c.nst);
+    std::vector<char> has_p(S->has_p.size());
+    r.get(psi.data(), big);
+    r.get(hpsi.data(), big);
+    if (hp) r.get(P.data(), big);
+    r.get(e.data(), 8 * e.size());
+    r.get(res.data(), 8 * res.size());
+    r.get(has_p.data(), has_p.size());
+    uint32_t stored = 0;
+    const uint32_t h = r.h;
+    const bool tail = fread(&stored, 1, 4, f) == 4;
+    fclose(f);
+    if (!r.ok || !tail || stored != h) return fail(RS_EINVAL, "rs_solver_checkpoint_load: %s is damaged", path);
+    RS_CUDA(cudaDeviceSynchronize());
+    RS_CUDA(cudaMemcpy(S->psi.p, psi.data(), big, cudaMemcpyHostToDevice));
+    RS_CUDA(cudaMemcpy(S->hpsi.p, hpsi.data(), big, cudaMemcpyHostToDevice));
+    if (hp) RS_CUDA(cudaMemcpy(S->P.p, P.data(), big, cudaMemcpyHostToDevice));
+    RS_CUDA(cudaMemcpy(S->eig.p, e.data(), 8 * e.size(), cudaMemcpyHostToDevice));
+    RS_CUDA(cudaMemcpy(S->res.p, res.data(), 8 * res.size(), cudaMemcpyHostToDevice));
+    S->has_p = has_p;
+    S->sweeps = hdr[4];
+    return RS_OK;
+}
+
 extern "C" int rs_solver_set_potential(rs_solver *S, const double *V_dev, void *stream) {
     if (!S || !V_dev) return fail(RS_EINVAL, "rs_solver_set_potential: null argument");
     cudaStream_t st = (cudaStream_t)stream;

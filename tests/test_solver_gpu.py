@@ -360,3 +360,38 @@ def test_rmm_diis_mol100_mixed_reaches_oracle_eigenvalues():
     S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).float().cuda(), w.block, 1e-4,
                    n_wanted=len(ref), method=_lib.RS_EIG_RMMDIIS, **SCHEDULE)
     _solve_to_golden(S, ref, 1e-6, 300)
+
+
+def test_checkpoint_restart_continues_the_iteration(tmp_path):
+    """rs_solver_checkpoint_save after five sweeps, then three more sweeps,
+    equal (to rounding: atomic summation order) three sweeps of a second
+    solver restarted from the file; a damaged file and a solver of another
+    shape are refused."""
+    from paper_1306_2953_gb300 import api
+    from paper_1306_2953_gb300._lib import RS_EINVAL, RsError
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    psi0 = torch.from_numpy(np.ascontiguousarray(wl.random_block(g_ora.npts, w.n_states, w.seed)[idx])).cuda()
+    A = api.Solver(H, psi0, w.block, 1e-8)
+    for _ in range(5):
+        A.step()
+    path = tmp_path / "ck.rsck"
+    A.checkpoint_save(str(path))
+    for _ in range(3):
+        ea, ra, _ = A.step()
+    B = api.Solver(H, torch.zeros_like(psi0).normal_(), w.block, 1e-8)
+    B.checkpoint_load(str(path))
+    for _ in range(3):
+        eb, rb, _ = B.step()
+    assert A.stats()["sweeps"] == B.stats()["sweeps"] == 8
+    assert torch.allclose(ea, eb, rtol=0, atol=1e-10) and torch.allclose(ra, rb, rtol=1e-6, atol=1e-12)
+    raw = bytearray(path.read_bytes())
+    raw[len(raw) // 2] ^= 0x10
+    (tmp_path / "bad.rsck").write_bytes(bytes(raw))
+    with pytest.raises(RsError) as e:
+        B.checkpoint_load(str(tmp_path / "bad.rsck"))
+    assert e.value.code == RS_EINVAL
+    C = api.Solver(H, psi0[:, :32].contiguous(), w.block, 1e-8)
+    with pytest.raises(RsError) as e:
+        C.checkpoint_load(str(path))
+    assert e.value.code == RS_EINVAL
