@@ -11,7 +11,9 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librsdft.so")
+# RSDFT_LIB selects another build of the library, e.g. the bounds-checked
+# debugging build librsdft_check.so (python -m paper_1306_2953_gb300.build --bounds-check)
+LIB_PATH = os.environ.get("RSDFT_LIB") or os.path.join(_HERE, "librsdft.so")
 
 RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENOTSPD, RS_ENOCONV, RS_ENAN, RS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 RS_F64, RS_F32 = 0, 1

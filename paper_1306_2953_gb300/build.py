@@ -51,21 +51,27 @@ def _digest() -> str:
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    stamp = os.path.join(BUILD, "stamp")
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    """Builds librsdft.so (or, with bounds_check, librsdft_check.so: the
+    debugging build whose H psi kernel tests every point index it copies from
+    or stores to and records an index out of range in its status word)."""
+    out = LIB if not bounds_check else os.path.join(HERE, "librsdft_check.so")
+    bdir = BUILD if not bounds_check else BUILD + "_check"
+    stamp = os.path.join(bdir, "stamp")
     dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    if not force and os.path.exists(out) and os.path.exists(stamp) and open(stamp).read() == dig:
+        return out
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     inc = [f"-I{INCLUDE}", f"-I{CSRC}"]
+    extra = ["-DRS_BOUNDS_CHECK=1"] if bounds_check else []
     jobs = []
     for src in _sources():
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(bdir, src + ".o")
         path = os.path.join(CSRC, src)
         if src.endswith(".cu"):
             cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-                   "--expt-relaxed-constexpr", *inc, "-c", path, "-o", obj]
+                   "--expt-relaxed-constexpr", *extra, *inc, "-c", path, "-o", obj]
         else:
             cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", *inc,
                    "-I/usr/local/cuda/include", "-c", path, "-o", obj]
@@ -82,17 +88,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(run, jobs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     link = [nvcc, ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(" ".join(link) + "\n" + r.stdout + r.stderr)
         raise RuntimeError("link failed")
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     with open(stamp, "w") as f:
         f.write(dig)
-    return LIB
+    return out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds_check="--bounds-check" in sys.argv))

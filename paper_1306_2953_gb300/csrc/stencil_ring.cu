@@ -42,7 +42,10 @@
 // of a unit contribute only their z-terms (tile rows only, no record).
 //
 // Every mbarrier wait is bounded; on a timeout the kernel sets its status
-// word and leaves the march.
+// word and leaves the march.  Built with RS_BOUNDS_CHECK=1 (a debugging
+// build standing in for a memory checker), every point index the kernel
+// copies from or stores to is tested against the point count first; an index
+// out of range is skipped and sets bit 2 of the status word.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -50,6 +53,10 @@
 
 #include "device.h"
 #include "stencil_ring.h"
+
+#ifndef RS_BOUNDS_CHECK
+#define RS_BOUNDS_CHECK 0
+#endif
 
 namespace rs {
 
@@ -127,6 +134,7 @@ struct Args {
     int64_t ldh;
     int nb, rec_slot, cs_atoms;   // cs_atoms: the largest atom count of a CTA
     int spin;                     // barrier tests before a wait gives up
+    int npts;                     // point count (the bounds-checked build tests indices against it)
     float w[5];
     int *status;
 };
@@ -180,6 +188,8 @@ struct Lane {
     int rb0, rb1;  // first of the four right of rows 0 / 1
     int to;        // tile index of patch row 0, column 0 (record tables)
     int w, h, sl;
+    int npts;      // point count and status word (bounds-checked build)
+    int *status;
 };
 
 // position p -> float2 offset of the lane's state pair: p * PS + lane
@@ -271,6 +281,18 @@ __device__ __forceinline__ void plane_terms(float2 (&T)[2][4], const float2 (&cc
     }
 }
 
+// A point index the kernel may store to or copy from (always true unless
+// the bounds-checked build finds it out of range, which it records).
+__device__ __forceinline__ bool index_ok(int i, int npts, int *status) {
+#if RS_BOUNDS_CHECK
+    if (i >= npts) {
+        atomicOr(status, 2);
+        return false;
+    }
+#endif
+    return true;
+}
+
 // Writes the finished output of the plane in accumulator slot R.
 template <int R>
 __device__ __forceinline__ void emit(const float2 (&A)[8][2][4], const int *rowring, float *hp, int64_t ldh,
@@ -278,7 +300,13 @@ __device__ __forceinline__ void emit(const float2 (&A)[8][2][4], const int *rowr
     const int4 *ring4 = reinterpret_cast<const int4 *>(rowring + R * NPOS) + (c.to >> 2);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const int4 id = ring4[r * (TX / 4)];
+        int4 id = ring4[r * (TX / 4)];
+#if RS_BOUNDS_CHECK
+        if (!index_ok(id.x, c.npts, c.status)) id.x = -1;
+        if (!index_ok(id.y, c.npts, c.status)) id.y = -1;
+        if (!index_ok(id.z, c.npts, c.status)) id.z = -1;
+        if (!index_ok(id.w, c.npts, c.status)) id.w = -1;
+#endif
         if (id.x >= 0) *reinterpret_cast<float2 *>(hp + (int64_t)id.x * ldh) = A[R][r][0];
         if (id.y >= 0) *reinterpret_cast<float2 *>(hp + (int64_t)id.y * ldh) = A[R][r][1];
         if (id.z >= 0) *reinterpret_cast<float2 *>(hp + (int64_t)id.z * ldh) = A[R][r][2];
@@ -417,7 +445,8 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
             const uint32_t mask = d >> 28;
             const bool has = (mask & rbit) != 0;
             const int pnt = (int)(d & 0x0fffffffu) + __popc(mask & (rbit - 1u));
-            cp_async16(dst + k * (NW * 4 * ROWB), has ? src0 + (int64_t)pnt * a.ldp : src0, has);
+            const bool use = has && index_ok(pnt, a.npts, a.status);
+            cp_async16(dst + k * (NW * 4 * ROWB), use ? src0 + (int64_t)pnt * a.ldp : src0, use);
         }
         if (pfull) {
             const uint32_t rx = __shfl_sync(0xffffffffu, rq.x, 10 * g), ry = __shfl_sync(0xffffffffu, rq.y, 10 * g);
@@ -440,6 +469,8 @@ __global__ void __launch_bounds__(NT, 1) k_hpsi_ring(Args a) {
     c.w = warp;
     c.h = lane >> 4;
     c.sl = lane & 15;
+    c.npts = a.npts;
+    c.status = a.status;
     {
         const int px = warp & 3, ty0 = 4 * (warp >> 2) + 2 * c.h, sl = c.sl;
         const int tx0 = 4 * px;
@@ -823,6 +854,7 @@ int ring_launch(RingPlan *p, const float *psi, int64_t ldp, float *hpsi, int64_t
     a.nb = nb;
     a.rec_slot = p->rec_slot;
     a.spin = p->spin;
+    a.npts = (int)p->npts;
     for (int j = 0; j < 5; ++j) a.w[j] = w[j];
     a.status = p->status.as<int>();
     const dim3 grid((unsigned)p->n_cta, (unsigned)(nb / SG));

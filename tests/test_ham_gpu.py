@@ -22,6 +22,8 @@ sign (~65 u) and its worst case is n u: c_nl = 512 is eight times the
 typical growth.  A wrong or missing nonlocal entry changes an element by a
 term of size ~M_nl, 2^24 / 512 = 32768 times this bound.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -227,3 +229,34 @@ def test_hpsi_full_size_mol300_f32():
     m_loc, m_nl = _term_magnitudes(g_ora, H_ora, psi_ora)
     _assert_elementwise_f32(out, ref, m_loc[idx], m_nl[idx])
     assert H.status() == 0
+
+
+def test_bounds_checked_build_runs_clean():
+    """The debugging build (RS_BOUNDS_CHECK=1: every point index the FP32 ring
+    kernel copies from or stores to is tested first, an index out of range is
+    skipped and recorded in the status word) computes the same H psi with a
+    clean status word, in a child process that loads that build."""
+    import subprocess
+    import sys
+    from paper_1306_2953_gb300 import build
+    lib = build.build(bounds_check=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = """
+import numpy as np, torch, workloads as wl
+from tests.helpers import lib_to_oracle_index, oracle_system
+from paper_1306_2953_gb300 import api
+s = wl.MOL20.system
+g, Ho, atoms, E = oracle_system("mol", s)
+lg = api.Grid.spheres(atoms, s.radius, s.h)
+idx = lib_to_oracle_index(g, lg.ijk())
+H = api.Hamiltonian(lg, Ho.V[idx], api.Projectors(lg, atoms, E, s.r_c, s.r_cut))
+psi = wl.random_block(g.npts, 64, 5).astype(np.float32)
+ref = Ho.apply(psi.astype(np.float64))[idx]
+out = H.apply(torch.from_numpy(np.ascontiguousarray(psi[idx])).cuda()).double().cpu().numpy()
+err = np.max(np.linalg.norm(out - ref, axis=0) / np.linalg.norm(ref, axis=0))
+assert err <= 2e-6 and H.status() == 0, (err, H.status())
+print("checked build ok", err)
+"""
+    env = dict(os.environ, RSDFT_LIB=lib, PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "checked build ok" in r.stdout, r.stdout + r.stderr

@@ -209,3 +209,14 @@ def test_empty_and_invalid_grids_are_rejected():
     with pytest.raises(RsError) as e:
         api.Grid.box(0, 4, 4, 0.3)
     assert e.value.code == RS_EINVAL
+
+
+def test_bounds_checked_build_compiles():
+    # the debugging build of the library (index tests in the FP32 H psi
+    # kernel) builds beside the normal one and exports the same symbols
+    import ctypes
+    from paper_1306_2953_gb300 import _lib, build
+    path = build.build(bounds_check=True)
+    L = ctypes.CDLL(path)
+    for name in _lib.exported_names():
+        assert hasattr(L, name), name
