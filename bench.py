@@ -379,13 +379,15 @@ def certificate_bound(eps, res):
 
 
 def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f64_sweeps=2, cert_below=3e-4,
-                    cert_every=100):
+                    cert_every=100, n_smooth=4):
     """Time to a certified tol Ha for a workload without an oracle reference
     (the 300-atom molecule): sweeps, with r_stop as the solver's tolerance
     (a block whose residuals are all below it is left alone), until the
     largest FP32-measured residual of the judged states is below r_stop,
-    then rs_solver_certify (FP64 Rayleigh-Ritz and FP64 residual norms of
-    the Ritz vectors); the bound of certificate_bound for every judged state
+    then rs_solver_certify_smoothed (n_smooth damped FP64 Richardson steps
+    on the orbitals, which remove their FP32 rounding noise, then the FP64
+    Rayleigh-Ritz and FP64 residual norms of the Ritz vectors; n_smooth = 0
+    is the plain rs_solver_certify); the bound of certificate_bound for every judged state
     must be <= tol, otherwise cert_every more sweeps and a new certificate;
     certificates are also taken every cert_every sweeps once the residual is
     below cert_below, and at the time cap a last one is taken and reported.  The plain FP64 path
@@ -396,8 +398,9 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
     g, H = build_any(workload)
     judged = workload.judged
     out = {"workload": workload.name, "npts": g.npts, "states": workload.n_states, "judged": judged,
-           "tolerance_ha": tol, "r_stop": r_stop, "reference": "FP64 certificate (rs_solver_certify): "
-           "max over judged states of r^2/gap (r where gap <= r)", "modes": {}}
+           "tolerance_ha": tol, "r_stop": r_stop, "smoothing_steps": n_smooth,
+           "reference": "FP64 certificate (rs_solver_certify_smoothed): max over judged states of r^2/gap "
+           "(r where gap <= r)", "modes": {}}
     psi0 = wl.random_block(g.npts, workload.n_states, workload.seed)
     w0 = initial_weights(LEARN["seed"])
     for mode in modes:
@@ -443,7 +446,7 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
             if final or periodic or (nxt is None and rmax <= r_stop) or (nxt is not None and st["sweeps"] >= nxt):
                 tc = time.perf_counter()
                 try:
-                    eps, r64 = S.certify()
+                    eps, r64 = S.certify_smoothed(n_smooth)
                 except _lib.RsError as exc:
                     certs.append({"sweep": st["sweeps"], "error": str(exc)})
                     break
@@ -461,7 +464,15 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
                               "solver_create_seconds": t_create, "certificates": certs, "trajectory": traj,
                               "train_seconds": st["train_target_seconds"] + st["train_fit_seconds"],
                               "filter_fallback_after_sweep": st["fallback_sweep"] or None,
+                              "lambda_max_estimate": st["lambda_max"] or None,
                               "eigenvalues_head": [float(x) for x in e[:8]] if certs else None}
+        if certs and n_smooth > 0 and "error" not in certs[-1]:
+            # outside the timed region: the same subspace certified without
+            # smoothing, and the largest change of a judged Ritz value
+            e0, r0 = (t.cpu().numpy() for t in S.certify())
+            out["modes"][mode]["unsmoothed"] = {"max_r64": float(r0[:judged].max()),
+                                                "bound_ha": float(certificate_bound(e0, r0)[:judged].max()),
+                                                "max_ritz_shift_ha": float(np.abs(e0[:judged] - e[:judged]).max())}
         del S, psi0_d
     for mixed, f64name in (("mixed_filter", "f64_filter"), ("mixed_rmm", "f64_rmm")):
         f, f64 = out["modes"].get(mixed), out["modes"].get(f64name)
@@ -699,6 +710,8 @@ def main():
                          "mol300_h0.3): prints one JSON object per workload and exits (no benchmark line)")
     ap.add_argument("--certified-modes", default="f64_filter,mixed_filter,mixed_learned")
     ap.add_argument("--certified-max-seconds", type=float, default=720.0)
+    ap.add_argument("--certified-smooth", type=int, default=4,
+                    help="FP64 smoothing steps before each certificate (rs_solver_certify_smoothed; 0: none)")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling aid: run this many mixed-precision eigensolver sweeps on --workload, "
                          "print their times and exit (no benchmark line)")
@@ -711,7 +724,7 @@ def main():
     if args.certified:
         for n in args.certified.split(","):
             certified_solve(wl.WORKLOADS[n], args.certified_modes.split(","),
-                            max_seconds=args.certified_max_seconds)
+                            max_seconds=args.certified_max_seconds, n_smooth=args.certified_smooth)
         return 0
     if args.profile_sweeps > 0:
         return profile_sweeps(workload, args.profile_sweeps, args.sweep_precision, args.sweep_method)

@@ -384,6 +384,8 @@ typedef struct {
     double max_residual;          /* largest residual norm of the wanted states in the last sweep */
     double train_target_seconds;  /* last rs_precond_train: residuals and CG targets (wall clock) */
     double train_fit_seconds;     /* last rs_precond_train: tile cutting and Adam steps (wall clock) */
+    double lambda_max;            /* estimate of the largest eigenvalue of H taken by
+                                   * rs_solver_certify_smoothed (0: not taken yet) */
 } rs_solver_stats_t;
 
 /* Host-side statistics of the solver (no device work). */
@@ -506,6 +508,30 @@ int rs_solver_rayleigh_ritz_f64(rs_solver *s, double *eps_dev, void *stream);
  * orbitals.  The residual norms measure the returned pairs whatever the
  * dense eigensolver's iteration did.  Errors: RS_ENOTSPD. */
 int rs_solver_certify(rs_solver *s, double *eps_dev, double *res_dev, void *stream);
+
+/* Smoothed certificate (no counterpart in the paper): rs_solver_certify
+ * after n_smooth damped Richardson steps on the FP64 copy of the orbitals,
+ *     psi_k <- psi_k - (H psi_k - eps_k psi_k) / (lambda_max - eps_k),
+ * eps_k the solver's current eigenvalues, H applied in FP64.  A step leaves
+ * an eigenvector of H unchanged and multiplies the component of psi_k along
+ * an eigenvector of eigenvalue mu by 1 - (mu - eps_k) / (lambda_max - eps_k):
+ * zero at the top of the spectrum, one half midway.  It damps the
+ * high-energy rounding noise that FP32 storage leaves in the orbitals, which
+ * inflates the residual norms (by the noise times up to lambda_max) far more
+ * than it moves the eigenvalues; what the steps do to components inside the
+ * subspace (the lower states are amplified by at most
+ * 1 + (eps_k - eps_0) / (lambda_max - eps_k)) the Rayleigh-Ritz undoes.  The
+ * Ritz pairs returned are exact Rayleigh-Ritz pairs of the smoothed subspace,
+ * so their residual norms certify them as in rs_solver_certify.
+ * lambda_max > 0 is used as given and must exceed every current eigenvalue
+ * (RS_EINVAL otherwise); lambda_max <= 0 takes an estimate of the largest
+ * eigenvalue of H: 120 power iterations on H - eps_0 in FP64 from a fixed
+ * start vector, the Rayleigh quotient of the last iterate (a lower bound of
+ * it; taken once per solver, reported by rs_solver_stats).  n_smooth in
+ * 0 .. 16; 0 is rs_solver_certify.  The iteration state is not modified.
+ * Blocking.  Errors: RS_EINVAL, RS_ENOTSPD, RS_ENAN (the estimate failed). */
+int rs_solver_certify_smoothed(rs_solver *s, int n_smooth, double lambda_max, double *eps_dev, double *res_dev,
+                               void *stream);
 
 /* Ritz residuals R = H psi_k - eps_k psi_k of states first..first+ncols-1
  * of the current orbitals (after the last sweep's subspace diagonalisation),

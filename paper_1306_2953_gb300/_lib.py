@@ -52,7 +52,8 @@ class SolverCfg(ctypes.Structure):
 class SolverStats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("eps_f64", ctypes.c_int), ("precond", ctypes.c_int),
                 ("fallback_sweep", ctypes.c_int), ("max_residual", ctypes.c_double),
-                ("train_target_seconds", ctypes.c_double), ("train_fit_seconds", ctypes.c_double)]
+                ("train_target_seconds", ctypes.c_double), ("train_fit_seconds", ctypes.c_double),
+                ("lambda_max", ctypes.c_double)]
 
 
 class ScfCfg(ctypes.Structure):
@@ -111,6 +112,7 @@ SIGNATURES = {
     "rs_solver_residual": (None, [P, I32, I32, P, I64, P]),
     "rs_solver_rayleigh_ritz_f64": (None, [P, P, P]),
     "rs_solver_certify": (None, [P, P, P, P]),
+    "rs_solver_certify_smoothed": (None, [P, I32, F64, P, P, P]),
     "rs_solver_set_precond_weights": (None, [P, P]),
     "rs_solver_set_precond": (None, [P, I32]),
     "rs_solver_set_precond_cg": (None, [P, P, I32]),

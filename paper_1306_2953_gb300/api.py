@@ -343,6 +343,17 @@ class Solver:
         call("rs_solver_certify", self._h, _c(eps.data_ptr()), _c(res.data_ptr()), _stream(stream))
         return eps, res
 
+    def certify_smoothed(self, n_smooth: int, lambda_max: float = 0.0, stream=None):
+        """rs_solver_certify_smoothed: the certificate after n_smooth damped
+        FP64 Richardson steps on the orbitals (lambda_max <= 0: the library's
+        estimate of the largest eigenvalue of H), as device tensors (eps, res)."""
+        import torch
+        eps = torch.empty(self.nst, dtype=torch.float64, device=self.device)
+        res = torch.empty(self.nst, dtype=torch.float64, device=self.device)
+        call("rs_solver_certify_smoothed", self._h, int(n_smooth), float(lambda_max), _c(eps.data_ptr()),
+             _c(res.data_ptr()), _stream(stream))
+        return eps, res
+
     def residual(self, first: int, ncols: int, stream=None):
         """Ritz residuals of states first..first+ncols-1 as a device tensor."""
         import torch

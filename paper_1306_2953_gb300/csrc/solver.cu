@@ -400,6 +400,7 @@ struct rs_solver {
     int sweeps = 0, eps_f64 = 0, fallback_sweep = 0, stall = 0;
     double best = std::numeric_limits<double>::infinity(), max_res = 0;
     double train_target_s = 0, train_fit_s = 0;
+    double lam_max = 0;   // power-iteration estimate of the largest eigenvalue of H (0: not taken)
     DevBuf eps64;   // FP64 Rayleigh-Ritz eigenvalues when the caller passes no eps_dev
     // RMM-DIIS: iterates x_i, H x_i, r_i ([slot][npts][nb] each kind), p, H p,
     // the combinations, and the small per-column arrays
@@ -743,9 +744,107 @@ __global__ void k_sqrt_scale(double *a, int n, double s) {
     if (k < n) a[k] = sqrt(s * a[k]);
 }
 
-extern "C" int rs_solver_certify(rs_solver *S, double *eps_dev, double *res_dev, void *stream) {
-    if (!S || !eps_dev || !res_dev) return fail(RS_EINVAL, "rs_solver_certify: null argument");
-    cudaStream_t st = (cudaStream_t)stream;
+// one damped Richardson step per column, P[p][k] -= (Q[p][k] - eps[k] P[p][k]) / (lam - eps[k])
+__global__ void k_smooth_step(double *__restrict__ P, const double *__restrict__ Q, const double *__restrict__ eps,
+                              double lam, int n, int64_t total) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % n);
+        const double t = eps[k];
+        P[e] -= (Q[e] - t * P[e]) / (lam - t);
+    }
+}
+
+// power iteration: a fixed pseudo-random start vector (splitmix64 of the index)
+__global__ void k_pi_start(double *x, int64_t npts) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npts; p += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = (uint64_t)p + 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[p] = (double)(z >> 11) * 0x1.0p-53 - 0.5;
+    }
+}
+
+// acc[0] += sum x y', acc[1] += sum y'^2 with y' = y - sigma x (one CTA per chunk)
+__global__ void k_pi_dots(const double *__restrict__ x, const double *__restrict__ y, double sigma, int64_t npts,
+                          double *acc) {
+    __shared__ double red[2][32];
+    double a = 0, b = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npts; p += (int64_t)gridDim.x * blockDim.x) {
+        const double v = y[p] - sigma * x[p];
+        a += x[p] * v;
+        b += v * v;
+    }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (!lane) {
+        red[0][wid] = a;
+        red[1][wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? red[0][lane] : 0;
+        b = lane < nw ? red[1][lane] : 0;
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (!lane) {
+            atomicAdd(acc, a);
+            atomicAdd(acc + 1, b);
+        }
+    }
+}
+
+// x <- (y - sigma x) / ||y - sigma x|| (acc[1] holds the squared norm;
+// every iteration accumulates into its own pair of zeroed words)
+__global__ void k_pi_scale(double *__restrict__ x, const double *__restrict__ y, double sigma, int64_t npts,
+                           const double *acc) {
+    const double s = acc[1] > 0 ? 1.0 / sqrt(acc[1]) : 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npts; p += (int64_t)gridDim.x * blockDim.x)
+        x[p] = (y[p] - sigma * x[p]) * s;
+}
+
+// largest eigenvalue of H: power iteration on H - sigma with sigma the
+// solver's lowest Ritz value (an upper bound of the lowest eigenvalue, so
+// that H - sigma is positive up to that small overlap and the iteration
+// converges to the top of the spectrum), Rayleigh quotient of the last
+// iterate.  A Rayleigh quotient never exceeds lambda_max.
+static int lambda_max_estimate(rs_solver *S, double *x, double *y, cudaStream_t st, double *out) {
+    constexpr int ITERS = 120;
+    double sigma = 0;
+    RS_CUDA(cudaMemcpyAsync(&sigma, S->eig.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    DevBuf acc;
+    RS_TRY(acc.alloc(sizeof(double) * 2 * (ITERS + 1)));
+    RS_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(double) * 2 * (ITERS + 1), st));
+    const int64_t n = S->npts;
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_pi_start<<<g, 256, 0, st>>>(x, n);
+    k_pi_dots<<<g, 256, 0, st>>>(x, x, 0.0, n, acc.as<double>());
+    k_pi_scale<<<g, 256, 0, st>>>(x, x, 0.0, n, acc.as<double>());
+    RS_LAUNCH_CHECK();
+    for (int it = 1; it <= ITERS; ++it) {
+        double *a = acc.as<double>() + 2 * it;
+        RS_TRY(rs_ham_apply_block(S->h, x, 1, y, 1, 1, RS_F64, st));
+        k_pi_dots<<<g, 256, 0, st>>>(x, y, sigma, n, a);
+        if (it < ITERS) k_pi_scale<<<g, 256, 0, st>>>(x, y, sigma, n, a);
+        RS_LAUNCH_CHECK();
+    }
+    double last[2] = {0, 0};
+    RS_CUDA(cudaMemcpyAsync(last, acc.as<double>() + 2 * ITERS, sizeof(last), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    // x has unit norm: the Rayleigh quotient of H - sigma is x . (H - sigma) x
+    if (!std::isfinite(last[0]) || !(last[0] > 0)) return fail(RS_ENAN, "lambda_max estimate failed");
+    *out = last[0] + sigma;
+    return RS_OK;
+}
+
+static int certify_impl(rs_solver *S, int n_smooth, double lam, double *eps_dev, double *res_dev, cudaStream_t st) {
     const rs_solver_cfg &c = S->cfg;
     const int n = c.nst;
     const size_t nn = (size_t)n * n;
@@ -761,14 +860,33 @@ extern "C" int rs_solver_certify(rs_solver *S, double *eps_dev, double *res_dev,
     int *status = reinterpret_cast<int *>(T + nn);
     void *ew = reinterpret_cast<void *>(T + nn + 16);
     double *P = S->psi64.as<double>(), *Q = S->hpsi64.as<double>();
+    const int64_t total = S->npts * n;
+    if (n_smooth > 0 && !(lam > 0)) {
+        if (!(S->lam_max > 0)) RS_TRY(lambda_max_estimate(S, P, Q, st, &S->lam_max));
+        lam = S->lam_max;
+    }
     // FP64 orbitals (a widened copy of FP32 ones) and H applied in FP64
     if (c.dtype == RS_F32) {
-        k_widen<<<1024, 256, 0, st>>>(S->psi.as<float>(), P, S->npts * n);
+        k_widen<<<1024, 256, 0, st>>>(S->psi.as<float>(), P, total);
         RS_LAUNCH_CHECK();
     } else {
-        RS_CUDA(cudaMemcpyAsync(P, S->psi.p, sizeof(double) * (size_t)S->npts * n, cudaMemcpyDeviceToDevice, st));
+        RS_CUDA(cudaMemcpyAsync(P, S->psi.p, sizeof(double) * (size_t)total, cudaMemcpyDeviceToDevice, st));
     }
     for (int b = 0; b < n; b += c.nb) RS_TRY(rs_ham_apply_block(S->h, P + b, n, Q + b, n, c.nb, RS_F64, st));
+    if (n_smooth > 0) {
+        // the step must damp every mode above the subspace: lam above the
+        // largest current eigenvalue
+        std::vector<double> e(n);
+        RS_CUDA(cudaMemcpyAsync(e.data(), S->eig.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+        for (double v : e)
+            if (!(lam > v)) return fail(RS_EINVAL, "rs_solver_certify_smoothed: lambda_max %g below an eigenvalue %g", lam, v);
+    }
+    for (int s = 0; s < n_smooth; ++s) {
+        k_smooth_step<<<1024, 256, 0, st>>>(P, Q, S->eig.as<double>(), lam, n, total);
+        RS_LAUNCH_CHECK();
+        for (int b = 0; b < n; b += c.nb) RS_TRY(rs_ham_apply_block(S->h, P + b, n, Q + b, n, c.nb, RS_F64, st));
+    }
     // h x = eps S x (Sec. VI, Eq. 7) with S = U^T U: the Ritz vectors are
     // Psi C with C = U^-1 Y, Y the eigenvectors of U^-T h U^-1
     RS_TRY(gram<double>(P, n, n, P, n, n, S->npts, S->dV, Sm, n, st));
@@ -798,6 +916,19 @@ extern "C" int rs_solver_certify(rs_solver *S, double *eps_dev, double *res_dev,
     // residual norms measure the Ritz pairs whatever path produced them)
     RS_CUDA(cudaStreamSynchronize(st));
     return RS_OK;
+}
+
+extern "C" int rs_solver_certify(rs_solver *S, double *eps_dev, double *res_dev, void *stream) {
+    if (!S || !eps_dev || !res_dev) return fail(RS_EINVAL, "rs_solver_certify: null argument");
+    return certify_impl(S, 0, 0.0, eps_dev, res_dev, (cudaStream_t)stream);
+}
+
+extern "C" int rs_solver_certify_smoothed(rs_solver *S, int n_smooth, double lambda_max, double *eps_dev,
+                                          double *res_dev, void *stream) {
+    if (!S || !eps_dev || !res_dev) return fail(RS_EINVAL, "rs_solver_certify_smoothed: null argument");
+    if (n_smooth < 0 || n_smooth > 16) return fail(RS_EINVAL, "rs_solver_certify_smoothed: n_smooth must be in 0 .. 16");
+    if (!std::isfinite(lambda_max)) return fail(RS_EINVAL, "rs_solver_certify_smoothed: lambda_max must be finite");
+    return certify_impl(S, n_smooth, lambda_max, eps_dev, res_dev, (cudaStream_t)stream);
 }
 
 extern "C" int rs_solver_rayleigh_ritz_f64(rs_solver *S, double *eps_dev, void *stream) {
@@ -975,6 +1106,7 @@ extern "C" int rs_solver_stats(rs_solver *S, rs_solver_stats_t *out) {
     out->max_residual = S->max_res;
     out->train_target_seconds = S->train_target_s;
     out->train_fit_seconds = S->train_fit_s;
+    out->lambda_max = S->lam_max;
     return RS_OK;
 }
 

@@ -274,6 +274,31 @@ MUTANTS = [
            "            hx = hx + lam * hp",
            "            hx = hx + 0.0 * hp",
            "rmm"),
+    # certificate and its smoothing (no paper equation; Rayleigh-Ritz of Sec. VI)
+    Mutant("smooth_step_sign", "certificate.py",
+           "X = X - (apply_h(X) - X * theta) / (lam - theta)",
+           "X = X + (apply_h(X) - X * theta) / (lam - theta)",
+           "richardson"),
+    Mutant("smooth_theta_dropped", "certificate.py",
+           "X = X - (apply_h(X) - X * theta) / (lam - theta)",
+           "X = X - apply_h(X) / (lam - theta)",
+           "richardson"),
+    Mutant("smooth_step_length_unshifted", "certificate.py",
+           "X = X - (apply_h(X) - X * theta) / (lam - theta)",
+           "X = X - (apply_h(X) - X * theta) / lam",
+           "richardson"),
+    Mutant("certificate_residual_without_dV", "certificate.py",
+           "res = np.sqrt(dV * ((HXr - Xr * eps) ** 2).sum(axis=0))",
+           "res = np.sqrt(((HXr - Xr * eps) ** 2).sum(axis=0))",
+           "ritz_certificate"),
+    Mutant("certificate_overlap_ignored", "certificate.py",
+           "eps, Y = scipy.linalg.eigh(h, 0.5 * (S + S.T))",
+           "eps, Y = scipy.linalg.eigh(h)",
+           "ritz_certificate"),
+    Mutant("certificate_residual_sign", "certificate.py",
+           "res = np.sqrt(dV * ((HXr - Xr * eps) ** 2).sum(axis=0))",
+           "res = np.sqrt(dV * ((HXr + Xr * eps) ** 2).sum(axis=0))",
+           "ritz_certificate"),
     Mutant("adam_second_moment_uses_gradient", "precond.py",
            "self.v[i] = self.b2 * self.v[i] + (1 - self.b2) * g * g",
            "self.v[i] = self.b2 * self.v[i] + (1 - self.b2) * np.abs(g)",

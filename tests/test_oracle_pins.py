@@ -764,3 +764,77 @@ def test_scf_fixed_point_against_dense_diagonalisation():
         n = mix.mix(n, F)
     assert np.abs(w[:12] - S.eps).max() < 1e-8
     assert np.sqrt(g.dV * np.sum((n - scf.n_in) ** 2)) < 1e-8
+
+
+# ------------------------------------------------ certificate (no paper eq.) ---
+
+def _ho_pair(n=10, h=0.35):
+    """Two exact separable eigenvectors (ground state and the x-excited
+    state) of the harmonic oscillator on a box, normalised <phi|phi> = 1."""
+    from oracle import certificate as oc  # noqa: F401
+    g = og.box_grid(n, h)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, 1.0))
+    e1, v1 = one_d_levels(n, h, 1.0)
+    phi = [np.einsum("i,j,k->ijk", v1[:, a], v1[:, 0], v1[:, 0]).ravel() / np.sqrt(g.dV) for a in (0, 1)]
+    mu = [e1[a] + 2 * e1[0] for a in (0, 1)]
+    return g, H, phi, mu
+
+
+def test_ritz_certificate_two_level_closed_form():
+    # x = phi_a + t phi_b: Ritz value (mu_a + t^2 mu_b) / (1 + t^2) and
+    # residual norm t |mu_b - mu_a| / (1 + t^2)
+    from oracle import certificate as oc
+    g, H, (pa, pb), (ma, mb) = _ho_pair()
+    for t in (1e-3, 0.2, 0.7):
+        eps, res, xr = oc.ritz_certificate(H.apply, (pa + t * pb)[:, None], g.dV)
+        assert abs(eps[0] - (ma + t * t * mb) / (1 + t * t)) < 1e-12
+        assert abs(res[0] - t * abs(mb - ma) / (1 + t * t)) < 1e-10 * max(t, 1e-2)
+        assert abs(g.dV * xr[:, 0] @ xr[:, 0] - 1) < 1e-12
+
+
+def test_ritz_certificate_invariant_subspace_exact():
+    # a skewed (non-orthonormal) basis of an exact invariant subspace: Ritz
+    # values are the exact eigenvalues and every residual vanishes
+    from oracle import certificate as oc
+    g, H, (pa, pb), (ma, mb) = _ho_pair()
+    X = np.stack([pa + 0.3 * pb, 2.0 * pb - 0.5 * pa], axis=1)
+    eps, res, _ = oc.ritz_certificate(H.apply, X, g.dV)
+    assert np.abs(eps - np.sort([ma, mb])).max() < 1e-11
+    assert res.max() < 1e-9
+
+
+def test_richardson_step_damping_closed_form():
+    # one column phi_a + c phi_b with theta = mu_a: after n steps the phi_a
+    # part is unchanged and the phi_b part is c (1 - (mu_b - mu_a)/(lam - mu_a))^n
+    from oracle import certificate as oc
+    g, H, (pa, pb), (ma, mb) = _ho_pair()
+    lam, c = 40.0, 0.25
+    for n in (1, 3):
+        X = oc.richardson_smooth(H.apply, (pa + c * pb)[:, None], np.array([ma]), lam, n)[:, 0]
+        assert abs(g.dV * pa @ X - 1.0) < 1e-11
+        assert abs(g.dV * pb @ X - c * (1 - (mb - ma) / (lam - ma)) ** n) < 1e-11
+
+
+def test_smoothing_removes_high_energy_noise():
+    # rounding-like white noise on exact eigenvectors: the smoothed
+    # certificate's residuals are several times smaller and its Ritz values
+    # stay on the exact eigenvalues
+    from oracle import certificate as oc
+    g, H, (pa, pb), (ma, mb) = _ho_pair()
+    lam = oc.largest_eigenvalue(H.apply, g.npts)
+    rng = np.random.default_rng(3)
+    X = np.stack([pa, pb], axis=1)
+    X = X * (1 + 1e-7 * rng.uniform(-1, 1, X.shape))
+    e0, r0, _ = oc.ritz_certificate(H.apply, X, g.dV)
+    e4, r4, _ = oc.smoothed_certificate(H.apply, X, np.array([ma, mb]), lam, 4, g.dV)
+    assert r4.max() < r0.max() / 4
+    assert np.abs(e4 - [ma, mb]).max() < 1e-12
+
+
+def test_largest_eigenvalue_against_dense():
+    from oracle import certificate as oc
+    atoms = np.array([[0.0, 0.0, 0.0], [1.8, 0.0, 0.0]])
+    g = og.sphere_union_grid(atoms, 2.5, 0.6)
+    pr = oh.make_projectors(g, atoms, np.array([[1.0, 0.8], [1.5, 0.6]]), 1.0, 3.0)
+    H = oh.Hamiltonian(g, wl.local_potential(g.coords, atoms), pr)
+    assert abs(oc.largest_eigenvalue(H.apply, g.npts) - np.linalg.eigvalsh(H.dense())[-1]) < 1e-9

@@ -317,6 +317,78 @@ def test_certificate_bounds_the_error_against_the_oracle():
     assert np.all(err <= bound + 1e-12), (err.max(), bound.max())
 
 
+def test_smoothed_certificate_matches_oracle():
+    """rs_solver_certify_smoothed against the oracle's certificate on the
+    same FP32 orbitals (widened exactly), the same eigenvalue estimates and
+    the same lambda_max: Ritz values to 1e-10 Ha and residual norms to 1e-6
+    relative, unsmoothed (0 steps) and after 3 Richardson steps."""
+    from oracle import certificate as oc
+    from paper_1306_2953_gb300 import api
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).float().cuda(), w.block, 1e-4)
+    for _ in range(25):
+        eps, _, _ = S.step()
+    theta = eps.cpu().numpy()
+    psi = np.zeros((g_ora.npts, w.n_states))
+    psi[idx] = S.psi().double().cpu().numpy()
+    lam = 75.0   # above the largest eigenvalue of H (70.65 Ha)
+    for n in (0, 3):
+        e_g, r_g = S.certify_smoothed(n, lam)
+        e_o, r_o, _ = oc.smoothed_certificate(H_ora.apply, psi, theta, lam, n, g_ora.dV)
+        e_g, r_g = e_g.cpu().numpy(), r_g.cpu().numpy()
+        assert np.abs(e_g - e_o).max() <= 1e-10, n
+        assert np.abs(r_g - r_o).max() <= 1e-6 * r_o.max(), n
+    # the library's own estimate of lambda_max: a lower bound within 2 %
+    S.certify_smoothed(1)
+    lam_est = S.stats()["lambda_max"]
+    lam_true = oc.largest_eigenvalue(H_ora.apply, g_ora.npts)
+    assert 0.98 * lam_true <= lam_est <= lam_true + 1e-9, (lam_est, lam_true)
+
+
+def test_smoothed_certificate_tightens_the_mixed_bound():
+    """On the converged mixed solve of the 20-atom molecule, four FP64
+    smoothing steps cut the largest residual norm at least threefold (the
+    FP32 rounding noise of the orbitals), the Ritz values stay within 1e-6 Ha
+    of the oracle's eigenvalues, and the tighter bound still covers every
+    state's actual error."""
+    from paper_1306_2953_gb300 import api
+    w = wl.MOL20
+    lg, H, g_ora, H_ora, idx = _system(w)
+    ref = np.array(golden(w.name)["eigenvalues"])
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]
+    # a tolerance below the FP32 floor keeps every block iterating
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).float().cuda(), w.block, 1e-8,
+                   n_wanted=len(ref), **SCHEDULE)
+    _solve_to_golden(S, ref, 1e-6, 400)
+    for _ in range(60):   # into the FP32 noise floor
+        S.step()
+    e0, r0 = (t.cpu().numpy() for t in S.certify())
+    e4, r4 = (t.cpu().numpy() for t in S.certify_smoothed(4))
+    k = len(ref)
+    assert r4[:k].max() <= r0[:k].max() / 3, (r0[:k].max(), r4[:k].max())
+    err = np.abs(e4[:k] - ref)
+    assert err.max() <= 1e-6
+    bound = certificate_bound(e4, r4)[:k]
+    assert np.all(err <= bound + 1e-12), (err.max(), bound.max())
+    assert bound.max() <= certificate_bound(e0, r0)[:k].max()
+
+
+def test_smoothed_certificate_rejects_bad_arguments():
+    from paper_1306_2953_gb300 import api
+    from paper_1306_2953_gb300._lib import RsError
+    w = wl.HO32
+    lg, H, g_ora, H_ora, idx = _system(w)
+    psi0 = wl.random_block(g_ora.npts, w.n_states, w.seed)[idx]
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).cuda(), w.block, 1e-6)
+    eps, _, _ = S.step()
+    below_top = float(eps.cpu().numpy().min())   # positive, and below the largest current eigenvalue
+    for n, lam in ((-1, 0.0), (17, 0.0), (2, below_top), (2, float("nan"))):
+        with pytest.raises(RsError):
+            S.certify_smoothed(n, lam)
+
+
 def test_rmm_diis_steps_match_oracle_f64():
     """The paper's eigensolver (RMM-DIIS) on the GPU against the oracle's own
     RMM-DIIS from the same start vectors, sweep by sweep (same definition,
