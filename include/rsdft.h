@@ -646,7 +646,10 @@ int rs_scf_create(rs_solver *s, const rs_grid *g, const double *v_ext_host, cons
 /* One SCF step; residual = ||n_out - n_in|| (grid norm, before mixing) and
  * energy = the Mermin free energy sum f eps - E_H - int n v_xc + E_xc
  * - sigma S of the step's input density (ion-ion repulsion omitted), both
- * may be NULL.  Blocking.  Errors: RS_ENAN, and the solver's. */
+ * may be NULL.  With an RS_F32 solver the eigenvalues eps that set the
+ * occupations and the band energy are those of rs_solver_rayleigh_ritz_f64
+ * (FP64 H), taken every step.  Blocking.  Errors: RS_ENAN, and the
+ * solver's. */
 int rs_scf_step(rs_scf *scf, double *residual, double *energy, void *stream);
 
 /* Current input density (device double [npts], may be NULL), the last

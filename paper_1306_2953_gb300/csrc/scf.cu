@@ -157,7 +157,7 @@ struct rs_scf {
     rs_scf_cfg cfg{};
     int64_t np = 0;
     double dV = 0;
-    rs::DevBuf vext, n_in, n_out, F, vh, vxc, exc, veff, fdev, prev_n, prev_F, hist, dots;
+    rs::DevBuf vext, n_in, n_out, F, vh, vxc, exc, veff, fdev, prev_n, prev_F, hist, dots, eps64;
     std::vector<int> order;    // history slots, oldest first
     bool have_prev = false;
     std::vector<double> f;
@@ -225,11 +225,20 @@ extern "C" int rs_scf_step(rs_scf *S, double *residual, double *energy, void *st
     RS_LAUNCH_CHECK();
     RS_TRY(rs_solver_set_potential(S->s, S->veff.as<double>(), st));
     for (int k = 0; k < c.sweeps; ++k) RS_TRY(rs_eigensolver_step(S->s, nullptr, nullptr, nullptr, st));
-    // occupations (host bisection on the eigenvalues) and the output density
+    // occupations (host bisection on the eigenvalues) and the output density;
+    // FP32 solvers: the eigenvalues of the FP64 Rayleigh-Ritz of their
+    // subspace (H applied in FP64), so that the occupations and the band
+    // energy carry no FP32 rounding of H
     rs::SolverView v;
     rs::solver_view(S->s, &v);
+    const double *eig = v.eig;
+    if (v.dtype == RS_F32) {
+        if (!S->eps64.p) RS_TRY(S->eps64.alloc(sizeof(double) * v.nst));
+        RS_TRY(rs_solver_rayleigh_ritz_f64(S->s, S->eps64.as<double>(), st));
+        eig = S->eps64.as<double>();
+    }
     std::vector<double> eps(v.nst);
-    RS_CUDA(cudaMemcpyAsync(eps.data(), v.eig, sizeof(double) * v.nst, cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaMemcpyAsync(eps.data(), eig, sizeof(double) * v.nst, cudaMemcpyDeviceToHost, st));
     RS_CUDA(cudaStreamSynchronize(st));
     const double emin = *std::min_element(eps.begin(), eps.end()), emax = *std::max_element(eps.begin(), eps.end());
     auto fd = [&](double mu, std::vector<double> &f) {

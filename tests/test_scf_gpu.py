@@ -50,12 +50,15 @@ def test_scf_two_atoms_matches_oracle():
     assert np.abs(occ - scf_o.f).max() <= 1e-7
 
 
-def test_scf_mol20_matches_oracle_golden():
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_scf_mol20_matches_oracle_golden(dtype):
     """The 20-atom molecule made self-consistent (80 electrons, 64 states,
     three block-CG sweeps per step) from the atomic-Gaussian start: the GPU
     reaches the oracle's residual bar and the eigenvalues of its states with
     occupation above 0.01, and its free energy, agree with the oracle's
-    self-consistent ones within the self-consistency error (1e-5 Ha)."""
+    self-consistent ones within the self-consistency error (1e-5 Ha), in
+    FP64 and in mixed precision (FP32 orbitals and H psi, eigenvalues of the
+    FP64 Rayleigh-Ritz)."""
     from paper_1306_2953_gb300 import api
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "scf_scf_mol20_h0.35.json")
     gold = json.load(open(path))
@@ -70,7 +73,8 @@ def test_scf_mol20_matches_oracle_golden():
     g_ora = og.sphere_union_grid(atoms, s.radius, s.h)
     idx = lib_to_oracle_index(g_ora, lg.ijk())
     psi0 = wl.random_block(g_ora.npts, spec.n_states, spec.base.seed)[idx]
-    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).cuda(), spec.block, 1e-10)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    S = api.Solver(H, torch.from_numpy(np.ascontiguousarray(psi0)).to(tdt).cuda(), spec.block, 1e-10)
     scf = api.SCF(S, lg, vext, wl.atomic_density_guess(coords, atoms, spec.n_electrons, lg.dV), spec.n_electrons,
                   sigma=spec.sigma, alpha=spec.alpha, history=spec.history, sweeps=spec.sweeps)
     for _ in range(300):
@@ -79,7 +83,8 @@ def test_scf_mol20_matches_oracle_golden():
             break
     assert r < spec.tol
     _, occ, _, _ = scf.state()
-    eps = S.step()[0].cpu().numpy()
+    S.step()
+    eps = S.rayleigh_ritz_f64().cpu().numpy()
     occupied = np.array(gold["occupations"]) > 1e-2
     assert np.abs(eps[occupied] - np.array(gold["eigenvalues"])[occupied]).max() <= 1e-5
     assert abs(e - gold["energy"]) <= 1e-5
