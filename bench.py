@@ -464,7 +464,7 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
                               "solver_create_seconds": t_create, "certificates": certs, "trajectory": traj,
                               "train_seconds": st["train_target_seconds"] + st["train_fit_seconds"],
                               "filter_fallback_after_sweep": st["fallback_sweep"] or None,
-                              "lambda_max_estimate": st["lambda_max"] or None,
+                              "lambda_max_estimate": S.stats()["lambda_max"] or None,
                               "eigenvalues_head": [float(x) for x in e[:8]] if certs else None}
         if certs and n_smooth > 0 and "error" not in certs[-1]:
             # outside the timed region: the same subspace certified without
