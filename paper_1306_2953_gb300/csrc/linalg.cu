@@ -204,7 +204,8 @@ template int rowmul<float>(const float *, int64_t, int, const double *, int64_t,
 // upper triangle receives U with A = U^T U, the strict lower triangle is
 // zeroed.  status[0] = 0, or j+1 if pivot j is not finite or not larger
 // than rel * (original A_jj).  One CTA; the matrix is worked on in shared
-// memory when it fits (IN_SMEM), else in global memory (L1/L2 resident).
+// memory when it fits (IN_SMEM, the path cholesky takes up to
+// CHOL_SMEM_MAX), else in global memory (L1/L2 resident).
 // Rows are spread over warps and columns over lanes, so no index division.
 constexpr int CHOL_MAX = 2048;
 constexpr int CHOL_SMEM_MAX = 160;   // n x n FP64 in 200 KB
@@ -312,15 +313,125 @@ int gemm_small(int m, int n, int k, double alpha, const double *A, int lda, bool
     return RS_OK;
 }
 
+// Blocked right-looking Cholesky for n > CHOL_SMEM_MAX, block rows of
+// CHOL_NB.  The original diagonal, which the pivot test compares against,
+// is kept in column 0 of the strict lower triangle (A[j][0], j >= 1: never
+// inside a trailing block, and zeroed at the end with the rest of the lower
+// triangle).  Per block row k: the diagonal block is factored in shared
+// memory (k_chol_diag), the panel U[k][rest] = U_kk^-T A[k][rest] is solved
+// by forward substitution, one thread per column (k_chol_panel), and the
+// trailing matrix takes A[rest][rest] -= U[k][rest]^T U[k][rest]
+// (k_gemm_small; the full square, of which only the upper triangle is read
+// later).  status[0] = j+1 of the first failing pivot j; once it is set the
+// later diagonal and panel kernels return at once.
+constexpr int CHOL_NB = 64;
+
+__global__ void k_chol_save_diag(double *A, int lda, int n) {
+    for (int j = 1 + blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        A[(int64_t)j * lda] = A[(int64_t)j * lda + j];
+}
+
+// factor the bk x bk diagonal block at (k, k) in shared memory
+__global__ void __launch_bounds__(1024) k_chol_diag(double *Ag, int lda, int k, int bk, double rel, int *status) {
+    __shared__ double A[CHOL_NB * CHOL_NB];
+    __shared__ double piv;
+    __shared__ int bad;
+    if (*(volatile int *)status) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    double *blk = Ag + (int64_t)k * lda + k;
+    for (int r = warp; r < bk; r += nw)
+        for (int c = lane; c < bk; c += 32) A[r * bk + c] = blk[(int64_t)r * lda + c];
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < bk; ++j) {
+        if (tid == 0) {
+            const int g = k + j;
+            const double d0 = g == 0 ? A[0] : Ag[(int64_t)g * lda];   // original diagonal (saved)
+            const double d = A[j * bk + j];
+            if (!isfinite(d) || !(d > 0.0) || !(d > rel * d0)) {
+                bad = g + 1;
+                piv = 1.0;
+            } else {
+                piv = sqrt(d);
+            }
+            A[j * bk + j] = piv;
+        }
+        __syncthreads();
+        if (bad) break;
+        const double inv = 1.0 / piv;
+        double *uj = A + j * bk;
+        for (int c = j + 1 + tid; c < bk; c += blockDim.x) uj[c] *= inv;
+        __syncthreads();
+        for (int r = j + 1 + warp; r < bk; r += nw) {
+            const double ujr = uj[r];
+            for (int c = r + lane; c < bk; c += 32) A[r * bk + c] -= ujr * uj[c];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) atomicCAS(status, 0, bad);
+        return;
+    }
+    for (int r = warp; r < bk; r += nw)
+        for (int c = r + lane; c < bk; c += 32) blk[(int64_t)r * lda + c] = A[r * bk + c];
+}
+
+// panel: rows k..k+bk-1, columns c >= k+bk, x = U_kk^-T a by forward
+// substitution, x_i = (a_i - sum_{l<i} U_li x_l) / U_ii, in place
+__global__ void __launch_bounds__(128) k_chol_panel(double *Ag, int lda, int n, int k, int bk, const int *status) {
+    __shared__ double U[CHOL_NB * CHOL_NB];
+    if (*(volatile const int *)status) return;
+    const int tid = threadIdx.x;
+    const double *blk = Ag + (int64_t)k * lda + k;
+    for (int e = tid; e < bk * bk; e += blockDim.x) U[e] = blk[(int64_t)(e / bk) * lda + e % bk];
+    __syncthreads();
+    const int c = k + bk + blockIdx.x * blockDim.x + tid;
+    if (c >= n) return;
+    double *col = Ag + (int64_t)k * lda + c;
+    double x[CHOL_NB];   // the column's solution, in registers (fully unrolled loops)
+#pragma unroll
+    for (int i = 0; i < CHOL_NB; ++i) {
+        if (i < bk) {
+            double t = col[(int64_t)i * lda];
+#pragma unroll
+            for (int l = 0; l < i; ++l) t -= U[l * bk + i] * x[l];
+            t /= U[i * bk + i];
+            x[i] = t;
+            col[(int64_t)i * lda] = t;
+        }
+    }
+}
+
+__global__ void k_zero_lower(double *A, int lda, int n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), c = (int)(e % n);
+        if (c < r) A[(int64_t)r * lda + c] = 0.0;
+    }
+}
+
 int cholesky(double *A, int lda, int n, double rel, int *status_dev, cudaStream_t st) {
-    if (n > CHOL_MAX) return fail(RS_EINVAL, "cholesky: n > %d", CHOL_MAX);
     if (n <= CHOL_SMEM_MAX) {
         const size_t sm = sizeof(double) * (size_t)n * n;
         RS_TRY(smem_optin((const void *)k_chol<true>, sm));
         k_chol<true><<<1, 1024, sm, st>>>(A, lda, n, rel, status_dev);
-    } else {
-        k_chol<false><<<1, 1024, 0, st>>>(A, lda, n, rel, status_dev);
+        RS_LAUNCH_CHECK();
+        return RS_OK;
     }
+    RS_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int), st));
+    k_chol_save_diag<<<(n + 255) / 256, 256, 0, st>>>(A, lda, n);
+    RS_LAUNCH_CHECK();
+    for (int k = 0; k < n; k += CHOL_NB) {
+        const int bk = std::min(CHOL_NB, n - k), m = n - k - bk;
+        k_chol_diag<<<1, 1024, 0, st>>>(A, lda, k, bk, rel, status_dev);
+        RS_LAUNCH_CHECK();
+        if (m == 0) break;
+        k_chol_panel<<<(m + 127) / 128, 128, 0, st>>>(A, lda, n, k, bk, status_dev);
+        RS_LAUNCH_CHECK();
+        double *Xk = A + (int64_t)k * lda + k + bk, *C = A + (int64_t)(k + bk) * lda + k + bk;
+        RS_TRY(gemm_small(m, m, bk, -1.0, Xk, lda, true, Xk, lda, false, 1.0, C, lda, st));
+    }
+    k_zero_lower<<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(A, lda, n);
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
@@ -362,11 +473,26 @@ int symmetrize(double *A, int lda, int n, cudaStream_t st) {
 // Matrices whose packed triangle fits one CTA's shared memory use
 // k_jacobi_pk below; larger ones the cooperative multi-CTA k_jacobi_grid.
 
-// Multi-CTA variant for matrices too large for one CTA's shared memory: the
-// same rounds, with every CTA computing all rotations of a round redundantly,
-// rows split by rotation pair and columns split by row, and a software grid
-// barrier (bounded spin; on timeout err[0] is set and every CTA returns).
-// All CTAs must be resident (launched cooperatively).
+// Multi-CTA variant for matrices too large for one CTA's shared memory
+// (cooperative launch: every CTA resident).  A and V stay in global memory
+// (L2-resident).  A round has three parts:
+//  - Every CTA computes all n/2 rotations of the round.  Their inputs (the
+//    diagonal and the pivot entries A[p_k][q_k]) come from a compact buffer
+//    that the previous round wrote.
+//  - Each warp takes whole units.  An A unit is a pair of rows (p_k, q_k),
+//    rotated as rows by (c_k, s_k) and as columns by every (c_l, s_l) in the
+//    warp's shared memory (row and column rotations commute in J^T A J).  A
+//    V unit is a pair of rows of V, rotated as columns only.  A unit's loads
+//    and stores are whole coalesced rows.  The A unit that owns row x also
+//    writes the next round's inputs from x: its diagonal entry, and its
+//    entry in the next round's pivot if x is that pair's p.  These go to the
+//    other half of the double-buffered input, so one grid barrier per round
+//    suffices.
+//  - A software grid barrier (bounded spin; on timeout err[0] is set and
+//    every CTA returns).
+// FP32 rotates A - sigma I, sigma the mean of the diagonal (the same
+// eigenvectors): its rounding and stopping test then scale with the spread
+// of the spectrum, not its offset.
 constexpr long long GRID_SPIN_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks, int *err) {
@@ -395,113 +521,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned 
     return *(volatile int *)err == 0;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_jacobi_grid(T *A, T *V, int n, int max_sweeps, double tol, double *w,
-                                                     double *Vout, int ldv, int *info, unsigned *bar, double *red_g,
-                                                     int *err) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *cs = reinterpret_cast<T *>(smraw);
-    T *sn = cs + n / 2;
-    int *pp = reinterpret_cast<int *>(sn + n / 2);
-    int *qq = pp + n / 2;
-    __shared__ double red[8];
-    const int tid = threadIdx.x, nt = blockDim.x, G = gridDim.x, bid = blockIdx.x;
-    const int h = n / 2, m = n - 1;
-    unsigned *count = bar;
-    volatile unsigned *gen = bar + 1;
-    for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)n * n; e += (int64_t)G * nt) V[e] = (e / n == e % n) ? T(1) : T(0);
-    auto block_sum = [&](double v) -> double {
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) red[tid >> 5] = v;
-        __syncthreads();
-        double t = 0;
-        if (tid == 0)
-            for (int i = 0; i < nt / 32; ++i) t += red[i];
-        __syncthreads();
-        return t;
-    };
-    // Frobenius norm (red_g[0]) and off-diagonal sums per sweep (red_g[1 + sweep])
-    double loc = 0;
-    for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)n * n; e += (int64_t)G * nt) loc += (double)__ldcg(A + e) * (double)__ldcg(A + e);
-    const double f = block_sum(loc);
-    if (tid == 0) atomicAdd(red_g, f);
-    if (!grid_barrier(count, gen, G, err)) return;
-    const double fro2 = *(volatile double *)red_g;
-    int sweep = 0, done = 0;
-    for (; sweep < max_sweeps; ++sweep) {
-        loc = 0;
-        for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)n * n; e += (int64_t)G * nt)
-            if (e / n != e % n) loc += (double)__ldcg(A + e) * (double)__ldcg(A + e);
-        const double o = block_sum(loc);
-        if (tid == 0) atomicAdd(red_g + 1 + sweep, o);
-        if (!grid_barrier(count, gen, G, err)) return;
-        if (*(volatile double *)(red_g + 1 + sweep) <= tol * tol * fro2) {
-            done = 1;
-            break;
-        }
-        for (int r = 0; r < m; ++r) {
-            for (int k = tid; k < h; k += nt) {
-                int p, q;
-                if (k == 0) {
-                    p = 0;
-                    q = 1 + r % m;
-                } else {
-                    p = 1 + (r + k) % m;
-                    q = 1 + (r - k + m) % m;
-                }
-                const T apq = __ldcg(A + (int64_t)p * n + q);
-                T c = 1, s_ = 0;
-                if (apq != T(0)) {
-                    const T theta = (__ldcg(A + (int64_t)q * n + q) - __ldcg(A + (int64_t)p * n + p)) / (T(2) * apq);
-                    const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-                    c = T(1) / sqrt(t * t + T(1));
-                    s_ = t * c;
-                }
-                cs[k] = c;
-                sn[k] = s_;
-                pp[k] = p;
-                qq[k] = q;
-            }
-            __syncthreads();
-            if (!grid_barrier(count, gen, G, err)) return;   // every CTA has read the round's pivots
-            // rows: pairs split over CTAs
-            for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)h * n; e += (int64_t)G * nt) {
-                const int k = (int)(e / n), j = (int)(e % n);
-                const int p = pp[k], q = qq[k];
-                const T c = cs[k], s_ = sn[k];
-                const T a = __ldcg(A + (int64_t)p * n + j), b = __ldcg(A + (int64_t)q * n + j);
-                A[(int64_t)p * n + j] = c * a - s_ * b;
-                A[(int64_t)q * n + j] = s_ * a + c * b;
-            }
-            if (!grid_barrier(count, gen, G, err)) return;
-            // columns of A and V: rows split over CTAs
-            for (int64_t e = bid * (int64_t)nt + tid; e < (int64_t)h * n; e += (int64_t)G * nt) {
-                const int i = (int)(e / h), k = (int)(e % h);
-                const int p = pp[k], q = qq[k];
-                const T c = cs[k], s_ = sn[k];
-                const T a = __ldcg(A + (int64_t)i * n + p), b = __ldcg(A + (int64_t)i * n + q);
-                A[(int64_t)i * n + p] = c * a - s_ * b;
-                A[(int64_t)i * n + q] = s_ * a + c * b;
-                const T va = __ldcg(V + (int64_t)i * n + p), vb = __ldcg(V + (int64_t)i * n + q);
-                V[(int64_t)i * n + p] = c * va - s_ * vb;
-                V[(int64_t)i * n + q] = s_ * va + c * vb;
-            }
-            if (!grid_barrier(count, gen, G, err)) return;
-        }
-    }
-    // ascending order (ties by index), outputs split over CTAs
-    for (int i = bid * nt + tid; i < n; i += G * nt) {
-        const T di = __ldcg(A + (int64_t)i * n + i);
-        int rk = 0;
-        for (int j = 0; j < n; ++j) {
-            const T dj = __ldcg(A + (int64_t)j * n + j);
-            rk += (dj < di) || (dj == di && j < i);
-        }
-        w[rk] = (double)di;
-        for (int k = 0; k < n; ++k) Vout[(int64_t)k * ldv + rk] = (double)__ldcg(V + (int64_t)k * n + i);
-    }
-    if (bid == 0 && tid == 0) info[0] = done ? sweep : -1;
-}
 
 // Single-CTA cyclic Jacobi with the matrix held in shared memory as its
 // packed upper triangle (n (n+1)/2 elements), for n up to a few hundred.  A
@@ -549,6 +568,200 @@ template <typename T> __device__ __forceinline__ void jacobi_cs(T app, T aqq, T 
     }
     c = r;
     s = t * r;
+}
+
+// shared memory of k_jacobi_grid ahead of its row buffers: (c, s) and
+// (p, q) of the n/2 rotations, 16-byte aligned
+__host__ __device__ inline size_t jacobi_grid_head_bytes(int n, size_t es) {
+    const size_t h = n / 2;
+    return (2 * h * es + 2 * h * sizeof(int) + 15) / 16 * 16;
+}
+
+// slot of index x in round r of the circle ordering: pair k and whether x
+// is that pair's p (x = p_k) or q (x = q_k)
+__device__ __forceinline__ void circle_slot(int x, int r, int m, int h, int &k, bool &is_p) {
+    if (x == 0) {
+        k = 0;
+        is_p = true;
+        return;
+    }
+    const int y = x - 1, rr = r % m;
+    if (y == rr) {
+        k = 0;
+        is_p = false;
+        return;
+    }
+    const int d = ((y - rr) % m + m) % m;   // 1 .. m-1
+    if (d <= h - 1) {
+        k = d;
+        is_p = true;
+    } else {
+        k = m - d;
+        is_p = false;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_jacobi_grid(T *A, T *V, int n, int max_sweeps, double tol, double *w,
+                                                     double *Vout, int ldv, int *info, unsigned *bar, double *red_g,
+                                                     int *err, T *pivots) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int h = n / 2, m = n - 1;
+    T *cs = reinterpret_cast<T *>(smraw);
+    T *sn = cs + h;
+    int *pp = reinterpret_cast<int *>(sn + h);
+    int *qq = pp + h;
+    const int tid = threadIdx.x, nt = blockDim.x, G = gridDim.x, bid = blockIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, W = nt >> 5;
+    T *r0 = reinterpret_cast<T *>(smraw + jacobi_grid_head_bytes(n, sizeof(T))) + (size_t)warp * 2 * n;
+    T *r1 = r0 + n;
+    // round inputs, two halves of (diagonal [n], pivots [h])
+    auto diag_of = [&](int half) { return pivots + (size_t)half * (n + h); };
+    auto piv_of = [&](int half) { return pivots + (size_t)half * (n + h) + n; };
+    __shared__ double red[8];
+    unsigned *count = bar;
+    volatile unsigned *gen = bar + 1;
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        double t = 0;
+        if (tid == 0)
+            for (int i = 0; i < W; ++i) t += red[i];
+        __syncthreads();
+        return t;
+    };
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t e = bid * (int64_t)nt + tid; e < nn; e += (int64_t)G * nt) V[e] = (e / n == e % n) ? T(1) : T(0);
+    // the shift (FP32): mean of the diagonal, in red_g[max_sweeps + 1]
+    double shift = 0;
+    if constexpr (sizeof(T) == 4) {
+        double d = 0;
+        for (int i = bid * nt + tid; i < n; i += G * nt) d += (double)__ldcg(A + (int64_t)i * n + i);
+        const double t = block_sum(d);
+        if (tid == 0) atomicAdd(red_g + max_sweeps + 1, t);
+        if (!grid_barrier(count, gen, G, err)) return;
+        shift = *(volatile double *)(red_g + max_sweeps + 1) / n;
+    }
+    // shifted diagonal, Frobenius norm (red_g[0]) and round 0's inputs
+    double loc = 0;
+    for (int64_t e = bid * (int64_t)nt + tid; e < nn; e += (int64_t)G * nt) {
+        T x = __ldcg(A + e);
+        const int i = (int)(e / n);
+        if (i == (int)(e % n)) {
+            x = (T)((double)x - shift);
+            A[e] = x;
+            diag_of(0)[i] = x;
+        }
+        loc += (double)x * (double)x;
+    }
+    for (int k = bid * nt + tid; k < h; k += G * nt) {
+        int p, q;
+        circle_pair(0, k, m, p, q);
+        piv_of(0)[k] = __ldcg(A + (int64_t)p * n + q);
+    }
+    {
+        const double f = block_sum(loc);
+        if (tid == 0) atomicAdd(red_g, f);
+    }
+    if (!grid_barrier(count, gen, G, err)) return;
+    const double fro2 = *(volatile double *)red_g;
+    int sweep = 0, done = 0;
+    int64_t t = 0;   // rounds taken: round t reads half t % 2 of the inputs and writes the other
+    for (; sweep < max_sweeps; ++sweep) {
+        loc = 0;
+        for (int64_t e = bid * (int64_t)nt + tid; e < nn; e += (int64_t)G * nt)
+            if (e / n != e % n) loc += (double)__ldcg(A + e) * (double)__ldcg(A + e);
+        const double o = block_sum(loc);
+        if (tid == 0) atomicAdd(red_g + 1 + sweep, o);
+        if (!grid_barrier(count, gen, G, err)) return;
+        if (*(volatile double *)(red_g + 1 + sweep) <= tol * tol * fro2) {
+            done = 1;
+            break;
+        }
+        for (int r = 0; r < m; ++r, ++t) {
+            const int cur = (int)(t & 1), nxt = cur ^ 1;
+            const T *dg = diag_of(cur), *pv = piv_of(cur);
+            for (int k = tid; k < h; k += nt) {
+                int p, q;
+                circle_pair(r, k, m, p, q);
+                T c, s_;
+                jacobi_cs(__ldcg(dg + p), __ldcg(dg + q), __ldcg(pv + k), c, s_);
+                cs[k] = c;
+                sn[k] = s_;
+                pp[k] = p;
+                qq[k] = q;
+            }
+            __syncthreads();
+            const int rn = (r + 1) % m;   // the next round (round 0 of the next sweep after the last)
+            for (int u = bid * W + warp; u < 2 * h; u += G * W) {
+                const bool is_a = u < h;
+                const int p = is_a ? pp[u] : 2 * (u - h), q = is_a ? qq[u] : 2 * (u - h) + 1;
+                T *x0 = (is_a ? A : V) + (int64_t)p * n, *x1 = (is_a ? A : V) + (int64_t)q * n;
+                if (is_a) {
+                    const T c = cs[u], s_ = sn[u];
+                    for (int j = lane; j < n; j += 32) {
+                        const T a = __ldcg(x0 + j), b = __ldcg(x1 + j);
+                        r0[j] = c * a - s_ * b;
+                        r1[j] = s_ * a + c * b;
+                    }
+                } else {
+                    for (int j = lane; j < n; j += 32) {
+                        r0[j] = __ldcg(x0 + j);
+                        r1[j] = __ldcg(x1 + j);
+                    }
+                }
+                __syncwarp();
+                for (int l = lane; l < h; l += 32) {
+                    const int P = pp[l], Q = qq[l];
+                    const T c = cs[l], s_ = sn[l];
+                    T a = r0[P], b = r0[Q];
+                    r0[P] = c * a - s_ * b;
+                    r0[Q] = s_ * a + c * b;
+                    a = r1[P];
+                    b = r1[Q];
+                    r1[P] = c * a - s_ * b;
+                    r1[Q] = s_ * a + c * b;
+                }
+                __syncwarp();
+                if (is_a && lane == 0) {
+                    r0[q] = T(0);   // the annihilated pivot
+                    r1[p] = T(0);
+                    for (int side = 0; side < 2; ++side) {
+                        const int x = side ? q : p;
+                        const T *rx = side ? r1 : r0;
+                        diag_of(nxt)[x] = rx[x];
+                        int k2, p2, q2;
+                        bool is_p;
+                        circle_slot(x, rn, m, h, k2, is_p);
+                        if (is_p) {
+                            circle_pair(rn, k2, m, p2, q2);
+                            piv_of(nxt)[k2] = rx[q2];
+                        }
+                    }
+                }
+                __syncwarp();
+                for (int j = lane; j < n; j += 32) {
+                    x0[j] = r0[j];
+                    x1[j] = r1[j];
+                }
+                __syncwarp();
+            }
+            if (!grid_barrier(count, gen, G, err)) return;
+        }
+    }
+    // ascending order (ties by index), outputs split over CTAs
+    for (int i = bid * nt + tid; i < n; i += G * nt) {
+        const T di = __ldcg(A + (int64_t)i * n + i);
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const T dj = __ldcg(A + (int64_t)j * n + j);
+            rk += (dj < di) || (dj == di && j < i);
+        }
+        w[rk] = (double)di + shift;
+        for (int k = 0; k < n; ++k) Vout[(int64_t)k * ldv + rk] = (double)__ldcg(V + (int64_t)k * n + i);
+    }
+    if (bid == 0 && tid == 0) info[0] = done ? sweep : -1;
 }
 
 template <typename T>
@@ -889,7 +1102,8 @@ size_t jacobi_log_elems(int n, int max_sweeps) { return 2 * (size_t)max_sweeps *
 size_t jacobi_scratch_bytes(int n, int max_sweeps, size_t es) {
     if (jacobi_pk_smem(n, es) <= JACOBI_PK_MAX_SMEM)
         return es * jacobi_log_elems(n, max_sweeps) + sizeof(int) * (size_t)n + 64;
-    return 2 * es * (size_t)n * n + 16 + sizeof(double) * ((size_t)max_sweeps + 2) + 16 + 64;
+    return 2 * es * (size_t)n * n + 16 + sizeof(double) * ((size_t)max_sweeps + 2) + 16 + 2 * es * ((size_t)n + n / 2) +
+           64;
 }
 
 // FP64 -> T copy of an n x n matrix into a dense buffer
@@ -927,19 +1141,28 @@ int jacobi(const double *A, int lda, int n, int max_sweeps, double tol, double *
     T *v = a + (size_t)n * n;
     k_copy_cast<T><<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(A, lda, n, a);
     RS_LAUNCH_CHECK();
-    const size_t small = (size_t)n * sizeof(T) + (size_t)n * 3 * sizeof(int) + 64;
-    // grid variant: barrier words, reduction slots and the error flag follow V in the scratch
+    // grid variant: barrier words, reduction slots, the error flag and the
+    // double-buffered round inputs follow V in the scratch
     unsigned *bar = reinterpret_cast<unsigned *>(v + (size_t)n * n);
     double *red_g = reinterpret_cast<double *>(bar + 4);
     int *err = reinterpret_cast<int *>(red_g + max_sweeps + 2);
+    T *pivots = reinterpret_cast<T *>(reinterpret_cast<char *>(err) + 16);
     RS_CUDA(cudaMemsetAsync(bar, 0, 16 + sizeof(double) * (max_sweeps + 2) + 16, st));
+    // row buffers: two rows of n per warp, at most 8 warps, within 200 KB
+    const size_t head = jacobi_grid_head_bytes(n, sizeof(T)), per_warp = 2 * (size_t)n * sizeof(T);
+    const int W = (int)std::min<size_t>(8, (200 * 1024 - head) / per_warp);
+    if (W < 1) return fail(RS_EINVAL, "jacobi: order %d too large for the multi-CTA variant", n);
+    const size_t smem = head + (size_t)W * per_warp;
+    RS_TRY(smem_optin((const void *)k_jacobi_grid<T>, smem));
     int nsm = 0, dev = 0, per_sm = 0;
     RS_CUDA(cudaGetDevice(&dev));
     RS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_grid<T>, 256, small));
-    const int G = std::max(1, std::min({n / 2, nsm * std::max(per_sm, 1), 128}));
-    void *args[] = {&a, &v, &n, &max_sweeps, &tol, &w, &V, &ldv, &info, &bar, &red_g, &err};
-    RS_CUDA(cudaLaunchCooperativeKernel((const void *)k_jacobi_grid<T>, dim3(G), dim3(256), args, small, st));
+    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_grid<T>, 32 * W, smem));
+    if (per_sm < 1) return fail(RS_ECUDA, "jacobi: the multi-CTA variant cannot be resident");
+    // one unit (a row pair of A or of V) per warp and round
+    const int G = std::max(1, std::min(nsm * per_sm, (n + W - 1) / W));
+    void *args[] = {&a, &v, &n, &max_sweeps, &tol, &w, &V, &ldv, &info, &bar, &red_g, &err, &pivots};
+    RS_CUDA(cudaLaunchCooperativeKernel((const void *)k_jacobi_grid<T>, dim3(G), dim3(32 * W), args, smem, st));
     RS_LAUNCH_CHECK();
     return RS_OK;
 }

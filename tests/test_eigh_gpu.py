@@ -1,7 +1,8 @@
 """Dense symmetric eigensolver (the Rayleigh-Ritz diagonalisation of Sec. VI)
 on the GPU against the oracle's cyclic Jacobi, for the sizes the solver uses
-(one CTA in shared memory up to n = 160 in FP32 / 112 in FP64, the
-multi-CTA variant above) and all three modes.  FP64 modes: eigenvalues to
+(one CTA in shared memory while the packed triangle fits, about n = 330 in
+FP32 and 234 in FP64; the cooperative multi-CTA variant above, so 256 in
+FP64 and 400 and 1024 in both) and all three modes.  FP64 modes: eigenvalues to
 1e-12 of the spectral radius and A V = V diag(w) to 1e-11; FP32 Jacobi
 alone stops at its rounding floor: 1e-5 of the Frobenius norm."""
 import numpy as np
@@ -19,7 +20,7 @@ def _matrix(n, seed, spread=1.0):
     return (Q * w) @ Q.T
 
 
-@pytest.mark.parametrize("n", [16, 48, 96, 130, 192, 256])
+@pytest.mark.parametrize("n", [16, 48, 96, 130, 192, 256, 400])
 @pytest.mark.parametrize("refine", [2, 0, -1])
 def test_eigh_matches_oracle(n, refine):
     from oracle import linalg as ol
@@ -36,3 +37,18 @@ def test_eigh_matches_oracle(n, refine):
     else:
         assert np.abs(w - ref).max() <= 1e-12 * np.abs(ref).max()
         assert np.abs(A @ V - V * w).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_eigh_order_1024_refined():
+    """The order of the 300-atom subspace matrix (1024): the multi-CTA FP32
+    Jacobi, the FP64 refinement and the multi-CTA FP64 Jacobi of the
+    refined problem, against the library eigensolver (LAPACK through
+    numpy) of the same matrix."""
+    from paper_1306_2953_gb300 import api
+    A = _matrix(1024, 5, 60.0)
+    w, V = api.eigh(torch.from_numpy(A).cuda(), refine=2)
+    w, V = w.cpu().numpy(), V.cpu().numpy()
+    ref = np.linalg.eigvalsh(A)
+    assert np.abs(w - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(A @ V - V * w).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(V.T @ V - np.eye(1024)).max() <= 1e-12

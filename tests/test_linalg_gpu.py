@@ -53,8 +53,10 @@ def test_overlap_full_size_mol100_f32():
     assert np.abs(S - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("nst", [16, 48])
+@pytest.mark.parametrize("nst", [16, 48, 256, 400])
 def test_orthonormalize_parity_f64(nst):
+    """Up to 160 states the Cholesky runs in one CTA; above, blocked over
+    many (400: a ragged last block of 16 rows)."""
     from paper_1306_2953_gb300 import api
     from oracle import linalg as ol
     lg, H, g_ora, H_ora, idx = _lib_system(*SYS)
@@ -74,6 +76,22 @@ def test_orthonormalize_not_spd():
     lg, H, g_ora, H_ora, idx = _lib_system(*SYS)
     psi = wl.random_block(g_ora.npts, 8, 3)[idx]
     psi[:, 5] = psi[:, 2]            # linearly dependent columns
+    P = _dev(psi)
+    before = P.clone()
+    with pytest.raises(RsError) as e:
+        api.orthonormalize(lg, P)
+    assert e.value.code == RS_ENOTSPD
+    assert torch.equal(P, before)
+
+
+def test_orthonormalize_not_spd_blocked():
+    """A dependent column past the first block row of the blocked Cholesky
+    (state 250 of 300): RS_ENOTSPD and the orbitals untouched."""
+    from paper_1306_2953_gb300 import api
+    from paper_1306_2953_gb300._lib import RS_ENOTSPD, RsError
+    lg, H, g_ora, H_ora, idx = _lib_system(*SYS)
+    psi = wl.random_block(g_ora.npts, 300, 3)[idx]
+    psi[:, 250] = psi[:, 10]
     P = _dev(psi)
     before = P.clone()
     with pytest.raises(RsError) as e:
