@@ -613,6 +613,42 @@ def nb_sweep(workload, orders=(4,)):
     return 0
 
 
+def f64_hpsi(H, workload, nb=NB, steps=10):
+    """FP64 H psi, the paper's precision, on the benchmark's workload: all
+    states applied block by block (the generic fused kernel), timed with
+    CUDA events after three untimed steps.  Reported as algorithmic bytes
+    per second (rs_ham_apply_bytes in FP64) against the measured HBM copy
+    bandwidth, and as flops per second: per point-state 49 for the 25-point
+    stencil and 2 for the potential, plus per projector-sphere entry and
+    state 16 for the four projections and the four scatters."""
+    import torch
+    from paper_1306_2953_gb300 import _lib
+    nst = workload.n_states
+    psi = torch.from_numpy(wl.random_block(H.npts, nst, workload.seed)).cuda()
+    hpsi = torch.empty_like(psi)
+    na, ne = ctypes.c_int32(), ctypes.c_int64()
+    _lib.call("rs_proj_info", H.proj._h, ctypes.byref(na), ctypes.byref(ne))
+    for _ in range(3):
+        H.apply_all(psi, hpsi, nb=nb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        H.apply_all(psi, hpsi, nb=nb)
+    e1.record()
+    torch.cuda.synchronize()
+    if H.status() != 0:
+        raise RuntimeError("an H psi pipeline wait gave up during the FP64 timing")
+    s_per_step = e0.elapsed_time(e1) * 1e-3 / steps
+    by = H.apply_bytes(nb, _lib.RS_F64) * (nst // nb)
+    fl = nst * (51 * H.npts + 16 * ne.value)
+    peak, kind = measured_peaks()
+    return {"dtype": "f64", "states": nst, "block": nb, "ms_per_step": s_per_step * 1e3,
+            "gbs": by / s_per_step / 1e9, "frac_of_hbm_peak": by / s_per_step / 1e9 / peak, "peak_source": kind,
+            "tflops": fl / s_per_step / 1e12, "fp64_nominal_tflops": 1.25,
+            "flops_model": "49 (stencil) + 2 (V) per point-state, 16 per sphere entry and state"}
+
+
 def learned_apply_timing(workload, n):
     """n applications of the learned preconditioner (the 1-8-8-1 network on
     the point map) to one 32-state residual block, after three untimed ones;
@@ -858,6 +894,9 @@ def main():
                     "pipeline": "32-state blocks from pinned host memory; copy in, H psi, copy out overlapped on 3 streams",
                     "max_rel_diff_vs_device_result": e2e_err},
             "gpu_launches": int(2 * (nst // NB) * args.steps), "clocks": clk}
+    if rank == 0 and world == 1:
+        del hpsi
+        line["f64_hpsi"] = f64_hpsi(H, workload)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gcpu, dt, cores, dt1 = cpu_baseline(workload, NB)
         by = bytes_per_apply  # the same FP32 block bytes, computed by the oracle in FP64
