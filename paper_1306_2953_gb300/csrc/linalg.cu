@@ -685,8 +685,12 @@ __global__ void __launch_bounds__(256) k_jacobi_grid(T *A, T *V, int n, int max_
             for (int k = tid; k < h; k += nt) {
                 int p, q;
                 circle_pair(r, k, m, p, q);
-                T c, s_;
-                jacobi_cs(__ldcg(dg + p), __ldcg(dg + q), __ldcg(pv + k), c, s_);
+                // (c, s) in FP64, rounded once: in FP32 the reciprocal square
+                // root and its Newton step leave c^2 + s^2 off 1 by a biased
+                // fraction of an ulp, which n rotations per round compound
+                double c64, s64;
+                jacobi_cs<double>((double)__ldcg(dg + p), (double)__ldcg(dg + q), (double)__ldcg(pv + k), c64, s64);
+                const T c = (T)c64, s_ = (T)s64;
                 cs[k] = c;
                 sn[k] = s_;
                 pp[k] = p;
