@@ -455,6 +455,7 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
                 bound = float(b.max())
                 certs.append({"sweep": st["sweeps"], "seconds": time.perf_counter() - t0,
                               "certify_seconds": time.perf_counter() - tc, "max_r64": float(r[:judged].max()),
+                              "worst_state": int(np.argmax(b)), "worst_fp32_state": int(np.argmax(res[:judged].cpu().numpy())),
                               "bound_ha": bound, "fp32_max_residual": rmax})
                 nxt = st["sweeps"] + cert_every
                 if bound <= tol or final:

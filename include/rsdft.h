@@ -644,6 +644,8 @@ int rs_scf_create(rs_solver *s, const rs_grid *g, const double *v_ext_host, cons
                   const rs_scf_cfg *cfg, rs_scf **out);
 
 /* One SCF step; residual = ||n_out - n_in|| (grid norm, before mixing) and
+ * n_out = sum_k f_k |phi_k|^2 / <phi_k|phi_k>, each orbital's norm summed in
+ * FP64 so that the density carries exactly n_electrons; and
  * energy = the Mermin free energy sum f eps - E_H - int n v_xc + E_xc
  * - sigma S of the step's input density (ion-ion repulsion omitted), both
  * may be NULL.  With an RS_F32 solver the eigenvalues eps that set the

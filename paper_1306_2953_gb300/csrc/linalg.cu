@@ -643,17 +643,22 @@ __global__ void __launch_bounds__(256) k_jacobi_grid(T *A, T *V, int n, int max_
         if (!grid_barrier(count, gen, G, err)) return;
         shift = *(volatile double *)(red_g + max_sweeps + 1) / n;
     }
-    // shifted diagonal, Frobenius norm (red_g[0]) and round 0's inputs
+    // shifted diagonal, round 0's inputs, and the Frobenius norm of the
+    // unshifted matrix (red_g[0]), against which the stopping test measures
+    // the off-diagonal part: inside the FP32 eigensolver's subspace steps a
+    // tighter test (the shifted norm) keeps rotating by couplings that an FP32
+    // Jacobi resolves only to about 1e-3 of a column, and those rotations
+    // stalled the 300-atom solve at that residual
     double loc = 0;
     for (int64_t e = bid * (int64_t)nt + tid; e < nn; e += (int64_t)G * nt) {
         T x = __ldcg(A + e);
+        loc += (double)x * (double)x;
         const int i = (int)(e / n);
         if (i == (int)(e % n)) {
             x = (T)((double)x - shift);
             A[e] = x;
             diag_of(0)[i] = x;
         }
-        loc += (double)x * (double)x;
     }
     for (int k = bid * nt + tid; k < h; k += G * nt) {
         int p, q;

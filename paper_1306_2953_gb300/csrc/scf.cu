@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "device.h"
+#include "linalg.h"
 #include "solver_view.h"
 
 namespace {
@@ -73,6 +74,11 @@ __global__ void k_density(const T *__restrict__ psi, int nst, const double *__re
         }
         n[p] = acc;
     }
+}
+
+__global__ void k_weight_by_norm(double *f, const double *norm2, double dV, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) f[k] /= dV * norm2[k];
 }
 
 __global__ void k_diff(const double *__restrict__ a, const double *__restrict__ b, int64_t np, double *__restrict__ c) {
@@ -157,7 +163,7 @@ struct rs_scf {
     rs_scf_cfg cfg{};
     int64_t np = 0;
     double dV = 0;
-    rs::DevBuf vext, n_in, n_out, F, vh, vxc, exc, veff, fdev, prev_n, prev_F, hist, dots, eps64;
+    rs::DevBuf vext, n_in, n_out, F, vh, vxc, exc, veff, fdev, prev_n, prev_F, hist, dots, eps64, norm2;
     std::vector<int> order;    // history slots, oldest first
     bool have_prev = false;
     std::vector<double> f;
@@ -262,6 +268,19 @@ extern "C" int rs_scf_step(rs_scf *S, double *residual, double *energy, void *st
     fd(S->mu, f);
     S->f = f;
     RS_CUDA(cudaMemcpyAsync(S->fdev.p, f.data(), sizeof(double) * f.size(), cudaMemcpyHostToDevice, st));
+    // each orbital's weight divided by its norm <phi_k|phi_k>, summed in FP64:
+    // FP32 orbitals are normalised through the tensor-core overlap, whose
+    // FP32 accumulation leaves norms off one by up to ~1e-6, enough to change
+    // the total charge (and every eigenvalue, through v_H) by ~1e-4
+    if (!S->norm2.p) RS_TRY(S->norm2.alloc(sizeof(double) * v.nst));
+    for (int k0 = 0; k0 < v.nst; k0 += 256) {
+        const int nc = std::min(256, v.nst - k0);
+        const int64_t es = v.dtype == RS_F64 ? 8 : 4;
+        const void *col = (const char *)v.psi + k0 * es;
+        RS_TRY(rs::coldots(v.dtype, col, v.nst, col, v.nst, nc, np, S->norm2.as<double>() + k0, st));
+    }
+    k_weight_by_norm<<<(v.nst + 255) / 256, 256, 0, st>>>(S->fdev.as<double>(), S->norm2.as<double>(), S->dV, v.nst);
+    RS_LAUNCH_CHECK();
     if (v.dtype == RS_F64)
         k_density<double><<<grid1d(np), 256, 0, st>>>((const double *)v.psi, v.nst, S->fdev.as<double>(), np,
                                                       S->n_out.as<double>());

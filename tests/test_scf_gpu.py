@@ -82,7 +82,9 @@ def test_scf_mol20_matches_oracle_golden(dtype):
         if r < spec.tol:
             break
     assert r < spec.tol
-    _, occ, _, _ = scf.state()
+    n_in, occ, _, _ = scf.state()
+    # charge neutrality of the self-consistent density (FP64 orbital norms)
+    assert abs(float(n_in.sum()) * lg.dV - spec.n_electrons) <= 1e-9 * spec.n_electrons
     S.step()
     eps = S.rayleigh_ritz_f64().cpu().numpy()
     occupied = np.array(gold["occupations"]) > 1e-2
