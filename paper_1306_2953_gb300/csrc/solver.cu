@@ -155,46 +155,67 @@ struct DotPairs {
 };
 
 // out[q * 64 + k] = sum_p a_q[p][k] b_q[p][k] for q < d.n, k < ncols (out
-// zeroed by the caller), accumulated to FP64-level accuracy as in k_coldots
-template <typename T>
-__global__ void __launch_bounds__(256) k_multidot(DotPairs d, int ncols, int64_t npts, double *out) {
+// zeroed by the caller), accumulated to FP64-level accuracy as in k_coldots.
+// The pairs name their operands in a list of distinct arrays (d.arr, d.ia,
+// d.ib): every array is read once per point row into the thread's own slots
+// of shared memory and each pair takes its operands from there, so pairs
+// that share an array do not read it from memory again.  Each pair's sum
+// runs over the points in the same order as one pair alone would.
+constexpr int MD_ARR = 2 * MD_MAX;
+struct DotArrays {
+    const void *arr[MD_ARR];
+    unsigned char ia[MD_MAX], ib[MD_MAX];
+    int narr, n;
+};
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(256) k_multidot(DotArrays d, int ncols, int64_t npts, double *out) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *vals = reinterpret_cast<T *>(smraw);   // [narr][blockDim]
     __shared__ double red[256];
-    const int rows = blockDim.x / ncols;
-    const int k = threadIdx.x % ncols, r = threadIdx.x / ncols;
-    for (int q = 0; q < d.n; ++q) {
-        const T *A = (const T *)d.a[q], *B = (const T *)d.b[q];
-        double acc = 0.0;
-        if (r < rows) {
-            if constexpr (sizeof(T) == 4) {
-                float hi = 0.f, lo = 0.f;
-                for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
-                    const float a = A[p * ncols + k], b = B[p * ncols + k];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int rows = nt / ncols;
+    const int k = tid % ncols, r = tid / ncols;
+    // compensated sums: FP32 (hi, lo) or FP64 (acc, comp) per pair
+    T s0[NP], s1[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) s0[q] = s1[q] = T(0);
+    if (r < rows) {
+        for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
+            for (int j = 0; j < d.narr; ++j) vals[j * nt + tid] = ((const T *)d.arr[j])[p * ncols + k];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if (q >= d.n) break;
+                const T a = vals[d.ia[q] * nt + tid], b = vals[d.ib[q] * nt + tid];
+                if constexpr (sizeof(T) == 4) {
                     const float pr = __fmul_rn(a, b);
                     const float pe = fmaf(a, b, -pr);
-                    const float sum = __fadd_rn(hi, pr);
-                    const float bb = __fsub_rn(sum, hi);
-                    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(pr, bb));
-                    hi = sum;
-                    lo = __fadd_rn(lo, __fadd_rn(err, pe));
-                }
-                acc = (double)hi + (double)lo;
-            } else {
-                double comp = 0.0;
-                for (int64_t p = (int64_t)blockIdx.x * rows + r; p < npts; p += (int64_t)gridDim.x * rows) {
-                    const double v = (double)A[p * ncols + k] * (double)B[p * ncols + k];
-                    const double y = v - comp;
-                    const double t = acc + y;
-                    comp = (t - acc) - y;
-                    acc = t;
+                    const float sum = __fadd_rn(s0[q], pr);
+                    const float bb = __fsub_rn(sum, s0[q]);
+                    const float err = __fadd_rn(__fsub_rn(s0[q], __fsub_rn(sum, bb)), __fsub_rn(pr, bb));
+                    s0[q] = sum;
+                    s1[q] = __fadd_rn(s1[q], __fadd_rn(err, pe));
+                } else {
+                    const double v = a * b;
+                    const double y = v - s1[q];
+                    const double t = s0[q] + y;
+                    s1[q] = (t - s0[q]) - y;
+                    s0[q] = t;
                 }
             }
         }
-        red[threadIdx.x] = r < rows ? acc : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        if (q >= d.n) break;
+        double acc = 0.0;
+        if (r < rows) acc = sizeof(T) == 4 ? (double)s0[q] + (double)s1[q] : (double)s0[q];
+        red[tid] = r < rows ? acc : 0.0;
         __syncthreads();
         if (r == 0) {
-            double s = 0;
-            for (int qq = 0; qq < rows; ++qq) s += red[qq * ncols + k];
-            atomicAdd(out + q * 64 + k, s);
+            double t = 0;
+            for (int qq = 0; qq < rows; ++qq) t += red[qq * ncols + k];
+            atomicAdd(out + q * 64 + k, t);
         }
         __syncthreads();
     }
@@ -370,11 +391,38 @@ __global__ void k_rmm_store(const double *dots, PairIndex t, int nb, double *A, 
 }
 
 int multidot(int dtype, const DotPairs &d, int ncols, int64_t npts, double *out, cudaStream_t st) {
+    if (d.n < 1 || d.n > MD_MAX) return fail(RS_EINVAL, "multidot: %d pairs", d.n);
     RS_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 64 * d.n, st));
+    // the distinct operand arrays of the pairs
+    DotArrays a{};
+    auto slot = [&](const void *ptr) {
+        for (int j = 0; j < a.narr; ++j)
+            if (a.arr[j] == ptr) return j;
+        a.arr[a.narr] = ptr;
+        return a.narr++;
+    };
+    for (int q = 0; q < d.n; ++q) {
+        a.ia[q] = (unsigned char)slot(d.a[q]);
+        a.ib[q] = (unsigned char)slot(d.b[q]);
+    }
+    a.n = d.n;
     const int rows = 256 / ncols;
     const unsigned blocks = (unsigned)std::min<int64_t>((npts + rows - 1) / rows, 152 * 8);
-    if (dtype == RS_F64) k_multidot<double><<<blocks, 256, 0, st>>>(d, ncols, npts, out);
-    else k_multidot<float><<<blocks, 256, 0, st>>>(d, ncols, npts, out);
+    const size_t es = dtype == RS_F64 ? 8 : 4, smem = (size_t)a.narr * 256 * es;
+    // the usual passes hold at most six pairs: a kernel with registers for
+    // six sums keeps more warps resident than one sized for MD_MAX
+    auto launch = [&](const void *fn, auto kern) -> int {
+        RS_TRY(smem_optin(fn, smem));
+        kern<<<blocks, 256, smem, st>>>(a, ncols, npts, out);
+        return RS_OK;
+    };
+    if (dtype == RS_F64) {
+        if (d.n <= 6) RS_TRY(launch((const void *)k_multidot<double, 6>, k_multidot<double, 6>));
+        else RS_TRY(launch((const void *)k_multidot<double, MD_MAX>, k_multidot<double, MD_MAX>));
+    } else {
+        if (d.n <= 6) RS_TRY(launch((const void *)k_multidot<float, 6>, k_multidot<float, 6>));
+        else RS_TRY(launch((const void *)k_multidot<float, MD_MAX>, k_multidot<float, MD_MAX>));
+    }
     RS_LAUNCH_CHECK();
     return RS_OK;
 }
