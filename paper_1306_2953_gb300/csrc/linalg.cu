@@ -690,12 +690,29 @@ __global__ void __launch_bounds__(256) k_jacobi_grid(T *A, T *V, int n, int max_
             for (int k = tid; k < h; k += nt) {
                 int p, q;
                 circle_pair(r, k, m, p, q);
-                // (c, s) in FP64, rounded once: in FP32 the reciprocal square
-                // root and its Newton step leave c^2 + s^2 off 1 by a biased
-                // fraction of an ulp, which n rotations per round compound
-                double c64, s64;
-                jacobi_cs<double>((double)__ldcg(dg + p), (double)__ldcg(dg + q), (double)__ldcg(pv + k), c64, s64);
-                const T c = (T)c64, s_ = (T)s64;
+                T c, s_;
+                if constexpr (sizeof(T) == 4) {
+                    // t = tan(theta) in FP32 (it only has to annihilate the
+                    // pivot to FP32 accuracy); c = (1 + t^2)^-1/2 and s = t c
+                    // from an FP64 reciprocal square root, rounded once: in
+                    // FP32 the reciprocal square root and its Newton step leave
+                    // c^2 + s^2 off 1 by a biased fraction of an ulp, which the
+                    // n rotations of a round compound.  Every CTA computes all
+                    // n/2 rotations, so their FP64 work is kept to one rsqrt.
+                    const float app = __ldcg(dg + p), aqq = __ldcg(dg + q), apq = __ldcg(pv + k);
+                    const float d = aqq - app, a2 = 2.f * apq;
+                    c = 1.f;
+                    s_ = 0.f;
+                    if (a2 * a2 > 0.f) {
+                        float tt = fabsf(a2) / (fabsf(d) + sqrtf(d * d + a2 * a2));
+                        if ((d < 0.f) != (a2 < 0.f)) tt = -tt;
+                        const double r = rsqrt(1.0 + (double)tt * (double)tt);
+                        c = (float)r;
+                        s_ = (float)((double)tt * r);
+                    }
+                } else {
+                    jacobi_cs<T>(__ldcg(dg + p), __ldcg(dg + q), __ldcg(pv + k), c, s_);
+                }
                 cs[k] = c;
                 sn[k] = s_;
                 pp[k] = p;
