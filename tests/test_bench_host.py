@@ -99,3 +99,34 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
 def test_cpu_model_is_named():
     m = bench.cpu_model()
     assert isinstance(m, str) and m
+
+
+def test_certificate_bound_covers_the_true_error():
+    """bench.certificate_bound, the cluster-aware Kato-Temple bound the
+    300-atom certification rests on: Ritz pairs of a perturbed basis of the
+    ten lowest eigenvectors of a small harmonic oscillator (levels of
+    degeneracy 1, 3 and 6), FP64 Ritz values and residual norms from the
+    oracle's certificate; for the judged states (the two lowest levels, as
+    the solver judges states below a buffer) every Ritz value lies within
+    its bound of the exact eigenvalue, and the bound of the isolated ground
+    state is second order (far below its residual norm)."""
+    import numpy as np
+    from oracle import certificate as oc, grid as og, hamiltonian as oh
+    g = og.box_grid(8, 0.45)
+    H = oh.Hamiltonian(g, wl.harmonic_potential(g.coords, 1.0))
+    lam, Phi = np.linalg.eigh(H.dense())
+    Phi = Phi / np.sqrt(g.dV)
+    rng = np.random.default_rng(2)
+    for scale in (1e-3, 1e-4):
+        # a smooth perturbation: components along the next thirty eigenvectors
+        X = Phi[:, :10] + scale * Phi[:, 10:40] @ rng.standard_normal((30, 10))
+        eps, res, _ = oc.ritz_certificate(H.apply, X, g.dV)
+        b = bench.certificate_bound(eps, res)
+        err = np.abs(eps - lam[:10])
+        assert np.all(err[:4] <= b[:4]), (err[:4], b[:4])
+        assert b[0] < 0.1 * res[0]
+        # the top cluster (the third level) has no known gap above: residual bound
+        assert np.all(b[7:] >= np.sqrt(np.sum(res[7:] ** 2)) * (1 - 1e-12))
+    # one cluster holding every Ritz value: the bound is its residual, never zero
+    eps, res = np.array([1.0, 1.0 + 1e-6]), np.array([1e-3, 1e-3])
+    assert np.allclose(bench.certificate_bound(eps, res), np.sqrt(2) * 1e-3)

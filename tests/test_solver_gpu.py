@@ -271,7 +271,11 @@ def certificate_bound(eps, res):
     residual ||R_C||^2 = sum r_i^2 and gap delta_C to the nearest Ritz value
     outside it, every eigenvalue it approximates lies within
     ||R_C||^2 / delta_C (Kato-Temple for an invariant subspace) when
-    delta_C > ||R_C||, else within ||R_C||."""
+    delta_C > ||R_C||, else within ||R_C||.  The gaps are those between
+    Ritz values, so the bound assumes no eigenvalue is missing between them
+    or below the lowest; above the highest Ritz value the spectrum is not
+    known, so the top cluster takes ||R_C|| (and so do the judged states
+    only if they reach the top)."""
     e = np.asarray(eps, dtype=np.float64)
     r = np.asarray(res, dtype=np.float64)
     order = np.argsort(e)
@@ -286,8 +290,11 @@ def certificate_bound(eps, res):
     b = np.empty(len(es))
     for c in clusters:
         R = np.sqrt(np.sum(rs[c] ** 2))
+        if c[-1] + 1 == len(es):
+            b[c] = R   # no gap known above the highest Ritz value
+            continue
         lo = es[c[0]] - es[c[0] - 1] if c[0] > 0 else np.inf
-        hi = es[c[-1] + 1] - es[c[-1]] if c[-1] + 1 < len(es) else np.inf
+        hi = es[c[-1] + 1] - es[c[-1]]
         d = min(lo, hi)
         b[c] = R * R / d if d > R else R
     out = np.empty(len(es))
