@@ -386,7 +386,7 @@ def certificate_bound(eps, res):
 
 
 def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f64_sweeps=2, cert_below=3e-4,
-                    cert_every=100, n_smooth=4):
+                    cert_every=100, n_smooth=4, emit=True):
     """Time to a certified tol Ha for a workload without an oracle reference
     (the 300-atom molecule): sweeps, with r_stop as the solver's tolerance
     (a block whose residuals are all below it is left alone), until the
@@ -488,7 +488,8 @@ def certified_solve(workload, modes, r_stop=1e-5, tol=1e-6, max_seconds=720.0, f
             f64["extrapolated_seconds"] = f64["solver_create_seconds"] + f64["seconds_per_sweep"] * f["sweeps"]
             f64["extrapolation"] = (f"measured FP64 seconds per sweep x the sweeps of the {mixed} solve (same "
                                     "start, same method)")
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
     return out
 
 
@@ -752,8 +753,12 @@ def main():
     ap.add_argument("--certified", default="",
                     help="workload(s) for the certified time to 1e-6 Ha without an oracle reference (e.g. "
                          "mol300_h0.3): prints one JSON object per workload and exits (no benchmark line)")
-    ap.add_argument("--certified-modes", default="f64_filter,mixed_filter,mixed_learned")
+    ap.add_argument("--certified-modes", default="f64_rmm,mixed_rmm,mixed_rmm_learned")
     ap.add_argument("--certified-max-seconds", type=float, default=720.0)
+    ap.add_argument("--with-certified", default="",
+                    help="opt-in: after the benchmark line's own measurements, run the certified solve of these "
+                         "workload(s) (e.g. mol300_h0.3, --certified-modes) and attach it to the line as "
+                         "'certified_eigensolve' (minutes per mode)")
     ap.add_argument("--certified-smooth", type=int, default=4,
                     help="FP64 smoothing steps before each certificate (rs_solver_certify_smoothed; 0: none)")
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -921,6 +926,11 @@ def main():
                               for n in args.eigensolve.split(",")]
     if rank == 0 and world == 1 and args.eigensolve != "none":
         line["scf"] = scf_bench(wl.SCF_MOL20)
+    if rank == 0 and world == 1 and args.with_certified:
+        line["certified_eigensolve"] = [
+            certified_solve(wl.WORKLOADS[n], args.certified_modes.split(","), max_seconds=args.certified_max_seconds,
+                            n_smooth=args.certified_smooth, emit=False)
+            for n in args.with_certified.split(",")]
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
